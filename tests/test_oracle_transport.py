@@ -1,0 +1,235 @@
+"""Pins of the oracle's charge (Nernst-Planck), Cahn-Hilliard and hydrodynamic LBEs:
+closed-form solutions and the exact discrete budgets each LBE must satisfy."""
+import math
+
+import numpy as np
+import pytest
+
+import analytic as an
+from oracle import ehd
+from paper_2407_01654_gb300 import workloads as wl
+
+
+def _sim(p, f, p0=None):
+    s = ehd.Sim(p)
+    s.set_fields(f["phi"], f["q"], f["ux"], f["uy"], p0)
+    return s
+
+
+# ---------------------------------------------------------------------------------------
+# Nernst-Planck LBE
+# ---------------------------------------------------------------------------------------
+
+
+def gaussian_error(N):
+    # The charge is independent of the potential when sigma and eps are uniform
+    # (R = -sigma q / eps), so one potential sub-iteration per step suffices here.
+    p, f, n, s0 = wl.gaussian_bell(N, poisson_fixed_iter=1)
+    s = _sim(p, f)
+    s.step(n)
+    qa = an.gaussian_bell(N, n, s0, f["q"].max(), p["alpha"], p["sigma_v"], p["eps_v"])
+    return an.rel_l2(s.fields()["q"], qa)
+
+
+def test_gaussian_bell_second_order():
+    """Charge relaxation + diffusion of a Gaussian bell (Sec. 6.2, Eq. weq78 with
+    diffusion and the exponent read as a decay): second-order convergence under diffusive
+    scaling, the order the paper reports (Fig. 3b)."""
+    e = [gaussian_error(N) for N in (32, 64, 128)]
+    assert e[-1] < 5e-3
+    assert math.log2(e[0] / e[1]) > 1.9 and math.log2(e[1] / e[2]) > 1.9
+
+
+def _charge_budget_case(seed=5):
+    p, f, info = wl.droplet(N=24, r=6.0, R=3.0, S=0.5, Ca=0.3)
+    p["alpha"] = 0.05
+    f = wl.perturbed(p, f, seed=seed, u_amp=3e-3, q_amp=2e-3)
+    return p, f
+
+
+def test_charge_budget_exact():
+    """Exact discrete charge budget of the NP LBE (Eqs. weq58-weq62 with the lagged R of
+    Algorithm 1): sum_x sum_i l changes per step by sum_x [R^{n-1}/(2 tau_l) +
+    (1 - 1/(2 tau_l)) R^n]; streaming with bounce-back conserves the total."""
+    p, f = _charge_budget_case()
+    s = _sim(p, f)
+    for _ in range(4):
+        before = s.l.sum()
+        R_prev = s.R_prev.copy()
+        s.step(1)
+        tl = s.P.tau_l
+        expected = np.sum(R_prev / (2 * tl) + (1 - 1 / (2 * tl)) * s.R_prev)
+        scale = np.abs(s.l).sum()
+        assert abs((s.l.sum() - before) - expected) < 1e-12 * scale
+
+
+def test_planted_mistake_charge_closure_fails(monkeypatch):
+    """Dropping the R/2 correction of the charge moment (Eq. weq62) breaks the charge
+    budget pin."""
+    orig = ehd.Sim._moments
+
+    def wrong(self):
+        phi, q, rho, ux, uy = orig(self)
+        return phi, q - 0.5 * self.R_prev, rho, ux, uy
+
+    monkeypatch.setattr(ehd.Sim, "_moments", wrong)
+    p, f = _charge_budget_case()
+    s = _sim(p, f)
+    s.step(1)
+    worst = 0.0
+    for _ in range(3):
+        before = s.l.sum()
+        R_prev = s.R_prev.copy()
+        s.step(1)
+        tl = s.P.tau_l
+        expected = np.sum(R_prev / (2 * tl) + (1 - 1 / (2 * tl)) * s.R_prev)
+        worst = max(worst, abs((s.l.sum() - before) - expected) / np.abs(s.l).sum())
+    assert worst > 1e-9
+
+
+# ---------------------------------------------------------------------------------------
+# Cahn-Hilliard LBE
+# ---------------------------------------------------------------------------------------
+
+
+def test_phase_mass_budget_exact():
+    """Exact discrete budget of the well-balanced CH LBE (Eq. weq45, sum G_i = -u.grad phi):
+    sum_x phi^{n+1} - sum_x phi^n = -sum_x [s^n + (s^n - s^{n-1})/2], s = u.grad phi,
+    with s^{-1} = s^0 at the first step.  (Without flow the phase mass is conserved.)"""
+    p, f = _charge_budget_case(seed=11)
+    s = _sim(p, f)
+    scale = np.abs(s.g).sum()
+    for k in range(4):
+        before = s.g.sum()
+        s_prev = s.s_prev.copy()
+        first = not s.history_valid
+        s.step(1)
+        s_now = s.s_prev
+        sp = s_now if first else s_prev
+        expected = -np.sum(s_now + 0.5 * (s_now - sp))
+        assert abs((s.g.sum() - before) - expected) < 1e-12 * scale
+
+
+def test_phase_mass_conserved_without_flow():
+    """No flow, no field: sum phi is conserved to rounding (1e-12 relative)."""
+    p, f = wl.planar_layers(nx=6, ny=20, varphi_high=0.0)
+    s = _sim(p, f)
+    m0 = s.g.sum()
+    s.step(50)
+    # the flow induced by the diffuse interface is at the rounding level here
+    assert abs(s.g.sum() - m0) < 1e-12 * abs(m0)
+
+
+def test_planted_mistake_ch_source_sign_fails(monkeypatch):
+    """Flipping the sign of the CH source G_i breaks the phase-mass budget pin."""
+    orig = ehd.g_source
+    monkeypatch.setattr(ehd, "g_source", lambda s_adv: -orig(s_adv))
+    p, f = _charge_budget_case(seed=11)
+    s = _sim(p, f)
+    before = s.g.sum()
+    s.step(1)
+    s_now = s.s_prev
+    expected = -np.sum(s_now)
+    assert abs((s.g.sum() - before) - expected) > 1e-9 * np.abs(s.g).sum()
+
+
+def test_flat_interface_stationary():
+    """The tanh profile 1/2 + 1/2 tanh(2y/W) is the CH equilibrium of the double-well free
+    energy with kappa and beta of Sec. 2.2; the LBE keeps it to O(dx^2/W^2): the drift
+    after 500 steps is small and falls by more than 4x when W doubles."""
+    drift = []
+    for W in (4.0, 8.0):
+        p, f = wl.planar_layers(nx=4, ny=64, width=W, varphi_high=0.0)
+        s = _sim(p, f)
+        s.step(500)
+        drift.append(np.abs(s.fields()["phi"] - f["phi"]).max())
+    assert drift[0] < 1e-2 and drift[0] / drift[1] > 4.0
+
+
+# ---------------------------------------------------------------------------------------
+# Hydrodynamic LBE
+# ---------------------------------------------------------------------------------------
+
+
+def test_momentum_budget_exact():
+    """Exact momentum budget of the hydro LBE on a fully periodic domain (Eqs. weq38,
+    weq39 with sum c_i R_bar_i = F, and the lagged u closure of Algorithm 1): sum_x sum_i c f
+    changes per step by sum_x [F^{n-1}/(2 tau_f) + (1 - 1/(2 tau_f)) F^n]."""
+    N = 20
+    p = wl.make_params(nx=N, ny=N, walls_y=0, rho_l=3.0, rho_v=1.0, mu_l=0.3, mu_v=0.05,
+                       eps_l=5.0, eps_v=1.0, sigma_l=0.01, sigma_v=0.05, alpha=0.05,
+                       gamma=0.01, width=4.0, neutralize_charge=1)
+    y, x = np.meshgrid(np.arange(N, dtype=float), np.arange(N, dtype=float), indexing="ij")
+    phi = wl.tanh_profile(5.0 - np.sqrt((x - 9.5) ** 2 + (y - 9.5) ** 2), 4.0)
+    f = wl.perturbed(p, dict(phi=phi, q=0 * phi, ux=0 * phi, uy=0 * phi), seed=2)
+    s = _sim(p, f)
+    cx = ehd.CX[:, None, None]
+    cy = ehd.CY[:, None, None]
+    for _ in range(3):
+        mx, my = (cx * s.f).sum(), (cy * s.f).sum()
+        Fx_prev, Fy_prev = s.Fx_prev.copy(), s.Fy_prev.copy()
+        phi_n = s.g.sum(0)
+        s.step(1)
+        tf = ehd.tau_f_of(s.P, phi_n)
+        ex = np.sum(Fx_prev / (2 * tf) + (1 - 1 / (2 * tf)) * s.Fx_prev)
+        ey = np.sum(Fy_prev / (2 * tf) + (1 - 1 / (2 * tf)) * s.Fy_prev)
+        scale = np.abs(s.f).sum()
+        assert abs((cx * s.f).sum() - mx - ex) < 1e-12 * scale
+        assert abs((cy * s.f).sum() - my - ey) < 1e-12 * scale
+
+
+def test_poiseuille_second_order():
+    """Body-force-driven channel flow between half-way bounce-back walls: the steady
+    parabola is kept to O(dx^2) (error falls ~4x per doubling)."""
+    errs = []
+    for ny in (16, 32):
+        nu, g = 0.1, 1e-6
+        p = wl.make_params(nx=4, ny=ny, walls_y=1, mu_l=nu, mu_v=nu, body_gx=g)
+        z = np.zeros((ny, 4))
+        ua = np.repeat(an.poiseuille(ny, g, nu)[:, None], 4, axis=1)
+        s = _sim(p, dict(phi=z, q=z, ux=ua, uy=z))
+        s.step(1500)
+        errs.append(an.rel_l2(s.fields()["ux"], ua))
+    assert errs[0] < 5e-3 and errs[0] / errs[1] > 3.5
+
+
+def test_taylor_green_decay():
+    """Taylor-Green vortex on a periodic grid decays as exp(-2 nu k^2 t) (textbook);
+    measured amplitude decay rate within 2 %."""
+    N, nu, U = 32, 0.05, 1e-3
+    k = 2 * math.pi / N
+    y, x = np.meshgrid(np.arange(N, dtype=float), np.arange(N, dtype=float), indexing="ij")
+    ux = -U * np.cos(k * x) * np.sin(k * y)
+    uy = U * np.sin(k * x) * np.cos(k * y)
+    p0 = -U * U / 4 * (np.cos(2 * k * x) + np.cos(2 * k * y))
+    p = wl.make_params(nx=N, ny=N, walls_y=0, mu_l=nu, mu_v=nu)
+    z = np.zeros((N, N))
+    s = _sim(p, dict(phi=z, q=z, ux=ux, uy=uy), p0)
+    t = 200
+    s.step(t)
+    F = s.fields()
+    amp = math.sqrt((F["ux"] ** 2 + F["uy"] ** 2).mean() / (ux ** 2 + uy ** 2).mean())
+    rate = -math.log(amp) / t
+    assert abs(rate / (2 * nu * k * k) - 1.0) < 0.02
+
+
+def test_laplace_law():
+    """Static drop: the pressure jump equals gamma / r in two dimensions (Laplace law),
+    measured as the time average over the drop's capillary ringing, within 10 %."""
+    N, r, gamma = 48, 12, 0.03
+    p = wl.make_params(nx=N, ny=N, walls_y=0, gamma=gamma, width=4.0, mobility=0.1,
+                       mu_l=0.2, mu_v=0.2)
+    y, x = np.meshgrid(np.arange(N, dtype=float), np.arange(N, dtype=float), indexing="ij")
+    d = np.sqrt((x - (N - 1) / 2) ** 2 + (y - (N - 1) / 2) ** 2)
+    phi0 = wl.tanh_profile(r - d, 4.0)
+    z = np.zeros((N, N))
+    s = _sim(p, dict(phi=phi0, q=z, ux=z, uy=z))
+    s.step(600)
+    jumps = []
+    for _ in range(12):
+        s.step(50)
+        F = s.fields()
+        inside = F["p"][d < r - 4].mean()
+        outside = F["p"][d > r + 6].mean()
+        jumps.append(inside - outside)
+    assert abs(np.mean(jumps) / (gamma / r) - 1.0) < 0.1
