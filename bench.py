@@ -1,0 +1,379 @@
+"""Benchmark of the coupled EHD phase-field LB time step on GB300.
+
+Workload: the reversed-electrowetting sessile drop on a 512 x 1024 lattice (periodic x,
+electrode walls in y, drop radius 80, density / viscosity ratio 10, permittivity ratio
+20, ramped wall potential, the paper's potential stopping rule at 1e-5), FP32 storage.
+One benchmark step is one full coupled time step over every node (moments, the
+potential sub-iteration loop to the tolerance, the fused g / l / f pass).  The run
+starts mid-ramp (step 10000 of a 20000-step ramp) so the wall potential changes every
+step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  Metric: coupled-step MLUPS = nodes x steps / s / 1e6 (with K,
+the mean number of potential sub-iterations per step).  N > 1 (torchrun): one
+independent replica per GPU (the step does not shard), value summed over ranks with the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2407_01654_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "coupled-step MLUPS"
+UNIT = "MLUPS"
+WORKLOAD = ("reversed-electrowetting sessile drop, 512x1024 lattice (r=80, rho/mu ratio 10, "
+            "eps ratio 20, ramped potential), full coupled step, potential rule tol 1e-5")
+# algorithmic bytes per node (FP32 populations read once and written once per pass):
+# coupled pass: 27 populations read + written (216 B) + 6 lagged quantities read + written
+# (48 B); potential sub-iteration: 8 populations read + written (64 B) + (a, q) read (8 B).
+BYTES_COUPLED = 216 + 48
+BYTES_POTENTIAL = 64 + 8
+# FP32 operations per node and potential sub-iteration (collision: moments 18, eight
+# relaxations with forcing and source 8 x 8; stream and stopping sums 14), counted from
+# the kernel source with a fused multiply-add as 2
+FLOPS_POTENTIAL = 96
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+L2_FLUSH_BYTES = 512 << 20
+
+
+def workload(seed=0):
+    p, f, info = wl.sessile_drop(seed=seed, start_step=10000)
+    f = wl.perturbed(p, f, seed=seed + 1, u_amp=1e-3, q_amp=1e-4)
+    return p, f, info
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("kernels.cu", "poisson.cu", "poisson_resident.cu", "ehd_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2407_01654_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current
+    kernel sources (profiles/traffic.json: {kernel: {"bytes_per_launch", "src_hash", ...}})."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path)).get(kernel)
+    if not d or d.get("src_hash") != kernel_source_hash():
+        return None
+    return d.get("bytes_per_launch_full_size")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sms)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def cpu_baseline(steps_cap=20, budget_s=25.0):
+    """The oracle (numpy, FP64, one host thread) on a bounded sample of the same
+    workload: the full 512 x 1024 lattice for a few coupled steps with the same rule."""
+    from oracle import ehd as orc
+    p, f, _ = workload()
+    sim = orc.Sim(p)
+    sim.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
+    sim.step(1)  # warm-up
+    n, k, t0 = 0, 0, time.perf_counter()
+    while n < steps_cap:
+        st = sim.step(1)
+        n += 1
+        k += st.poisson_iters[0]
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    nodes = p["nx"] * p["ny"]
+    return {"value": nodes * n / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} coupled steps of the full 512x1024 workload after 1 warm-up step, "
+                      f"mean {k / max(n, 1):.2f} potential sub-iterations/step, numpy FP64, "
+                      f"one thread",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from oracle import ehd as orc
+    p, f, _ = workload()
+    sim = orc.Sim(p)
+    sim.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
+    warm = min(args.warmup, 2)
+    sim.step(warm)
+    steps = min(args.steps, 20)
+    t0 = time.perf_counter()
+    st = sim.step(steps)
+    dt = time.perf_counter() - t0
+    nodes = p["nx"] * p["ny"]
+    v = nodes * steps / dt / 1e6
+    kbar = float(np.mean(st.poisson_iters))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": warm, "ms_per_step": dt / steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": nodes, "poisson_iters_mean": kbar,
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{steps} coupled steps of the full workload after {warm} "
+                                   f"warm-up steps (requested {args.steps}/{args.warmup}), "
+                                   "numpy FP64, one thread"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_2407_01654_gb300 import build as ehd_build
+    from paper_2407_01654_gb300 import ehd
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    if rank == 0 or world == 1:
+        ehd_build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    p, f, info = workload(seed=rank)
+    nodes = p["nx"] * p["ny"]
+    stream = torch.cuda.current_stream()
+    sim = ehd.Sim(p, stream=stream)
+    sim.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
+    resident = sim.uses_resident_loop()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    sim.step(args.warmup)
+
+    # timed region: K steps as step graphs, L2 flushed before each, CUDA events around
+    # each step on the stream the library uses
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with ClockSampler(dev) as clk:
+        for j in range(args.steps):
+            flush.fill_(j & 0xff)
+            starts[j].record(stream)
+            sim.step(1, stats=False)
+            ends[j].record(stream)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    st = sim.read_stats()
+    if st["status"] not in (0, 4):
+        raise RuntimeError(f"timed steps failed with status {st['status']}")
+    kt_total = st["poisson_iters_total"]
+    launches = st["kernel_launches"]
+    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    # per-kernel device times: a further stretch of steps with CUDA events around every
+    # launch (the same kernels, queued from the host instead of a graph)
+    prof_steps = min(args.steps, 20)
+    sim.profile(True)
+    sim.step(prof_steps, stats=False)
+    prof = sim.profile_read()
+    sim.profile(False)
+    pst = sim.read_stats()
+    prof_iters = pst["poisson_iters_total"]
+    t_local = step_ms / 1e3
+    if world > 1:
+        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    value = world * nodes * args.steps / t_max / 1e6
+    kbar = kt_total / args.steps
+    # e2e through the C ABI with host buffers: set_fields (host -> device), the same
+    # number of steps, read all fields back to the host
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        host = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in f.items()}
+        sim2 = ehd.Sim(p, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim2.set_fields(host["phi"], host["q"], host["ux"], host["uy"])
+        sim2.step(args.steps)
+        out = sim2.read_fields()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        sim2.close()
+        h2d = 4 * 4 * nodes
+        d2h = 8 * 4 * nodes + 80
+        e2e = {"value": nodes * args.steps / te / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "what": "ehd_set_fields(host double) + ehd_step(K) + ehd_read_fields(host double, "
+                       "8 fields); float32 copies"}
+        assert np.isfinite(out["phi"]).all()
+
+    if rank != 0:
+        return
+    peak, peak_kind = peaks()
+    nodes_f = float(nodes)
+    kinds = {}
+    for k in ("moments", "potential", "coupled"):
+        d = prof[k]
+        kinds[k] = {"ms_total": d["ms"], "launches": d["launches"],
+                    "us_per_launch": d["ms"] / max(d["launches"], 1) * 1e3}
+    kinds["potential"]["sub_iterations"] = prof_iters
+    kinds["potential"]["us_per_sub_iteration"] = prof["potential"]["ms"] / max(prof_iters, 1) * 1e3
+    kinds["potential_idle"] = {"ms_total": prof["potential_idle"]["ms"],
+                               "launches": prof["potential_idle"]["launches"]}
+    dom = max(("moments", "potential", "coupled"), key=lambda k: kinds[k]["ms_total"])
+    # the coupled pass streams populations through HBM: its roofline is the HBM copy rate
+    tc = kinds["coupled"]["us_per_launch"] * 1e-6
+    roof_coupled = {"bound": "hbm", "kernel": "k_coupled", "achieved": BYTES_COUPLED * nodes_f / tc / 1e9,
+                    "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)", "unit": "GB/s",
+                    "frac": BYTES_COUPLED * nodes_f / tc / 1e9 / peak,
+                    "traffic": recorded_traffic("k_coupled"), "bytes_per_node": BYTES_COUPLED,
+                    "launch_us": tc * 1e6}
+    t_it = kinds["potential"]["us_per_sub_iteration"] * 1e-6
+    if resident:
+        # on-chip loop: FP32 arithmetic per node and sub-iteration against the FP32 rate
+        fl = FLOPS_POTENTIAL * nodes_f / t_it / 1e12
+        roof_pot = {"bound": "alu", "kernel": "k_poisson_resident", "achieved": fl,
+                    "peak": FP32_PEAK_TFLOPS, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x "
+                    "2 flop x 2.07 GHz", "unit": "TFLOP/s", "frac": fl / FP32_PEAK_TFLOPS,
+                    "traffic": recorded_traffic("k_poisson_resident"),
+                    "flops_per_node_iteration": FLOPS_POTENTIAL,
+                    "sub_iteration_us": t_it * 1e6,
+                    "streamed_equivalent_GBps": BYTES_POTENTIAL * nodes_f / t_it / 1e9}
+    else:
+        roof_pot = {"bound": "hbm", "kernel": "k_poisson", "achieved": BYTES_POTENTIAL * nodes_f / t_it / 1e9,
+                    "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)", "unit": "GB/s",
+                    "frac": BYTES_POTENTIAL * nodes_f / t_it / 1e9 / peak,
+                    "traffic": recorded_traffic("k_poisson"), "bytes_per_node": BYTES_POTENTIAL,
+                    "launch_us": t_it * 1e6}
+    roof = roof_pot if dom == "potential" else roof_coupled
+    # whole-step fraction with the method's algorithmic bytes B(K) per node
+    step_bytes = BYTES_COUPLED + BYTES_POTENTIAL * kbar
+    step_frac = value / world * 1e6 * step_bytes / (peak * 1e9)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": nodes, "parallelism": f"replicas x{world}",
+                   "poisson_iters_mean": kbar, "contact_angle_deg": round(info["theta"], 2),
+                   "storage": "fp32 SoA populations",
+                   "potential_loop": "resident (on chip, one cooperative launch per step)"
+                   if resident else "streaming (one launch per sub-iteration, graph WHILE node)",
+                   "l2": "flushed between timed steps (512 MiB device write outside the events)",
+                   "step_algorithmic_bytes_per_node": step_bytes,
+                   "step_hbm_roofline_frac": step_frac, "wall_s": wall},
+        "roofline": roof,
+        "roofline_hbm_kernel": roof_coupled,
+        "kernels": kinds,
+        "gpu_launches": launches,
+        "e2e": e2e,
+    }
+    line["clocks"] = clk.summary()
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+    if world > 1:
+        import torch
+        backend = "nccl" if args.impl == "gb300" else "gloo"
+        if args.impl == "gb300":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group(backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_gpu(args, rank, world)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

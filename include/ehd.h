@@ -1,0 +1,216 @@
+/*
+ * ehd.h -- C ABI of the GB300 library for the coupled phase-field lattice Boltzmann
+ * time step for two-phase electrohydrodynamics (Xiong, Wang, Huang & Luo,
+ * arXiv 2407.01654).
+ *
+ * One simulation is one rectangular D2Q9 lattice (Sec. 3, Eq. weq37) in lattice units
+ * (dx = dt = 1), periodic in x, with walls or periodicity in y.  A time step is
+ * Algorithm 1 (Sec. 5): the Cahn-Hilliard LBE (Eqs. weq45-weq49), the potential LBE with
+ * its large-permittivity-ratio forcing sub-iterated to the relative-change tolerance
+ * (Eqs. weq52-weq55, eqA.16), the Nernst-Planck LBE (Eqs. weq56-weq62) and the
+ * hydrodynamic LBE (Eqs. weq38-weq43), with the isotropic stencils of Sec. 3.2 and the
+ * wetting / electrowetting wall rule (Eqs. weq68, weq69).
+ *
+ * Conventions for every call:
+ *   - Fields are row-major [ny][nx] arrays, x fastest.
+ *   - `mem` selects where an array lives: EHD_HOST arrays are double, EHD_DEVICE arrays
+ *     are float32 device pointers (e.g. from a torch tensor).  The caller owns every
+ *     array it passes; the library keeps no pointer to it after the call returns.
+ *   - Work is queued on the CUDA stream given to ehd_create.  Calls that return data to
+ *     the host (ehd_step's statistics, ehd_solve_potential, ehd_read_fields to host,
+ *     ehd_save_state) synchronise that stream before returning.
+ *   - Every call returns an ehd_status; the library never aborts the process and never
+ *     traps the GPU.  ehd_error_string names a code.
+ */
+#ifndef EHD_H
+#define EHD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ehd_status {
+  EHD_OK = 0,
+  EHD_ERR_INVALID_ARG = 1,     /* null pointer, bad size, unknown enum value            */
+  EHD_ERR_UNSTABLE_PARAMS = 2, /* a relaxation time <= 0.5 + 1e-3, or sigma/eps > 0.5   */
+  EHD_ERR_NOMEM = 3,           /* workspace too small or device allocation failed       */
+  EHD_ERR_NOT_CONVERGED = 4,   /* a potential loop hit poisson_max_iter (state advanced)*/
+  EHD_ERR_NONFINITE = 5,       /* NaN or Inf in phi or q (state advanced)               */
+  EHD_ERR_BUSY = 6,            /* batch: no free slot or memory for a request           */
+  EHD_ERR_CUDA = 7             /* a CUDA runtime call failed                            */
+} ehd_status;
+
+enum { EHD_HOST = 0, EHD_DEVICE = 1 };
+enum { EHD_FP32 = 0, EHD_FP16DEV = 1 };
+/* Implementation of the potential sub-iteration loop (same arithmetic, same results):
+ * STREAM runs one kernel per sub-iteration over populations in device memory; RESIDENT
+ * runs the whole loop in one cooperative kernel with the populations held on chip (only
+ * for lattices that fit, about 600k nodes on a GB300); AUTO picks RESIDENT when it fits. */
+enum { EHD_LOOP_AUTO = 0, EHD_LOOP_STREAM = 1, EHD_LOOP_RESIDENT = 2 };
+
+/* Field selection bits for ehd_read_fields. */
+enum {
+  EHD_F_PHI = 1u << 0,     /* order parameter phi = sum g (Eq. weq49)                    */
+  EHD_F_Q = 1u << 1,       /* charge q = sum l + R/2 (Eq. weq62, lagged R of Alg. 1)     */
+  EHD_F_VARPHI = 1u << 2,  /* potential of the last potential solve (Eq. weq55)          */
+  EHD_F_EX = 1u << 3,      /* E = -grad(varphi) of the last solve, local (Eq. eqA.16)    */
+  EHD_F_EY = 1u << 4,
+  EHD_F_UX = 1u << 5,      /* velocity, rho u = sum c f + F/2 (Eq. weq43)                */
+  EHD_F_UY = 1u << 6,
+  EHD_F_P = 1u << 7        /* hydrodynamic pressure (Eq. eq32)                            */
+};
+#define EHD_NUM_FIELDS 8
+
+/* Parameters, lattice units.  Phase l is phi = 1, phase v is phi = 0 (Sec. 2.2). */
+typedef struct ehd_params {
+  int32_t nx, ny;               /* lattice size; x is periodic                           */
+  int32_t walls_y;              /* 1: walls half-way below row 0 and above row ny-1;
+                                   0: y periodic                                          */
+  int32_t precision;            /* EHD_FP32 or EHD_FP16DEV population storage             */
+  double rho_l, rho_v;          /* densities (linear in phi, Eq. weq36)                   */
+  double mu_l, mu_v;            /* dynamic viscosities (linear); tau_f from
+                                   mu = rho c_s^2 (tau_f - 1/2) (Sec. 3.1)                */
+  double sigma_l, sigma_v;      /* conductivities (linear)                                */
+  double eps_l, eps_v;          /* permittivities (Hermite law, Remark II);
+                                   tau_h = 1/2 + eps_v / c_s^2 (Eq. eqA.15)               */
+  double alpha;                 /* charge diffusivity; tau_l = 1/2 + alpha / c_s^2       */
+  double gamma, width, mobility;/* surface tension, interface width W, mobility M:
+                                   beta = 12 gamma/W, kappa = 3 gamma W/2,
+                                   tau_g = 1/2 + M / c_s^2 (Secs. 2.2, 3.2)               */
+  double theta_bottom_deg;      /* Young contact angles of the walls (Eq. weq68)          */
+  double theta_top_deg;
+  double ew_bottom;             /* electrowetting number eta/d of the bottom wall         */
+  double ew_sign;               /* +1 classical, -1 reversed electrowetting (Sec. 7.2)    */
+  double varphi_bottom;         /* Dirichlet wall potentials                              */
+  double varphi_top;
+  int32_t ramp_steps;           /* wall potentials ramp linearly from 0 over this many
+                                   steps (0: applied at once); the electrowetting number
+                                   follows the square of the ramp fraction                */
+  int32_t neutralize_charge;    /* 1: the potential source is q - mean(q) (for y periodic) */
+  double body_gx, body_gy;      /* optional body acceleration, force rho g                */
+  double poisson_tol;           /* stopping tolerance of the potential loop (Alg. 1: 1e-5)*/
+  int32_t poisson_max_iter;     /* cap on sub-iterations per solve                        */
+  int32_t poisson_min_iter;     /* at least this many sub-iterations (>= 1)               */
+  int32_t poisson_fixed_iter;   /* > 0: exactly this many sub-iterations, no stopping test*/
+  int32_t poisson_loop;         /* EHD_LOOP_AUTO, EHD_LOOP_STREAM or EHD_LOOP_RESIDENT     */
+  int64_t start_step;           /* step counter after ehd_set_fields                      */
+} ehd_params;
+
+/* Statistics of one ehd_step call. */
+typedef struct ehd_stats {
+  int64_t step;                 /* step counter after the call                           */
+  int32_t steps;                /* time steps made by the call                           */
+  int32_t poisson_iters_total;  /* potential sub-iterations over those steps             */
+  int32_t poisson_iters_min;
+  int32_t poisson_iters_max;
+  int32_t not_converged_steps;  /* steps whose potential loop hit poisson_max_iter       */
+  int32_t nonfinite;            /* 1 if phi or q held NaN/Inf at some step               */
+  double last_rel_change;       /* relative change of the last sub-iteration             */
+  double sum_phi;               /* FP64 sum of phi over the lattice, last step's level   */
+  double sum_q;                 /* FP64 sum of q, same level                             */
+  int64_t kernel_launches;      /* CUDA kernel launches the call queued                  */
+} ehd_stats;
+
+/* Device time per kernel kind, from CUDA events recorded around each launch on the
+ * simulation's stream while profiling is on.  Kinds: 0 moments, 1 potential
+ * sub-iteration, 2 potential launches queued after the loop had finished (they return at
+ * once), 3 coupled collide-and-push. */
+typedef struct ehd_kernel_times {
+  double ms[4];
+  int64_t launches[4];
+} ehd_kernel_times;
+
+typedef struct ehd_sim ehd_sim;
+
+/* Device workspace a simulation with these parameters needs, in bytes.
+ * Errors: EHD_ERR_INVALID_ARG (null pointer, nx or ny < 1). */
+int ehd_workspace_bytes(const ehd_params* params, size_t* bytes);
+
+/* Validates the parameters and creates a simulation.
+ *   params      copied; not referenced afterwards.
+ *   workspace   device memory of at least ehd_workspace_bytes() bytes, 256-byte aligned,
+ *               owned by the caller and kept alive until ehd_destroy; or NULL, in which
+ *               case the library allocates (and frees) its own.
+ *   stream      cudaStream_t on which every later call queues its work (NULL: the
+ *               default stream).
+ * The populations are zero until ehd_set_fields.
+ * Errors: EHD_ERR_INVALID_ARG, EHD_ERR_UNSTABLE_PARAMS, EHD_ERR_NOMEM, EHD_ERR_CUDA. */
+int ehd_create(const ehd_params* params, void* workspace, size_t workspace_bytes,
+               void* stream, ehd_sim** out);
+
+/* Initialisation, Algorithm 1 step 1: populations at equilibrium with the given fields
+ * (g = g_eq(phi, hbar(phi, E = 0)), l = l_eq(q, u), f = f_eq(p, u)), potential
+ * distribution at equilibrium with the potential interpolated linearly between the walls,
+ * lagged quantities zero, then one potential solve with the parameters' rule.
+ *   phi, q, ux, uy  required, [ny][nx]; p optional (NULL: 0).
+ *   mem             EHD_HOST (double) or EHD_DEVICE (float32).
+ * Returns the status of the potential solve (EHD_ERR_NOT_CONVERGED if it hit the cap). */
+int ehd_set_fields(ehd_sim* sim, const void* phi, const void* q, const void* ux,
+                   const void* uy, const void* p, int mem);
+
+/* Advances nsteps time steps (Algorithm 1 steps 2-6).  With `stats` non-NULL the call
+ * clears the statistics, synchronises the stream at the end and fills `stats` for these
+ * steps.  With `stats` NULL nothing is synchronised and the statistics keep accumulating
+ * until ehd_read_stats.  The state always advances; the return code reports
+ * EHD_ERR_NOT_CONVERGED / EHD_ERR_NONFINITE if a step met that condition (known only
+ * when the statistics are read). */
+int ehd_step(ehd_sim* sim, int nsteps, ehd_stats* stats);
+
+/* Which potential loop this simulation runs: EHD_LOOP_STREAM or EHD_LOOP_RESIDENT
+ * (negative: invalid handle). */
+int ehd_loop_kind(const ehd_sim* sim);
+
+/* Statistics accumulated since they were last cleared (by ehd_step with stats, or by this
+ * call); synchronises the stream and clears them.  Returns the status those steps would
+ * have returned. */
+int ehd_read_stats(ehd_sim* sim, ehd_stats* stats);
+
+/* Runs the potential loop alone for the phi and q of the current populations (the
+ * potential sub-iterations of Algorithm 1 step 3), with tolerance `tol` and cap
+ * `max_iter` (tol <= 0 or max_iter <= 0: the parameters' values).  Writes the number of
+ * sub-iterations and the last relative change when the pointers are non-NULL.
+ * Synchronises the stream. */
+int ehd_solve_potential(ehd_sim* sim, double tol, int max_iter, int* iters,
+                        double* rel_change);
+
+/* Macroscopic fields of the current state.  For each bit set in `mask`, in bit order,
+ * the next pointer of `out` receives a [ny][nx] array.  PHI, Q, UX, UY and P are those of
+ * the current populations; VARPHI, EX and EY those of the last potential solve (which,
+ * after a step, used that step's phi and q).  mem: EHD_HOST (double) or EHD_DEVICE
+ * (float32). */
+int ehd_read_fields(ehd_sim* sim, unsigned mask, void* const* out, int mem);
+
+/* Complete state (populations, potential distribution, lagged quantities, step counter)
+ * as an opaque host blob: ehd_state_bytes gives its size; ehd_save_state fills `buf`;
+ * ehd_load_state restores it into a simulation with the same parameters, after which the
+ * run continues bit for bit as if it had not been interrupted. */
+int ehd_state_bytes(const ehd_sim* sim, size_t* bytes);
+int ehd_save_state(ehd_sim* sim, void* buf, size_t bytes);
+int ehd_load_state(ehd_sim* sim, const void* buf, size_t bytes);
+
+/* Per-launch event timing: ehd_profile(sim, 1) clears the totals and starts recording,
+ * ehd_profile(sim, 0) stops; ehd_profile_read synchronises the stream and returns the
+ * totals since profiling was turned on. */
+int ehd_profile(ehd_sim* sim, int enable);
+int ehd_profile_read(ehd_sim* sim, ehd_kernel_times* out);
+
+/* Releases the simulation (and its workspace if the library allocated it). */
+void ehd_destroy(ehd_sim* sim);
+
+/* Static description of a status code. */
+const char* ehd_error_string(int code);
+
+/* Library version string. */
+const char* ehd_version(void);
+
+/* sizeof(ehd_params) and sizeof(ehd_stats) as compiled into the library, so that a
+ * binding can check its own struct layouts.  Either pointer may be NULL. */
+int ehd_abi_sizes(size_t* params_bytes, size_t* stats_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EHD_H */

@@ -1,0 +1,70 @@
+"""Builds the CUDA library libehd.so in-tree for sm_103a (GB300).
+
+Each translation unit is compiled by nvcc in parallel, then linked into one shared
+library with the CUDA runtime linked statically.  Usage: python -m
+paper_2407_01654_gb300.build [--verbose] [--ptxas-info]
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+BUILD_DIR = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libehd.so")
+SOURCES = ["kernels.cu", "poisson.cu", "poisson_resident.cu", "api.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+         "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
+
+
+def nvcc():
+    exe = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(exe):
+        raise RuntimeError("nvcc not found")
+    return exe
+
+
+def _run(cmd, verbose):
+    if verbose:
+        print(" ".join(cmd), flush=True)
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"command failed ({r.returncode}): {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+    return r.stdout + r.stderr
+
+
+def build(verbose=False, ptxas_info=False, force=False):
+    """Compiles the library if a source is newer than it (or force).  Returns its path."""
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    srcs = [os.path.join(CSRC, s) for s in SOURCES]
+    deps = srcs + [os.path.join(CSRC, "ehd_internal.cuh"), os.path.join(ROOT, "include", "ehd.h")]
+    if (not force and os.path.exists(LIB)
+            and all(os.path.getmtime(LIB) >= os.path.getmtime(d) for d in deps)):
+        return LIB
+    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    objs = []
+    cmds = []
+    for s in srcs:
+        o = os.path.join(BUILD_DIR, os.path.basename(s).replace(".cu", ".o"))
+        objs.append(o)
+        cmds.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", s, "-o", o])
+    with cf.ThreadPoolExecutor(max_workers=len(cmds)) as ex:
+        outs = list(ex.map(lambda c: _run(c, verbose), cmds))
+    if ptxas_info:
+        for o in outs:
+            print(o)
+    tmp = LIB + ".tmp"
+    _run([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs], verbose)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    build(verbose="--verbose" in sys.argv, ptxas_info="--ptxas-info" in sys.argv, force=True)
+    print(LIB)

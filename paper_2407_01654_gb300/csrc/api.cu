@@ -1,0 +1,716 @@
+// Host side of the C ABI declared in include/ehd.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ehd.h"
+#include "ehd_internal.cuh"
+
+using namespace ehd;
+
+struct ehd_sim {
+  ehd_params P;
+  KParams kp;
+  Buffers b;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool own_ws = false;
+  cudaStream_t stream = nullptr;
+  int cur = 0;              // which population copy is current
+  int64_t n = 0;            // step counter
+  bool history_valid = false;
+  int last_k = 1;           // sub-iterations of the last potential solve
+  Ctl* h_ctl = nullptr;     // pinned mirror of the loop control
+  DevStats* h_stats = nullptr;
+  float* h_stage = nullptr; // pinned staging for host field I/O, NIO * N floats
+  int64_t launches = 0;     // kernel launches queued since the statistics were cleared
+  int64_t graph_steps = 0;  // steps run as graphs since then
+  int64_t host_iters = 0;   // potential sub-iterations run from the host loop since then
+  bool stats_live = false;  // device statistics are accumulating
+  // per-launch event timing
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;     // start/stop pairs
+  std::vector<int> ev_kind;        // kind per pair
+  size_t ev_used = 0;              // pairs recorded and not yet accumulated
+  double prof_ms[4] = {0, 0, 0, 0};
+  int64_t prof_n[4] = {0, 0, 0, 0};
+  // one step graph per population copy (moments -> while{potential} -> coupled)
+  bool graphs_tried = false;
+  bool graphs_ok = false;
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  // resident (on-chip) potential loop, when the lattice fits
+  bool resident_ok = false;
+  ResidentGeom rg{};
+  int rthreads = 0;
+  size_t rsmem = 0;
+};
+
+namespace {
+
+constexpr double CS2D = 1.0 / 3.0;
+constexpr uint64_t STATE_MAGIC = 0x4548443153544154ull;  // "EHD1STAT"
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+  size_t ss, pops, h, hist, phi, aq, io, tmp, partials, ctl, stats, exports, rpartials, total;
+  size_t export_floats, rtiles;
+};
+
+// Design target for the resident loop's tiling: the GB300's SM count.  On a device with
+// fewer SMs the tiles are larger and fewer, which needs less export space.
+constexpr int DESIGN_SMS = 152;
+
+Layout layout_for(const ehd_params& P) {
+  const int64_t N = (int64_t)P.nx * P.ny;
+  Layout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes, 256);
+    return at;
+  };
+  L.ss = take(sizeof(StepState) * 2);
+  L.pops = take(sizeof(float) * 2 * NPOP * (size_t)N);
+  L.h = take(sizeof(float) * 2 * NH * (size_t)N);
+  L.hist = take(sizeof(float) * NHIST * (size_t)N);
+  L.phi = take(sizeof(float) * (size_t)N);
+  L.aq = take(sizeof(float2) * (size_t)N);
+  L.io = take(sizeof(float) * NIO * (size_t)N);
+  L.tmp = take(sizeof(float) * (size_t)N);
+  L.partials = take(sizeof(double2) * MAX_PARTIALS);
+  L.ctl = take(sizeof(Ctl));
+  L.stats = take(sizeof(DevStats));
+  ResidentGeom g;
+  int th;
+  size_t sm;
+  KParams kp{};
+  kp.nx = P.nx;
+  kp.ny = P.ny;
+  L.export_floats = 0;
+  L.rtiles = 0;
+  if (resident_geometry(kp, DESIGN_SMS, &g, &th, &sm)) {
+    L.rtiles = (size_t)g.ntx * g.nty;
+    L.export_floats = 2 * L.rtiles * 8 * (size_t)g.pmax;
+  }
+  L.exports = take(sizeof(float) * (L.export_floats ? L.export_floats : 1));
+  L.rpartials = take(sizeof(double2) * 2 * (L.rtiles > 0 ? DESIGN_SMS : 1));
+  L.total = o;
+  return L;
+}
+
+bool sizes_ok(const ehd_params* p) {
+  if (p->nx < 1 || p->ny < 1) return false;
+  const int64_t N = (int64_t)p->nx * p->ny;
+  // the one-pass reductions hold one partial per CTA
+  if ((N + 255) / 256 > MAX_PARTIALS) return false;
+  return true;
+}
+
+int validate(const ehd_params* p) {
+  if (!p || !sizes_ok(p)) return EHD_ERR_INVALID_ARG;
+  if (p->walls_y != 0 && p->walls_y != 1) return EHD_ERR_INVALID_ARG;
+  if (p->precision != EHD_FP32) return EHD_ERR_INVALID_ARG;
+  if (!(p->rho_l > 0 && p->rho_v > 0 && p->mu_l > 0 && p->mu_v > 0 && p->eps_l > 0 &&
+        p->eps_v > 0 && p->sigma_l >= 0 && p->sigma_v >= 0 && p->alpha > 0 && p->gamma >= 0 &&
+        p->width > 0 && p->mobility > 0))
+    return EHD_ERR_INVALID_ARG;
+  if (p->poisson_fixed_iter < 0 || p->poisson_max_iter < 1 || p->poisson_min_iter < 1)
+    return EHD_ERR_INVALID_ARG;
+  if (p->poisson_fixed_iter == 0 && !(p->poisson_tol > 0)) return EHD_ERR_INVALID_ARG;
+  if (p->ramp_steps < 0) return EHD_ERR_INVALID_ARG;
+  if (p->poisson_loop < EHD_LOOP_AUTO || p->poisson_loop > EHD_LOOP_RESIDENT)
+    return EHD_ERR_INVALID_ARG;
+  const double lim = 0.5 + 1e-3;
+  const double tau_g = 0.5 + p->mobility / CS2D;
+  const double tau_h = 0.5 + p->eps_v / CS2D;
+  const double tau_l = 0.5 + p->alpha / CS2D;
+  if (tau_g <= lim || tau_h <= lim || tau_l <= lim) return EHD_ERR_UNSTABLE_PARAMS;
+  for (int j = 0; j <= 100; ++j) {
+    const double phi = j / 100.0;
+    const double rho = p->rho_v + (p->rho_l - p->rho_v) * phi;
+    const double mu = p->mu_v + (p->mu_l - p->mu_v) * phi;
+    const double tau_f = 0.5 + mu / (rho * CS2D);
+    const double eps = p->eps_v + phi * phi * (2 * phi - 3) * (p->eps_v - p->eps_l);
+    const double sig = p->sigma_v + (p->sigma_l - p->sigma_v) * phi;
+    if (tau_f <= lim) return EHD_ERR_UNSTABLE_PARAMS;
+    if (sig / eps > 0.5) return EHD_ERR_UNSTABLE_PARAMS;
+  }
+  return EHD_OK;
+}
+
+KParams make_kparams(const ehd_params& P) {
+  KParams k{};
+  k.nx = P.nx;
+  k.ny = P.ny;
+  k.N = P.nx * P.ny;
+  k.walls = P.walls_y;
+  k.neutralize = P.neutralize_charge ? 1 : 0;
+  k.rho_v = (float)P.rho_v;
+  k.drho = (float)(P.rho_l - P.rho_v);
+  k.mu_v = (float)P.mu_v;
+  k.dmu = (float)(P.mu_l - P.mu_v);
+  k.sig_v = (float)P.sigma_v;
+  k.dsig = (float)(P.sigma_l - P.sigma_v);
+  k.eps_v = (float)P.eps_v;
+  k.deps = (float)(P.eps_v - P.eps_l);
+  const double beta = 12.0 * P.gamma / P.width;
+  const double kappa = 1.5 * P.gamma * P.width;
+  k.beta4 = (float)(4.0 * beta);
+  k.kappa = (float)kappa;
+  k.wet_a = (float)(kappa > 0 ? std::sqrt(2.0 * beta / kappa) : 4.0 / P.width);
+  const double tau_g = 0.5 + P.mobility / CS2D;
+  const double tau_l = 0.5 + P.alpha / CS2D;
+  const double tau_h = 0.5 + P.eps_v / CS2D;
+  k.omega_g = (float)(1.0 / tau_g);
+  k.omega_l = (float)(1.0 / tau_l);
+  k.pref_l = (float)(1.0 - 0.5 / tau_l);
+  k.omega_h = (float)(1.0 / tau_h);
+  k.cs2tauh = (float)(CS2D * tau_h);
+  k.gbx = (float)P.body_gx;
+  k.gby = (float)P.body_gy;
+  const double pi = 3.14159265358979323846;
+  k.cos_yb = std::cos(P.theta_bottom_deg * pi / 180.0);
+  k.cos_yt = std::cos(P.theta_top_deg * pi / 180.0);
+  k.ew_signed = P.ew_sign * P.ew_bottom;
+  k.varphi_b = P.varphi_bottom;
+  k.varphi_t = P.varphi_top;
+  k.ramp_steps = P.ramp_steps;
+  return k;
+}
+
+#define EHD_CUDA(call)                         \
+  do {                                         \
+    cudaError_t e_ = (call);                   \
+    if (e_ != cudaSuccess) return EHD_ERR_CUDA; \
+  } while (0)
+
+// Accumulates recorded event pairs into the totals (synchronises the stream).
+int prof_flush(ehd_sim* s) {
+  if (!s->ev_used) return EHD_OK;
+  EHD_CUDA(cudaStreamSynchronize(s->stream));
+  for (size_t j = 0; j < s->ev_used; ++j) {
+    float ms = 0.0f;
+    EHD_CUDA(cudaEventElapsedTime(&ms, s->ev[2 * j], s->ev[2 * j + 1]));
+    s->prof_ms[s->ev_kind[j]] += ms;
+    s->prof_n[s->ev_kind[j]] += 1;
+  }
+  s->ev_used = 0;
+  return EHD_OK;
+}
+
+// Records the start event of a launch of the given kind; returns its pair index or -1.
+long prof_begin(ehd_sim* s, int kind) {
+  s->launches += 1;
+  if (!s->profiling) return -1;
+  if (s->ev_used >= 4096 && prof_flush(s) != EHD_OK) return -1;
+  if (2 * (s->ev_used + 1) > s->ev.size()) {
+    for (int j = 0; j < 2; ++j) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      s->ev.push_back(e);
+    }
+    s->ev_kind.push_back(0);
+  }
+  const size_t j = s->ev_used++;
+  s->ev_kind[j] = kind;
+  cudaEventRecord(s->ev[2 * j], s->stream);
+  return (long)j;
+}
+
+void prof_end(ehd_sim* s, long j) {
+  if (j >= 0) cudaEventRecord(s->ev[2 * j + 1], s->stream);
+}
+
+#define EHD_LAUNCH(s, kind, call)             \
+  do {                                        \
+    const long pj_ = prof_begin((s), (kind)); \
+    cudaError_t e_ = (call);                  \
+    prof_end((s), pj_);                       \
+    if (e_ != cudaSuccess) return EHD_ERR_CUDA; \
+  } while (0)
+
+// The potential loop of one solve.  The moments kernel has reset the control.  Fixed
+// count: exactly that many launches.  Stopping rule: launches are queued in chunks; a
+// launch after the rule has fired returns at once; the pinned control mirror tells the
+// host when to stop queueing.
+int run_potential_loop(ehd_sim* s, int fixed, int max_iter) {
+  if (s->resident_ok) {
+    // the whole loop in one cooperative launch
+    EHD_LAUNCH(s, 1, launch_poisson_resident(s->kp, s->rg, s->rthreads, s->rsmem, s->b,
+                                             s->stream));
+    EHD_CUDA(cudaMemcpyAsync(s->h_ctl, s->b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost,
+                             s->stream));
+    EHD_CUDA(cudaStreamSynchronize(s->stream));
+    if (s->h_ctl->bar_error || !s->h_ctl->done) return EHD_ERR_CUDA;
+    s->last_k = s->h_ctl->iter;
+    return s->h_ctl->converged ? EHD_OK : EHD_ERR_NOT_CONVERGED;
+  }
+  if (fixed > 0) {
+    for (int i = 0; i < fixed; ++i) EHD_LAUNCH(s, 1, launch_poisson(s->kp, s->b, s->stream));
+    return EHD_OK;
+  }
+  int queued = 0;
+  int chunk = s->last_k + 1;
+  const size_t first_pair = s->ev_used;
+  for (;;) {
+    if (chunk > max_iter - queued + 1) chunk = max_iter - queued + 1;
+    if (chunk < 1) chunk = 1;
+    for (int i = 0; i < chunk; ++i) EHD_LAUNCH(s, 1, launch_poisson(s->kp, s->b, s->stream));
+    queued += chunk;
+    EHD_CUDA(cudaMemcpyAsync(s->h_ctl, s->b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost,
+                             s->stream));
+    EHD_CUDA(cudaStreamSynchronize(s->stream));
+    if (s->h_ctl->done) {
+      s->last_k = s->h_ctl->iter;
+      // launches after the loop finished did no work: file them under their own kind
+      if (s->profiling && s->ev_used >= first_pair)
+        for (size_t j = first_pair + (size_t)s->h_ctl->iter; j < s->ev_used; ++j)
+          s->ev_kind[j] = 2;
+      return s->h_ctl->converged ? EHD_OK : EHD_ERR_NOT_CONVERGED;
+    }
+    if (queued > max_iter + 2) return EHD_ERR_CUDA;  // the control never finished
+    chunk = chunk * 2;
+  }
+}
+
+void destroy_graphs(ehd_sim* s) {
+  for (int c = 0; c < 2; ++c) {
+    if (s->exec[c]) cudaGraphExecDestroy(s->exec[c]);
+    if (s->graph[c]) cudaGraphDestroy(s->graph[c]);
+    s->exec[c] = nullptr;
+    s->graph[c] = nullptr;
+  }
+  s->graphs_ok = false;
+}
+
+// Builds the two step graphs once.  If the driver refuses (e.g. no conditional nodes),
+// steps run through the host-side loop instead; both paths run the same kernels.
+void ensure_graphs(ehd_sim* s) {
+  if (s->graphs_tried) return;
+  s->graphs_tried = true;
+  const ehd_params& P = s->P;
+  for (int c = 0; c < 2; ++c) {
+    if (build_step_graph(s->kp, s->b, c, P.poisson_tol, P.poisson_min_iter, P.poisson_max_iter,
+                         P.poisson_fixed_iter, s->resident_ok ? &s->rg : nullptr, s->rthreads,
+                         s->rsmem, &s->graph[c]) != cudaSuccess ||
+        cudaGraphInstantiate(&s->exec[c], s->graph[c], 0) != cudaSuccess) {
+      cudaGetLastError();
+      destroy_graphs(s);
+      return;
+    }
+  }
+  s->graphs_ok = true;
+}
+
+int stage_in(ehd_sim* s, const void* src, int slot, int mem) {
+  const size_t N = (size_t)s->kp.N;
+  float* dst = s->b.io + slot * N;
+  if (mem == EHD_DEVICE) {
+    EHD_CUDA(cudaMemcpyAsync(dst, src, N * sizeof(float), cudaMemcpyDeviceToDevice,
+                             s->stream));
+  } else {
+    const double* d = static_cast<const double*>(src);
+    float* stage = s->h_stage + slot * N;
+    for (size_t i = 0; i < N; ++i) stage[i] = (float)d[i];
+    EHD_CUDA(cudaMemcpyAsync(dst, stage, N * sizeof(float), cudaMemcpyHostToDevice,
+                             s->stream));
+  }
+  return EHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ehd_version(void) { return "ehd-gb300 0.1 (sm_103a)"; }
+
+int ehd_abi_sizes(size_t* params_bytes, size_t* stats_bytes) {
+  if (params_bytes) *params_bytes = sizeof(ehd_params);
+  if (stats_bytes) *stats_bytes = sizeof(ehd_stats);
+  return EHD_OK;
+}
+
+const char* ehd_error_string(int code) {
+  switch (code) {
+    case EHD_OK: return "ok";
+    case EHD_ERR_INVALID_ARG: return "invalid argument";
+    case EHD_ERR_UNSTABLE_PARAMS: return "unstable parameters (relaxation time or sigma/eps)";
+    case EHD_ERR_NOMEM: return "out of memory or workspace too small";
+    case EHD_ERR_NOT_CONVERGED: return "potential loop reached its iteration cap";
+    case EHD_ERR_NONFINITE: return "non-finite values in phi or q";
+    case EHD_ERR_BUSY: return "no free slot or memory";
+    case EHD_ERR_CUDA: return "CUDA runtime error";
+    default: return "unknown status";
+  }
+}
+
+int ehd_workspace_bytes(const ehd_params* params, size_t* bytes) {
+  if (!params || !bytes || !sizes_ok(params)) return EHD_ERR_INVALID_ARG;
+  *bytes = layout_for(*params).total;
+  return EHD_OK;
+}
+
+int ehd_create(const ehd_params* params, void* workspace, size_t workspace_bytes, void* stream,
+               ehd_sim** out) {
+  if (!out) return EHD_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int v = validate(params);
+  if (v != EHD_OK) return v;
+  const int64_t N = (int64_t)params->nx * params->ny;
+  const Layout L = layout_for(*params);
+  ehd_sim* s = new (std::nothrow) ehd_sim();
+  if (!s) return EHD_ERR_NOMEM;
+  s->P = *params;
+  s->kp = make_kparams(*params);
+  s->stream = static_cast<cudaStream_t>(stream);
+  s->n = params->start_step;
+  if (workspace) {
+    if (workspace_bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) & 255u)) {
+      delete s;
+      return workspace_bytes < L.total ? EHD_ERR_NOMEM : EHD_ERR_INVALID_ARG;
+    }
+    s->ws = workspace;
+    s->own_ws = false;
+  } else {
+    if (cudaMalloc(&s->ws, L.total) != cudaSuccess) {
+      cudaGetLastError();
+      delete s;
+      return EHD_ERR_NOMEM;
+    }
+    s->own_ws = true;
+  }
+  s->ws_bytes = L.total;
+  char* base = static_cast<char*>(s->ws);
+  s->b.ss = reinterpret_cast<StepState*>(base + L.ss);
+  s->b.pops = reinterpret_cast<float*>(base + L.pops);
+  s->b.h = reinterpret_cast<float*>(base + L.h);
+  s->b.hist = reinterpret_cast<float*>(base + L.hist);
+  s->b.phi = reinterpret_cast<float*>(base + L.phi);
+  s->b.aq = reinterpret_cast<float2*>(base + L.aq);
+  s->b.io = reinterpret_cast<float*>(base + L.io);
+  s->b.tmp = reinterpret_cast<float*>(base + L.tmp);
+  s->b.partials = reinterpret_cast<double2*>(base + L.partials);
+  s->b.ctl = reinterpret_cast<Ctl*>(base + L.ctl);
+  s->b.stats = reinterpret_cast<DevStats*>(base + L.stats);
+  s->b.exports = reinterpret_cast<float*>(base + L.exports);
+  s->b.rpartials = reinterpret_cast<double2*>(base + L.rpartials);
+  // resident potential loop: needs cooperative launch, one tile per SM on this device,
+  // and an export area within the reserved space
+  {
+    int dev = 0, sms = 0, coop = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess &&
+        coop && L.export_floats && params->poisson_loop != EHD_LOOP_STREAM) {
+      const int use_sms = sms < DESIGN_SMS ? sms : DESIGN_SMS;
+      ResidentGeom g;
+      int th;
+      size_t sm;
+      if (resident_geometry(s->kp, use_sms, &g, &th, &sm) &&
+          2 * (size_t)g.ntx * g.nty * 8 * g.pmax <= L.export_floats &&
+          (size_t)g.ntx * g.nty <= (size_t)DESIGN_SMS &&
+          cudaFuncSetAttribute(resident_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sm) == cudaSuccess) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_kernel(), th, sm) ==
+                cudaSuccess &&
+            per_sm >= 1 && (long long)g.ntx * g.nty <= (long long)per_sm * sms) {
+          s->resident_ok = true;
+          s->rg = g;
+          s->rthreads = th;
+          s->rsmem = sm;
+        }
+      }
+    }
+    cudaGetLastError();
+    if (params->poisson_loop == EHD_LOOP_RESIDENT && !s->resident_ok) {
+      ehd_destroy(s);
+      return EHD_ERR_INVALID_ARG;  // the lattice does not fit on chip on this device
+    }
+  }
+  if (cudaMallocHost(&s->h_ctl, sizeof(Ctl)) != cudaSuccess ||
+      cudaMallocHost(&s->h_stats, sizeof(DevStats)) != cudaSuccess ||
+      cudaMallocHost(&s->h_stage, sizeof(float) * NIO * (size_t)N) != cudaSuccess) {
+    cudaGetLastError();
+    ehd_destroy(s);
+    return EHD_ERR_NOMEM;
+  }
+  // zero everything once: populations, control, tickets
+  if (cudaMemsetAsync(s->ws, 0, L.total, s->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess) {
+    ehd_destroy(s);
+    return EHD_ERR_CUDA;
+  }
+  *out = s;
+  return EHD_OK;
+}
+
+int ehd_profile(ehd_sim* s, int enable) {
+  if (!s) return EHD_ERR_INVALID_ARG;
+  if (prof_flush(s) != EHD_OK) return EHD_ERR_CUDA;
+  s->profiling = enable != 0;
+  for (int j = 0; j < 4; ++j) {
+    s->prof_ms[j] = 0.0;
+    s->prof_n[j] = 0;
+  }
+  return EHD_OK;
+}
+
+int ehd_profile_read(ehd_sim* s, ehd_kernel_times* out) {
+  if (!s || !out) return EHD_ERR_INVALID_ARG;
+  if (prof_flush(s) != EHD_OK) return EHD_ERR_CUDA;
+  for (int j = 0; j < 4; ++j) {
+    out->ms[j] = s->prof_ms[j];
+    out->launches[j] = s->prof_n[j];
+  }
+  return EHD_OK;
+}
+
+void ehd_destroy(ehd_sim* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->stream);
+  destroy_graphs(s);
+  for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+  if (s->own_ws && s->ws) cudaFree(s->ws);
+  if (s->h_ctl) cudaFreeHost(s->h_ctl);
+  if (s->h_stats) cudaFreeHost(s->h_stats);
+  if (s->h_stage) cudaFreeHost(s->h_stage);
+  delete s;
+}
+
+int ehd_solve_potential(ehd_sim* s, double tol, int max_iter, int* iters, double* rel_change) {
+  if (!s) return EHD_ERR_INVALID_ARG;
+  const ehd_params& P = s->P;
+  const double t = tol > 0 ? tol : P.poisson_tol;
+  const int mx = max_iter > 0 ? max_iter : P.poisson_max_iter;
+  const int fixed = (tol > 0 || max_iter > 0) ? 0 : P.poisson_fixed_iter;
+  EHD_LAUNCH(s, 0, launch_moments(s->kp, s->b, s->cur, t, P.poisson_min_iter, mx, fixed,
+                                   s->stream));
+  int st = run_potential_loop(s, fixed, mx);
+  if (st == EHD_ERR_CUDA) return st;
+  EHD_CUDA(cudaMemcpyAsync(s->h_ctl, s->b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
+  EHD_CUDA(cudaStreamSynchronize(s->stream));
+  if (iters) *iters = s->h_ctl->iter;
+  if (rel_change) *rel_change = s->h_ctl->rel;
+  if (s->h_ctl->nonfinite) return EHD_ERR_NONFINITE;
+  return s->h_ctl->converged ? EHD_OK : EHD_ERR_NOT_CONVERGED;
+}
+
+int ehd_set_fields(ehd_sim* s, const void* phi, const void* q, const void* ux, const void* uy,
+                   const void* p, int mem) {
+  if (!s || !phi || !q || !ux || !uy || (mem != EHD_HOST && mem != EHD_DEVICE))
+    return EHD_ERR_INVALID_ARG;
+  int st;
+  if ((st = stage_in(s, phi, 0, mem)) != EHD_OK) return st;
+  if ((st = stage_in(s, q, 1, mem)) != EHD_OK) return st;
+  if ((st = stage_in(s, ux, 2, mem)) != EHD_OK) return st;
+  if ((st = stage_in(s, uy, 3, mem)) != EHD_OK) return st;
+  if (p && (st = stage_in(s, p, 4, mem)) != EHD_OK) return st;
+  s->n = s->P.start_step;
+  s->history_valid = false;
+  s->cur = 0;
+  // the potential distribution restarts in copy 0
+  EHD_CUDA(cudaMemsetAsync(&s->b.ctl->parity, 0, sizeof(int), s->stream));
+  EHD_CUDA(cudaMemsetAsync(&s->b.ctl->nonfinite, 0, sizeof(int), s->stream));
+  s->launches += 1;
+  EHD_CUDA(launch_step_set(s->kp, s->b, s->cur, s->n, 1, s->stream));
+  EHD_LAUNCH(s, 0, launch_init(s->kp, s->b, s->cur, p != nullptr, s->stream));
+  s->last_k = 1;
+  return ehd_solve_potential(s, 0.0, 0, nullptr, nullptr);
+}
+
+static int fill_stats(ehd_sim* s, ehd_stats* out) {
+  EHD_CUDA(cudaMemcpyAsync(s->h_stats, s->b.stats, sizeof(DevStats), cudaMemcpyDeviceToHost,
+                           s->stream));
+  EHD_CUDA(cudaStreamSynchronize(s->stream));
+  const DevStats& d = *s->h_stats;
+  out->step = s->n;
+  out->steps = d.steps;
+  out->poisson_iters_total = d.iters_total;
+  out->poisson_iters_min = d.steps ? d.iters_min : 0;
+  out->poisson_iters_max = d.iters_max;
+  out->not_converged_steps = d.not_converged;
+  out->nonfinite = d.nonfinite;
+  out->last_rel_change = d.last_rel;
+  out->sum_phi = d.sum_phi;
+  out->sum_q = d.sum_q;
+  // host-driven launches are counted as they are queued; a graph step launches moments,
+  // the potential loop (one resident kernel, or one kernel per sub-iteration) and coupled
+  out->kernel_launches = s->launches + 2LL * s->graph_steps;
+  if (s->resident_ok)
+    out->kernel_launches += s->graph_steps;
+  else
+    out->kernel_launches += (int64_t)d.iters_total - s->host_iters;
+  int status = EHD_OK;
+  if (d.not_converged) status = EHD_ERR_NOT_CONVERGED;
+  if (d.nonfinite) status = EHD_ERR_NONFINITE;
+  if (d.barrier_error) status = EHD_ERR_CUDA;
+  return status;
+}
+
+static int reset_stats(ehd_sim* s) {
+  s->launches = 1;
+  s->graph_steps = 0;
+  s->host_iters = 0;
+  EHD_CUDA(launch_stats_reset(s->b, s->stream));
+  return EHD_OK;
+}
+
+int ehd_step(ehd_sim* s, int nsteps, ehd_stats* out) {
+  if (!s || nsteps < 0) return EHD_ERR_INVALID_ARG;
+  const ehd_params& P = s->P;
+  int status = EHD_OK;
+  if (out || !s->stats_live) {
+    if (reset_stats(s) != EHD_OK) return EHD_ERR_CUDA;
+    s->stats_live = true;
+  }
+  if (!s->profiling) ensure_graphs(s);
+  const bool use_graphs = s->graphs_ok && !s->profiling;
+  for (int k = 0; k < nsteps; ++k) {
+    if (use_graphs) {
+      // the whole step, potential loop included, without returning to the host
+      EHD_CUDA(cudaGraphLaunch(s->exec[s->cur], s->stream));
+      s->graph_steps += 1;
+    } else {
+      EHD_LAUNCH(s, 0, launch_moments(s->kp, s->b, s->cur, P.poisson_tol, P.poisson_min_iter,
+                                       P.poisson_max_iter, P.poisson_fixed_iter, s->stream));
+      const int st = run_potential_loop(s, P.poisson_fixed_iter, P.poisson_max_iter);
+      if (st == EHD_ERR_CUDA) return st;
+      if (st != EHD_OK) status = st;
+      if (!s->resident_ok) s->host_iters += s->h_ctl->iter;
+      EHD_LAUNCH(s, 3, launch_coupled(s->kp, s->b, s->cur, s->stream));
+    }
+    s->cur ^= 1;
+    s->n += 1;
+    s->history_valid = true;
+  }
+  if (out) {
+    const int st = fill_stats(s, out);
+    s->stats_live = false;
+    if (st != EHD_OK && status == EHD_OK) status = st;
+    if (st == EHD_ERR_NONFINITE || st == EHD_ERR_CUDA) status = st;
+  }
+  return status;
+}
+
+int ehd_loop_kind(const ehd_sim* s) {
+  if (!s) return -1;
+  return s->resident_ok ? EHD_LOOP_RESIDENT : EHD_LOOP_STREAM;
+}
+
+int ehd_read_stats(ehd_sim* s, ehd_stats* out) {
+  if (!s || !out) return EHD_ERR_INVALID_ARG;
+  if (!s->stats_live) {
+    std::memset(out, 0, sizeof(*out));
+    out->step = s->n;
+    return EHD_OK;
+  }
+  const int st = fill_stats(s, out);
+  s->stats_live = false;
+  return st;
+}
+
+int ehd_read_fields(ehd_sim* s, unsigned mask, void* const* out, int mem) {
+  if (!s || !out || (mem != EHD_HOST && mem != EHD_DEVICE) || (mask & ~0xffu)) return EHD_ERR_INVALID_ARG;
+  if (!mask) return EHD_OK;
+  int nf = 0;
+  for (int b = 0; b < EHD_NUM_FIELDS; ++b)
+    if (mask & (1u << b)) {
+      if (!out[nf]) return EHD_ERR_INVALID_ARG;
+      ++nf;
+    }
+  EHD_CUDA(launch_fields(s->kp, s->b, s->cur, mask, s->stream));
+  const size_t N = (size_t)s->kp.N;
+  for (int j = 0; j < nf; ++j) {
+    if (mem == EHD_DEVICE) {
+      EHD_CUDA(cudaMemcpyAsync(out[j], s->b.io + j * N, N * sizeof(float),
+                               cudaMemcpyDeviceToDevice, s->stream));
+    } else {
+      EHD_CUDA(cudaMemcpyAsync(s->h_stage + j * N, s->b.io + j * N, N * sizeof(float),
+                               cudaMemcpyDeviceToHost, s->stream));
+    }
+  }
+  EHD_CUDA(cudaStreamSynchronize(s->stream));
+  if (mem == EHD_HOST) {
+    for (int j = 0; j < nf; ++j) {
+      double* d = static_cast<double*>(out[j]);
+      const float* f = s->h_stage + j * N;
+      for (size_t i = 0; i < N; ++i) d[i] = (double)f[i];
+    }
+  }
+  return EHD_OK;
+}
+
+// State blob: header, then populations (27 N), potential populations (8 N), lagged
+// quantities (6 N) and the phi of the last potential solve (N), all float32.
+struct StateHeader {
+  uint64_t magic;
+  int32_t nx, ny;
+  int64_t n;
+  int32_t history_valid, last_k;
+};
+
+int ehd_state_bytes(const ehd_sim* s, size_t* bytes) {
+  if (!s || !bytes) return EHD_ERR_INVALID_ARG;
+  *bytes = sizeof(StateHeader) + sizeof(float) * (size_t)s->kp.N * (NPOP + NH + NHIST + 1);
+  return EHD_OK;
+}
+
+int ehd_save_state(ehd_sim* s, void* buf, size_t bytes) {
+  size_t need;
+  if (!s || !buf || ehd_state_bytes(s, &need) != EHD_OK || bytes < need)
+    return EHD_ERR_INVALID_ARG;
+  const size_t N = (size_t)s->kp.N;
+  EHD_CUDA(cudaMemcpyAsync(s->h_ctl, s->b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
+  EHD_CUDA(cudaStreamSynchronize(s->stream));
+  StateHeader hd{STATE_MAGIC, s->P.nx, s->P.ny, s->n, s->history_valid ? 1 : 0, s->last_k};
+  char* p = static_cast<char*>(buf);
+  std::memcpy(p, &hd, sizeof(hd));
+  p += sizeof(hd);
+  const float* pops = s->b.pops + (size_t)s->cur * NPOP * N;
+  const float* h = s->b.h + (size_t)s->h_ctl->parity * NH * N;
+  EHD_CUDA(cudaMemcpyAsync(p, pops, sizeof(float) * NPOP * N, cudaMemcpyDeviceToHost, s->stream));
+  p += sizeof(float) * NPOP * N;
+  EHD_CUDA(cudaMemcpyAsync(p, h, sizeof(float) * NH * N, cudaMemcpyDeviceToHost, s->stream));
+  p += sizeof(float) * NH * N;
+  EHD_CUDA(cudaMemcpyAsync(p, s->b.hist, sizeof(float) * NHIST * N, cudaMemcpyDeviceToHost,
+                           s->stream));
+  p += sizeof(float) * NHIST * N;
+  EHD_CUDA(cudaMemcpyAsync(p, s->b.phi, sizeof(float) * N, cudaMemcpyDeviceToHost, s->stream));
+  EHD_CUDA(cudaStreamSynchronize(s->stream));
+  return EHD_OK;
+}
+
+int ehd_load_state(ehd_sim* s, const void* buf, size_t bytes) {
+  size_t need;
+  if (!s || !buf || ehd_state_bytes(s, &need) != EHD_OK || bytes < need)
+    return EHD_ERR_INVALID_ARG;
+  StateHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (hd.magic != STATE_MAGIC || hd.nx != s->P.nx || hd.ny != s->P.ny) return EHD_ERR_INVALID_ARG;
+  const size_t N = (size_t)s->kp.N;
+  const char* p = static_cast<const char*>(buf) + sizeof(hd);
+  s->cur = 0;
+  EHD_CUDA(cudaMemcpyAsync(s->b.pops, p, sizeof(float) * NPOP * N, cudaMemcpyHostToDevice,
+                           s->stream));
+  p += sizeof(float) * NPOP * N;
+  EHD_CUDA(cudaMemcpyAsync(s->b.h, p, sizeof(float) * NH * N, cudaMemcpyHostToDevice, s->stream));
+  p += sizeof(float) * NH * N;
+  EHD_CUDA(cudaMemcpyAsync(s->b.hist, p, sizeof(float) * NHIST * N, cudaMemcpyHostToDevice,
+                           s->stream));
+  p += sizeof(float) * NHIST * N;
+  EHD_CUDA(cudaMemcpyAsync(s->b.phi, p, sizeof(float) * N, cudaMemcpyHostToDevice, s->stream));
+  EHD_CUDA(cudaMemsetAsync(&s->b.ctl->parity, 0, sizeof(int), s->stream));
+  s->n = hd.n;
+  s->history_valid = hd.history_valid != 0;
+  s->last_k = hd.last_k;
+  EHD_CUDA(launch_step_set(s->kp, s->b, 0, s->n, s->history_valid ? 0 : 1, s->stream));
+  EHD_CUDA(cudaStreamSynchronize(s->stream));
+  return EHD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,216 @@
+// Internal definitions shared by the CUDA kernels and the host side of the library.
+//
+// Lattice: D2Q9 (Sec. 3, Eq. weq37).  Direction i = 0 rest; 1..4 axis directions
+// (1,0), (0,1), (-1,0), (0,-1); 5..8 diagonals (1,1), (-1,1), (-1,-1), (1,-1).
+// Weights 4/9, 1/9, 1/36; c_s^2 = 1/3.
+//
+// Device layout of one simulation (N = nx * ny nodes, x fastest):
+//   pops[2][27][N]  post-stream populations g (0..8), l (9..17), f (18..26), two copies
+//                   used alternately (ping-pong);
+//   h[2][8][N]      post-stream potential populations h_1..h_8, two copies.  h_0 is not
+//                   stored: it never enters varphi (Eq. weq55), grad varphi (Eq. eqA.16)
+//                   or any other population, so it cannot influence any result;
+//   hist[6][N]      lagged quantities s = u.grad phi, J = q u (x, y), R, F (x, y);
+//   phi[N]          phi of the current step (input of the stencils and of the
+//                   potential coefficient);
+//   aq[N]           float2 per node: (a, q) with a = eps_hat / (c_s^2 tau_h (eps_hat +
+//                   c_s^2 tau_h)), the coefficient of the potential forcing once
+//                   grad varphi is written with the local first moment (Eq. eqA.16);
+//   io[8][N]        staging area for field input / output;
+//   partials[]      per-CTA FP64 partial sums;
+//   ctl, stats      loop control and statistics (device structs below).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ehd {
+
+constexpr int Q9 = 9;
+constexpr int NPOP = 27;   // g, l, f
+constexpr int NH = 8;      // h_1..h_8
+constexpr int NHIST = 6;
+constexpr int NIO = 8;
+constexpr int MAX_PARTIALS = 1 << 16;
+
+__host__ __device__ constexpr int cx(int i) {
+  return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int i) {
+  return i == 2 || i == 5 || i == 6 ? 1 : (i == 4 || i == 7 || i == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i) {
+  return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5);
+}
+__host__ __device__ constexpr float wgt(int i) {
+  return i == 0 ? 4.0f / 9.0f : (i <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+// CH source shape factor -1 + (|c_i|^2 - 2 c_s^2) / (2 c_s^2) of Eq. weq47:
+// -2 (rest), -1/2 (axis), +1 (diagonal).
+__host__ __device__ constexpr float ch_k(int i) {
+  return i == 0 ? -2.0f : (i <= 4 ? -0.5f : 1.0f);
+}
+
+// Coefficients of one simulation, single precision, computed on the host from the
+// double-precision parameters.
+struct KParams {
+  int nx, ny, N, walls;
+  int neutralize;
+  float rho_v, drho;        // rho = rho_v + drho phi
+  float mu_v, dmu;          // mu = mu_v + dmu phi
+  float sig_v, dsig;        // sigma = sig_v + dsig phi
+  float eps_v, deps;        // eps_hat = phi^2 (2 phi - 3) deps, deps = eps_v - eps_l
+  float beta4;              // 4 beta
+  float kappa;
+  float wet_a;              // sqrt(2 beta / kappa) = 4 / W
+  float omega_g;            // 1 / tau_g
+  float omega_l;            // 1 / tau_l
+  float pref_l;             // 1 - 1 / (2 tau_l)
+  float omega_h;            // 1 / tau_h
+  float cs2tauh;            // c_s^2 tau_h
+  float gbx, gby;           // body acceleration
+  // ramped wall values (double: evaluated once per step by one thread)
+  double cos_yb, cos_yt;    // cosines of the Young angles
+  double ew_signed;         // ew_sign * eta/d of the bottom wall
+  double varphi_b, varphi_t;
+  int ramp_steps;
+};
+
+// Values that change from step to step, kept on the device so that a step needs no
+// host input: written for the next step by the coupled kernel (one thread), for the
+// first step by k_step_set.  Two slots, indexed like the population copies.
+struct StepState {
+  long long n;              // step index
+  int first;                // 1: no history yet, backward differences are zero
+  int pad;
+  float cos_b, cos_t;       // effective contact-angle cosines of the bottom / top walls
+  float vw_b, vw_t;         // wall potentials
+};
+
+// Ramp fraction r = min(1, n / ramp_steps); wall potentials r varphi_w; the bottom
+// wall's electrowetting term scales with r^2 (Eq. weq69: eta/d is quadratic in the
+// voltage); cosines clamped to [-1, 1].  Explicit roundings keep it free of fused
+// multiply-adds.
+__device__ __forceinline__ StepState make_step(const KParams& k, long long n, int first) {
+  StepState s;
+  double r = 1.0;
+  if (k.ramp_steps > 0) {
+    r = __ddiv_rn((double)n, (double)k.ramp_steps);
+    r = r < 1.0 ? r : 1.0;
+  }
+  double cb = __dadd_rn(k.cos_yb, __dmul_rn(__dmul_rn(k.ew_signed, r), r));
+  double ct = k.cos_yt;
+  cb = cb < -1.0 ? -1.0 : (cb > 1.0 ? 1.0 : cb);
+  ct = ct < -1.0 ? -1.0 : (ct > 1.0 ? 1.0 : ct);
+  s.n = n;
+  s.first = first;
+  s.pad = 0;
+  s.cos_b = (float)cb;
+  s.cos_t = (float)ct;
+  s.vw_b = (float)__dmul_rn(r, k.varphi_b);
+  s.vw_t = (float)__dmul_rn(r, k.varphi_t);
+  return s;
+}
+
+// Potential loop control; written by the reduction of the moments kernel (reset) and of
+// the potential kernel (advance), read at the start of each potential launch.
+struct Ctl {
+  int iter;                 // sub-iterations made in the current solve
+  int done;                 // loop finished: later potential launches do nothing
+  int converged;            // finished by the stopping rule (or a fixed count)
+  int parity;               // which h copy holds the current state
+  double rel;               // relative change of the last sub-iteration
+  double tol;
+  int min_iter, max_iter, fixed_iter;
+  int nonfinite;            // phi or q held NaN / Inf
+  double sum_phi, sum_q;    // FP64 sums of phi and q of the last moments pass
+  float mean_q;             // sum_q / N (source shift when neutralising)
+  unsigned ticket_m;        // CTA arrival counters of the two reductions
+  unsigned ticket_p;
+  float vw_b, vw_t;         // wall potentials of the current solve
+  unsigned bar_count;       // grid barrier of the resident potential loop
+  unsigned bar_gen;
+  int bar_error;            // a barrier wait timed out (sticky)
+  int pad2;
+};
+
+// Tiling of the resident potential loop: ntx x nty tiles of TX x TY nodes (the last
+// column / row may be smaller), pmax perimeter slots per tile.
+struct ResidentGeom {
+  int TX, TY, ntx, nty, pmax;
+};
+
+struct DevStats {
+  int iters_total, iters_min, iters_max, not_converged, nonfinite, steps;
+  int barrier_error, pad;
+  double last_rel, sum_phi, sum_q;
+};
+
+// Property laws (Remark II, Eq. weq36).
+__device__ __forceinline__ float eps_hat_of(const KParams& k, float phi) {
+  return phi * phi * (2.0f * phi - 3.0f) * k.deps;
+}
+__device__ __forceinline__ float deps_of(const KParams& k, float phi) {
+  return 6.0f * phi * (phi - 1.0f) * k.deps;
+}
+
+__device__ __forceinline__ int wrap(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_cg(const T* p) { return __ldcg(p); }
+
+}  // namespace ehd
+
+// Launch functions implemented in the .cu files (host side).
+namespace ehd {
+struct Buffers {
+  StepState* ss;     // [2]
+  float* pops;       // [2][27][N]
+  float* h;          // [2][8][N]
+  float* hist;       // [6][N]
+  float* phi;        // [N]
+  float2* aq;        // [N]
+  float* io;         // [8][N]
+  float* tmp;        // [N]
+  double2* partials; // [MAX_PARTIALS]
+  Ctl* ctl;
+  DevStats* stats;
+  float* exports;    // resident loop: [2][tiles][8][pmax]
+  double2* rpartials;// resident loop: [2][tiles]
+};
+
+// Resident potential loop (poisson_resident.cu).
+bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* threads,
+                       size_t* smem);
+const void* resident_kernel();
+cudaError_t launch_poisson_resident(const KParams& kp, const ResidentGeom& g, int threads,
+                                    size_t smem, const Buffers& b, cudaStream_t st);
+cudaError_t add_poisson_resident_node(cudaGraph_t graph, const cudaGraphNode_t* deps, size_t nd,
+                                      cudaGraphNode_t* out, const KParams& kp,
+                                      const ResidentGeom& g, int threads, size_t smem,
+                                      const Buffers& b);
+
+cudaError_t launch_step_set(const KParams& kp, const Buffers& b, int slot, long long n,
+                            int first, cudaStream_t st);
+cudaError_t launch_init(const KParams& kp, const Buffers& b, int cur, bool have_p,
+                        cudaStream_t st);
+cudaError_t launch_moments(const KParams& kp, const Buffers& b, int cur, double tol,
+                           int min_iter, int max_iter, int fixed_iter, cudaStream_t st);
+cudaError_t launch_poisson(const KParams& kp, const Buffers& b, cudaStream_t st);
+cudaError_t launch_coupled(const KParams& kp, const Buffers& b, int cur, cudaStream_t st);
+cudaError_t launch_stats_reset(const Buffers& b, cudaStream_t st);
+cudaError_t launch_fields(const KParams& kp, const Buffers& b, int cur, unsigned mask,
+                          cudaStream_t st);
+
+// Graph of one time step for population copy `cur`: moments -> while(loop not done)
+// { potential sub-iteration } -> coupled pass.  All arguments live on the device, so the
+// graph is launched unchanged every step.
+// With `rg` non-null the potential loop is the single resident cooperative kernel instead
+// of the WHILE node.
+cudaError_t build_step_graph(const KParams& kp, const Buffers& b, int cur, double tol,
+                             int min_iter, int max_iter, int fixed_iter, const ResidentGeom* rg,
+                             int rthreads, size_t rsmem, cudaGraph_t* out);
+}  // namespace ehd

@@ -1,0 +1,611 @@
+// Kernels of the coupled step other than the potential sub-iteration:
+//   k_init      equilibrium initialisation (Algorithm 1 step 1)
+//   k_moments   phi, q and the potential coefficients of the current step, FP64 sums
+//   k_coupled   one fused collide-and-push of the g, l and f populations (Algorithm 1
+//               steps 2, 4, 5 with the field of step 3), history update
+//   k_fields    macroscopic fields for output
+#include "ehd_internal.cuh"
+
+namespace ehd {
+
+namespace {
+
+
+// phi at the 3x3 neighbourhood of (x, y); rows outside a wall are ghost values from the
+// wetting rule n_w.grad(phi) = -sqrt(2 beta/kappa) cos(theta) (phi - phi^2) (Eq. weq68):
+// ghost = phi_wall_row + a cos(theta) phi (1 - phi) with the first fluid row's value.
+struct Stencil {
+  float c, e, w, n, s, ne, nw, se, sw;
+};
+
+__device__ __forceinline__ float ghost(float v, float a_cos) { return v + a_cos * (v - v * v); }
+
+__device__ __forceinline__ Stencil load_stencil(const KParams& k, const StepState& sa,
+                                                const float* __restrict__ phi, int x, int y) {
+  const int nx = k.nx, ny = k.ny;
+  const int xm = x == 0 ? nx - 1 : x - 1;
+  const int xp = x + 1 == nx ? 0 : x + 1;
+  Stencil s;
+  const float* row = phi + (size_t)y * nx;
+  s.c = __ldg(row + x);
+  s.e = __ldg(row + xp);
+  s.w = __ldg(row + xm);
+  if (k.walls && y + 1 == ny) {
+    const float a = k.wet_a * sa.cos_t;
+    s.n = ghost(s.c, a);
+    s.ne = ghost(s.e, a);
+    s.nw = ghost(s.w, a);
+  } else {
+    const float* r = phi + (size_t)(y + 1 == ny ? 0 : y + 1) * nx;
+    s.n = __ldg(r + x);
+    s.ne = __ldg(r + xp);
+    s.nw = __ldg(r + xm);
+  }
+  if (k.walls && y == 0) {
+    const float a = k.wet_a * sa.cos_b;
+    s.s = ghost(s.c, a);
+    s.se = ghost(s.e, a);
+    s.sw = ghost(s.w, a);
+  } else {
+    const float* r = phi + (size_t)(y == 0 ? ny - 1 : y - 1) * nx;
+    s.s = __ldg(r + x);
+    s.se = __ldg(r + xp);
+    s.sw = __ldg(r + xm);
+  }
+  return s;
+}
+
+// Isotropic stencils of Sec. 3.2 with w_i / c_s^2 = 1/3 (axis), 1/12 (diagonal).
+__device__ __forceinline__ void grad_lap(const Stencil& s, float& gx, float& gy, float& lap) {
+  gx = (s.e - s.w) * (1.0f / 3.0f) + (s.ne + s.se - s.nw - s.sw) * (1.0f / 12.0f);
+  gy = (s.n - s.s) * (1.0f / 3.0f) + (s.ne + s.nw - s.se - s.sw) * (1.0f / 12.0f);
+  lap = (s.e + s.w + s.n + s.s) * (2.0f / 3.0f) + (s.ne + s.nw + s.se + s.sw) * (1.0f / 6.0f) -
+        s.c * (10.0f / 3.0f);
+}
+
+// Index of the node a population leaving (x, y) in direction i lands on, and the
+// direction it lands in: periodic in x; at a wall, half-way bounce-back returns it to
+// (x, y) in the opposite direction.
+__device__ __forceinline__ int push_target(const KParams& k, int x, int y, int i, int& dir) {
+  int ty = y + cy(i);
+  dir = i;
+  if (k.walls) {
+    if (ty < 0 || ty >= k.ny) {
+      dir = opp(i);
+      return y * k.nx + x;
+    }
+  } else {
+    ty = ty < 0 ? k.ny - 1 : (ty >= k.ny ? 0 : ty);
+  }
+  int tx = x + cx(i);
+  tx = tx < 0 ? k.nx - 1 : (tx >= k.nx ? 0 : tx);
+  return ty * k.nx + tx;
+}
+
+// FP32 warp sum.
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+// Initialisation: populations at equilibrium (Eqs. weq40, weq46, weq54, weq61).
+// ------------------------------------------------------------------------------------
+__global__ void k_init(KParams k, const StepState* __restrict__ ss, const float* __restrict__ in,
+                       int have_p, float* __restrict__ pops, float* __restrict__ h,
+                       float* __restrict__ hist) {
+  const int N = k.N;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N) return;
+  const StepState sa = *ss;
+  const int y = idx / k.nx, x = idx - y * k.nx;
+  const float* phi0 = in;
+  const float q = __ldg(in + N + idx);
+  const float ux = __ldg(in + 2 * N + idx);
+  const float uy = __ldg(in + 3 * N + idx);
+  const float p = have_p ? __ldg(in + 4 * N + idx) : 0.0f;
+  Stencil s = load_stencil(k, sa, phi0, x, y);
+  float gx, gy, lap;
+  grad_lap(s, gx, gy, lap);
+  const float phi = s.c;
+  // hbar without the field term (E = 0 at initialisation)
+  const float mu = k.beta4 * phi * (phi - 0.5f) * (phi - 1.0f) - k.kappa * lap;
+  const float rho = k.rho_v + k.drho * phi;
+  const float uu = ux * ux + uy * uy;
+  float* g = pops;
+  float* l = pops + 9 * (size_t)N;
+  float* f = pops + 18 * (size_t)N;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const float cu = cx(i) * ux + cy(i) * uy;
+    const float si = wgt(i) * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
+    g[i * (size_t)N + idx] = i == 0 ? phi - (1.0f - wgt(0)) * mu : wgt(i) * mu;
+    l[i * (size_t)N + idx] = wgt(i) * q * (1.0f + 3.0f * cu);
+    f[i * (size_t)N + idx] = (i == 0 ? (wgt(0) - 1.0f) : wgt(i)) * 3.0f * p + rho * si;
+  }
+  // potential at equilibrium with the linear wall interpolation (0 when periodic)
+  float vlin = 0.0f;
+  if (k.walls) vlin = sa.vw_b + (sa.vw_t - sa.vw_b) * ((y + 0.5f) / (float)k.ny);
+#pragma unroll
+  for (int i = 1; i < 9; ++i) h[(i - 1) * (size_t)N + idx] = wgt(i) * vlin;
+#pragma unroll
+  for (int j = 0; j < NHIST; ++j) hist[j * (size_t)N + idx] = 0.0f;
+}
+
+// Step values for step n (ramps, first-step flag) into one slot.
+__global__ void k_step_set(KParams k, StepState* ss, long long n, int first) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *ss = make_step(k, n, first);
+}
+
+// ------------------------------------------------------------------------------------
+// Moments of the current step (a1): phi = sum g (Eq. weq49), q = sum l + R^{n-1}/2
+// (Eq. weq62 with the lagged R of Algorithm 1).  Writes phi and the per-node potential
+// coefficients; FP64 sums of phi and q; the last CTA resets the potential loop.
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_moments(KParams k, const StepState* __restrict__ ss,
+                                                 const float* __restrict__ pops,
+                                                 const float* __restrict__ hist,
+                                                 float* __restrict__ phi_out,
+                                                 float2* __restrict__ aq,
+                                                 double2* __restrict__ partials, Ctl* ctl,
+                                                 double tol, int min_iter, int max_iter,
+                                                 int fixed_iter) {
+  const int N = k.N;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  float phi = 0.0f, q = 0.0f;
+  int bad = 0;
+  if (idx < N) {
+    const float* g = pops;
+    const float* l = pops + 9 * (size_t)N;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      phi += __ldg(g + i * (size_t)N + idx);
+      q += __ldg(l + i * (size_t)N + idx);
+    }
+    q += 0.5f * __ldg(hist + 3 * (size_t)N + idx);
+    const float eh = eps_hat_of(k, phi);
+    const float den = eh + k.cs2tauh;
+    const float a = eh / (k.cs2tauh * den);
+    phi_out[idx] = phi;
+    aq[idx] = make_float2(a, q);
+    bad = !(isfinite(phi) && isfinite(q));
+  }
+  // FP32 within a warp, FP64 across warps and CTAs
+  __shared__ double s_sum[8][2];
+  __shared__ int s_last;
+  const float wp = warp_sum(phi), wq = warp_sum(q);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_sum[warp][0] = (double)wp;
+    s_sum[warp][1] = (double)wq;
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&ctl->nonfinite, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += s_sum[w][0];
+      b += s_sum[w][1];
+    }
+    partials[blockIdx.x] = make_double2(a, b);
+    __threadfence();
+    const unsigned t = atomicAdd(&ctl->ticket_m, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // last CTA: fixed-order FP64 reduction of the per-CTA partials
+  __shared__ double s_red[256][2];
+  double a = 0.0, b = 0.0;
+  for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x) {
+    const double2 v = __ldcg(partials + j);
+    a += v.x;
+    b += v.y;
+  }
+  s_red[threadIdx.x][0] = a;
+  s_red[threadIdx.x][1] = b;
+  __syncthreads();
+  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      s_red[threadIdx.x][0] += s_red[threadIdx.x + o][0];
+      s_red[threadIdx.x][1] += s_red[threadIdx.x + o][1];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    ctl->sum_phi = s_red[0][0];
+    ctl->sum_q = s_red[0][1];
+    ctl->mean_q = (float)(s_red[0][1] / (double)N);
+    ctl->iter = 0;
+    ctl->done = 0;
+    ctl->converged = 0;
+    ctl->rel = 0.0;
+    ctl->tol = tol;
+    ctl->min_iter = min_iter;
+    ctl->max_iter = max_iter;
+    ctl->fixed_iter = fixed_iter;
+    ctl->vw_b = ss->vw_b;
+    ctl->vw_t = ss->vw_t;
+    ctl->ticket_m = 0u;
+    __threadfence();
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// The fused coupled pass (a1, a2, a4-a9): stencils on phi, field from the converged
+// potential populations, chemical potential, forces, charge source, then collision of
+// g (Eq. weq45), l (Eq. weq58) and f (Eq. weq38) and the push to the neighbours with
+// half-way bounce-back; history for the next step.
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_coupled(KParams k, StepState* ss, int cur,
+                                                 const float* __restrict__ pin,
+                                                 float* __restrict__ pout,
+                                                 const float* __restrict__ phi_f,
+                                                 const float* __restrict__ hbuf,
+                                                 float* __restrict__ hist, const Ctl* ctl,
+                                                 DevStats* stats) {
+  const int N = k.N;
+  const int parity = ld_cg(&ctl->parity);
+  const StepState sa = ss[cur];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // values of the next step, in the other slot (this step's slot is being read)
+    ss[cur ^ 1] = make_step(k, sa.n + 1, 0);
+    // the potential loop of this step has finished: record its statistics
+    const int it = ld_cg(&ctl->iter);
+    stats->iters_total += it;
+    stats->iters_min = min(stats->iters_min, it);
+    stats->iters_max = max(stats->iters_max, it);
+    stats->not_converged += ld_cg(&ctl->converged) ? 0 : 1;
+    stats->nonfinite |= ld_cg(&ctl->nonfinite);
+    stats->last_rel = ld_cg(&ctl->rel);
+    stats->sum_phi = ld_cg(&ctl->sum_phi);
+    stats->sum_q = ld_cg(&ctl->sum_q);
+    stats->barrier_error |= ld_cg(&ctl->bar_error);
+    stats->steps += 1;
+  }
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N) return;
+  const int y = idx / k.nx, x = idx - y * k.nx;
+  const float* hs = hbuf + (size_t)parity * NH * N;
+
+  // a2: stencils on phi
+  const Stencil st = load_stencil(k, sa, phi_f, x, y);
+  float gphx, gphy, lap;
+  grad_lap(st, gphx, gphy, lap);
+  const float phi = st.c;
+
+  // populations at this node (post-stream)
+  float g[9], l[9], f[9];
+  const float* gp = pin;
+  const float* lp = pin + 9 * (size_t)N;
+  const float* fp = pin + 18 * (size_t)N;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    g[i] = __ldg(gp + i * (size_t)N + idx);
+    l[i] = __ldg(lp + i * (size_t)N + idx);
+    f[i] = __ldg(fp + i * (size_t)N + idx);
+  }
+  float hv[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) hv[i] = __ldg(hs + i * (size_t)N + idx);
+  const float s_prev_in = hist[idx];
+  const float jx_prev_in = hist[(size_t)N + idx];
+  const float jy_prev_in = hist[2 * (size_t)N + idx];
+  const float R_prev = hist[3 * (size_t)N + idx];
+  const float Fx_prev = hist[4 * (size_t)N + idx];
+  const float Fy_prev = hist[5 * (size_t)N + idx];
+
+  // a1: moments and properties
+  float lsum = 0.0f, mx = 0.0f, my = 0.0f, fsum_nr = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    lsum += l[i];
+    mx += cx(i) * f[i];
+    my += cy(i) * f[i];
+    if (i) fsum_nr += f[i];
+  }
+  const float q = lsum + 0.5f * R_prev;
+  const float rho = k.rho_v + k.drho * phi;
+  const float inv_rho = 1.0f / rho;
+  const float ux = (mx + 0.5f * Fx_prev) * inv_rho;
+  const float uy = (my + 0.5f * Fy_prev) * inv_rho;
+
+  // a4: E = -grad(varphi) from the converged potential populations (Eq. eqA.16)
+  const float m1x = hv[0] - hv[2] + hv[4] - hv[5] - hv[6] + hv[7];
+  const float m1y = hv[1] - hv[3] + hv[4] + hv[5] - hv[6] - hv[7];
+  const float eh = eps_hat_of(k, phi);
+  const float inv_den = 1.0f / (eh + k.cs2tauh);
+  const float Ex = m1x * inv_den, Ey = m1y * inv_den;
+
+  // a5: chemical potential (Eq. weq31), force (Eq. weq30), charge source (Eq. weq57)
+  const float de = deps_of(k, phi);
+  const float mu = k.beta4 * phi * (phi - 0.5f) * (phi - 1.0f) - k.kappa * lap -
+                   0.5f * de * (Ex * Ex + Ey * Ey);
+  const float Fx = mu * gphx + q * Ex + rho * k.gbx;
+  const float Fy = mu * gphy + q * Ey + rho * k.gby;
+  const float eps = k.eps_v + eh;
+  const float sig = k.sig_v + k.dsig * phi;
+  const float gE = gphx * Ex + gphy * Ey;
+  const float R = (sig / eps) * (de * gE - q) - k.dsig * gE;
+
+  // a9 inputs: advection term and charge flux; zero backward differences at the start
+  const float s_adv = ux * gphx + uy * gphy;
+  const float Jx = q * ux, Jy = q * uy;
+  const float s_prev = sa.first ? s_adv : s_prev_in;
+  const float jx_prev = sa.first ? Jx : jx_prev_in;
+  const float jy_prev = sa.first ? Jy : jy_prev_in;
+
+  // pressure (Eq. eq32): c_s^2/(1 - w0) [sum_{i!=0} f + u.grad(rho)/2 + rho s_0(u)],
+  // s_0(u) = -w0 u.u / (2 c_s^2), grad rho = drho grad phi
+  const float uu = ux * ux + uy * uy;
+  const float p = 0.6f * (fsum_nr + 0.5f * k.drho * s_adv - (2.0f / 3.0f) * rho * uu);
+
+  // relaxation rates
+  const float mu_dyn = k.mu_v + k.dmu * phi;
+  const float tau_f = 0.5f + 3.0f * mu_dyn * inv_rho;
+  const float om_f = 1.0f / tau_f;
+  const float pref_f = 1.0f - 0.5f * om_f;
+  const float om_g = k.omega_g, om_l = k.omega_l, pref_l = k.pref_l;
+
+  // CH source: G_i + (G_i - G_i^{n-1})/2 = w_i k_i (3 s - s_prev)/2
+  const float gsrc = 1.5f * s_adv - 0.5f * s_prev;
+  const float djx = 3.0f * (Jx - jx_prev), djy = 3.0f * (Jy - jy_prev);
+  const float grx = k.drho * gphx, gry = k.drho * gphy;
+
+  float* go = pout;
+  float* lo = pout + 9 * (size_t)N;
+  float* fo = pout + 18 * (size_t)N;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const float w = wgt(i);
+    const float cu = cx(i) * ux + cy(i) * uy;
+    // a6: Cahn-Hilliard, g_eq of Eq. weq46
+    const float geq = i == 0 ? phi - (1.0f - wgt(0)) * mu : w * mu;
+    const float gn = g[i] - om_g * (g[i] - geq) + w * ch_k(i) * gsrc;
+    // a7: Nernst-Planck, l_eq of Eq. weq61, S_i + T_i of Eqs. weq59, weq60
+    const float leq = w * q * (1.0f + 3.0f * cu);
+    const float ln = l[i] - om_l * (l[i] - leq) + pref_l * w * (R + cx(i) * djx + cy(i) * djy);
+    // a8: hydrodynamics, f_eq of Eq. weq40, forcing of Eq. weq39 written as
+    // w_i [c_i.F + (c_i.u)(c_i.grad rho)] / c_s^2 (the u.grad rho terms cancel)
+    const float si = w * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
+    const float feq = (i == 0 ? (wgt(0) - 1.0f) : w) * 3.0f * p + rho * si;
+    const float cF = cx(i) * Fx + cy(i) * Fy;
+    const float cg = cx(i) * grx + cy(i) * gry;
+    const float fn = f[i] - om_f * (f[i] - feq) + pref_f * w * 3.0f * (cF + cu * cg);
+    int dir;
+    const int t = push_target(k, x, y, i, dir);
+    go[dir * (size_t)N + t] = gn;
+    lo[dir * (size_t)N + t] = ln;
+    fo[dir * (size_t)N + t] = fn;
+  }
+  hist[idx] = s_adv;
+  hist[(size_t)N + idx] = Jx;
+  hist[2 * (size_t)N + idx] = Jy;
+  hist[3 * (size_t)N + idx] = R;
+  hist[4 * (size_t)N + idx] = Fx;
+  hist[5 * (size_t)N + idx] = Fy;
+}
+
+__global__ void k_stats_reset(DevStats* s) {
+  s->iters_total = 0;
+  s->iters_min = 0x7fffffff;
+  s->iters_max = 0;
+  s->not_converged = 0;
+  s->nonfinite = 0;
+  s->steps = 0;
+  s->barrier_error = 0;
+  s->last_rel = 0.0;
+  s->sum_phi = 0.0;
+  s->sum_q = 0.0;
+}
+
+// ------------------------------------------------------------------------------------
+// Output fields.  k_phi_now: phi of the current populations; k_fields: the requested
+// fields (order of the mask bits) into io[slot][N].
+// ------------------------------------------------------------------------------------
+__global__ void k_phi_now(KParams k, const float* __restrict__ pops, float* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= k.N) return;
+  float s = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) s += __ldg(pops + i * (size_t)k.N + idx);
+  out[idx] = s;
+}
+
+__global__ void k_fields(KParams k, const StepState* __restrict__ ss, const float* __restrict__ pops,
+                         const float* __restrict__ phi_now, const float* __restrict__ phi_solve,
+                         const float* __restrict__ hbuf, const float* __restrict__ hist,
+                         const Ctl* ctl, unsigned mask, float* __restrict__ io) {
+  const int N = k.N;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N) return;
+  const int y = idx / k.nx, x = idx - y * k.nx;
+  const int parity = ld_cg(&ctl->parity);
+  const float* hs = hbuf + (size_t)parity * NH * N;
+  const StepState sa = *ss;
+  const Stencil st = load_stencil(k, sa, phi_now, x, y);
+  float gphx, gphy, lap;
+  grad_lap(st, gphx, gphy, lap);
+  const float phi = st.c;
+  float lsum = 0.0f, mx = 0.0f, my = 0.0f, fsum_nr = 0.0f;
+  const float* l = pops + 9 * (size_t)N;
+  const float* f = pops + 18 * (size_t)N;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const float fi = __ldg(f + i * (size_t)N + idx);
+    lsum += __ldg(l + i * (size_t)N + idx);
+    mx += cx(i) * fi;
+    my += cy(i) * fi;
+    if (i) fsum_nr += fi;
+  }
+  const float q = lsum + 0.5f * hist[3 * (size_t)N + idx];
+  const float rho = k.rho_v + k.drho * phi;
+  const float ux = (mx + 0.5f * hist[4 * (size_t)N + idx]) / rho;
+  const float uy = (my + 0.5f * hist[5 * (size_t)N + idx]) / rho;
+  const float uu = ux * ux + uy * uy;
+  const float p = 0.6f * (fsum_nr + 0.5f * k.drho * (ux * gphx + uy * gphy) -
+                          (2.0f / 3.0f) * rho * uu);
+  float hv[8];
+  float hsum = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    hv[i] = __ldg(hs + i * (size_t)N + idx);
+    hsum += hv[i];
+  }
+  const float varphi = hsum * (9.0f / 5.0f);
+  const float m1x = hv[0] - hv[2] + hv[4] - hv[5] - hv[6] + hv[7];
+  const float m1y = hv[1] - hv[3] + hv[4] + hv[5] - hv[6] - hv[7];
+  const float inv_den = 1.0f / (eps_hat_of(k, __ldg(phi_solve + idx)) + k.cs2tauh);
+  const float vals[8] = {phi, q, varphi, m1x * inv_den, m1y * inv_den, ux, uy, p};
+  int slot = 0;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    if (mask & (1u << b)) {
+      io[slot * (size_t)N + idx] = vals[b];
+      ++slot;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Launchers
+// ------------------------------------------------------------------------------------
+static inline int blocks_for(int n, int t) { return (n + t - 1) / t; }
+
+cudaError_t launch_step_set(const KParams& kp, const Buffers& b, int slot, long long n,
+                            int first, cudaStream_t st) {
+  k_step_set<<<1, 32, 0, st>>>(kp, b.ss + slot, n, first);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(const KParams& kp, const Buffers& b, int cur, bool have_p,
+                        cudaStream_t st) {
+  k_init<<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, b.ss + cur, b.io, have_p ? 1 : 0,
+                                                b.pops + (size_t)cur * NPOP * kp.N, b.h,
+                                                b.hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const KParams& kp, const Buffers& b, int cur, double tol,
+                           int min_iter, int max_iter, int fixed_iter, cudaStream_t st) {
+  const int nb = blocks_for(kp.N, 256);
+  if (nb > MAX_PARTIALS) return cudaErrorInvalidValue;
+  k_moments<<<nb, 256, 0, st>>>(kp, b.ss + cur, b.pops + (size_t)cur * NPOP * kp.N, b.hist,
+                                b.phi, b.aq, b.partials, b.ctl, tol, min_iter, max_iter,
+                                fixed_iter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coupled(const KParams& kp, const Buffers& b, int cur, cudaStream_t st) {
+  k_coupled<<<blocks_for(kp.N, 128), 128, 0, st>>>(
+      kp, b.ss, cur, b.pops + (size_t)cur * NPOP * kp.N,
+      b.pops + (size_t)(cur ^ 1) * NPOP * kp.N, b.phi, b.h, b.hist, b.ctl, b.stats);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats_reset(const Buffers& b, cudaStream_t st) {
+  k_stats_reset<<<1, 1, 0, st>>>(b.stats);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fields(const KParams& kp, const Buffers& b, int cur, unsigned mask,
+                          cudaStream_t st) {
+  const float* pops = b.pops + (size_t)cur * NPOP * kp.N;
+  k_phi_now<<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, pops, b.tmp);
+  k_fields<<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, b.ss + cur, pops, b.tmp, b.phi, b.h,
+                                                  b.hist, b.ctl, mask, b.io);
+  return cudaGetLastError();
+}
+
+// Graph nodes (the argument values are copied by cudaGraphAddKernelNode).
+cudaError_t add_moments_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
+                             cudaGraphNode_t* out, const KParams& kp, const Buffers& b, int cur,
+                             double tol, int min_iter, int max_iter, int fixed_iter) {
+  KParams k = kp;
+  const StepState* ss = b.ss + cur;
+  const float* pops = b.pops + (size_t)cur * NPOP * kp.N;
+  const float* hist = b.hist;
+  float* phi = b.phi;
+  float2* aq = b.aq;
+  double2* partials = b.partials;
+  Ctl* ctl = b.ctl;
+  void* args[] = {&k, &ss, &pops, &hist, &phi, &aq, &partials, &ctl, &tol, &min_iter, &max_iter,
+                  &fixed_iter};
+  cudaKernelNodeParams p = {};
+  p.func = (void*)k_moments;
+  p.gridDim = dim3(blocks_for(kp.N, 256));
+  p.blockDim = dim3(256);
+  p.kernelParams = args;
+  return cudaGraphAddKernelNode(out, g, deps, nd, &p);
+}
+
+cudaError_t add_coupled_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
+                             cudaGraphNode_t* out, const KParams& kp, const Buffers& b, int cur) {
+  KParams k = kp;
+  StepState* ss = b.ss;
+  const float* pin = b.pops + (size_t)cur * NPOP * kp.N;
+  float* pout = b.pops + (size_t)(cur ^ 1) * NPOP * kp.N;
+  const float* phi = b.phi;
+  const float* h = b.h;
+  float* hist = b.hist;
+  const Ctl* ctl = b.ctl;
+  DevStats* stats = b.stats;
+  void* args[] = {&k, &ss, &cur, &pin, &pout, &phi, &h, &hist, &ctl, &stats};
+  cudaKernelNodeParams p = {};
+  p.func = (void*)k_coupled;
+  p.gridDim = dim3(blocks_for(kp.N, 128));
+  p.blockDim = dim3(128);
+  p.kernelParams = args;
+  return cudaGraphAddKernelNode(out, g, deps, nd, &p);
+}
+
+cudaError_t add_poisson_node(cudaGraph_t g, cudaGraphNode_t* out, const KParams& kp,
+                             const Buffers& b, cudaGraphConditionalHandle cond);
+
+cudaError_t build_step_graph(const KParams& kp, const Buffers& b, int cur, double tol,
+                             int min_iter, int max_iter, int fixed_iter, const ResidentGeom* rg,
+                             int rthreads, size_t rsmem, cudaGraph_t* out) {
+  cudaGraph_t g;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphNode_t mn, wn, pn, cn;
+  if (rg) {
+    if ((e = add_moments_node(g, nullptr, 0, &mn, kp, b, cur, tol, min_iter, max_iter,
+                              fixed_iter)) != cudaSuccess ||
+        (e = add_poisson_resident_node(g, &mn, 1, &pn, kp, *rg, rthreads, rsmem, b)) !=
+            cudaSuccess ||
+        (e = add_coupled_node(g, &pn, 1, &cn, kp, b, cur)) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return e;
+    }
+    *out = g;
+    return cudaSuccess;
+  }
+  cudaGraphConditionalHandle h;
+  if ((e = add_moments_node(g, nullptr, 0, &mn, kp, b, cur, tol, min_iter, max_iter,
+                            fixed_iter)) != cudaSuccess ||
+      (e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault)) !=
+          cudaSuccess) {
+    cudaGraphDestroy(g);
+    return e;
+  }
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  if ((e = cudaGraphAddNode(&wn, g, &mn, nullptr, 1, &cp)) != cudaSuccess ||
+      (e = add_poisson_node(cp.conditional.phGraph_out[0], &pn, kp, b, h)) != cudaSuccess ||
+      (e = add_coupled_node(g, &wn, 1, &cn, kp, b, cur)) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return e;
+  }
+  *out = g;
+  return cudaSuccess;
+}
+
+}  // namespace ehd

@@ -1,0 +1,363 @@
+// The whole potential loop of one solve (Algorithm 1 step 3) in one cooperative launch,
+// with the potential populations held on chip.
+//
+// The lattice is cut into tiles, one CTA per tile and at most one tile per SM.  Each
+// thread keeps the post-stream populations h_1..h_8 of up to NPT nodes in registers for
+// the whole loop.  A sub-iteration (Eq. weq53, the same arithmetic as k_poisson):
+//   1. collide the tile's nodes; post-collision populations go to shared memory, and
+//      those of perimeter nodes also to a per-tile export area in global memory;
+//   2. grid barrier;
+//   3. decide: every CTA reduces the previous sub-iteration's FP64 partial sums in the
+//      same fixed order and applies the stopping rule identically; if the loop is done the
+//      registers hold exactly the paper's final state, which is written back;
+//   4. stream: gather h_i(x) = h*_i(x - c_i) from shared memory, from a neighbour tile's
+//      export area, or from the anti-bounce-back wall rule; form varphi^{k+1} and the
+//      partial sums of sum (varphi^{k+1} - varphi^k)^2 and sum (varphi^k)^2.
+// Export areas and partials are double-buffered by sub-iteration parity, so one grid
+// barrier per sub-iteration suffices.  The collision made just before the loop stops
+// never leaves the chip.
+//
+// The grid barrier spins on a generation counter with a time limit; a CTA that waits
+// longer than the limit sets an error flag and the kernel returns (with a cooperative
+// launch all CTAs are co-resident, so the limit is never reached in normal operation).
+#include "ehd_internal.cuh"
+
+namespace ehd {
+
+namespace {
+
+constexpr int NPT = 4;              // nodes per thread
+constexpr int MAX_THREADS = 1024;
+constexpr unsigned long long BARRIER_TIMEOUT_NS = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier for co-resident CTAs.  Returns false on timeout (error flag set).
+__device__ __forceinline__ bool grid_barrier(Ctl* sync, unsigned nblocks, unsigned& gen) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&sync->bar_count, 1u);
+    if (arrived == nblocks - 1u) {
+      sync->bar_count = 0u;
+      __threadfence();
+      atomicExch(&sync->bar_gen, g + 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*((volatile unsigned*)&sync->bar_gen) == g) {
+        if (global_ns() - t0 > BARRIER_TIMEOUT_NS) {
+          atomicOr(&sync->bar_error, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok && !*((volatile int*)&sync->bar_error);
+  }
+  __syncthreads();
+  gen += 1u;
+  return s_ok != 0;
+}
+
+struct TileGeom {
+  int tx0, ty0, tw, th;  // origin and size of this tile
+};
+
+__device__ __forceinline__ int perim_slot(int lx, int ly, int w, int h) {
+  if (ly == 0) return lx;
+  if (ly == h - 1) return w + lx;
+  if (lx == 0) return 2 * w + ly;
+  return 2 * w + h + ly;  // lx == w - 1
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(MAX_THREADS, 1)
+    k_poisson_resident(KParams k, ResidentGeom rg, float* __restrict__ hbuf,
+                       const float2* __restrict__ aq, float* __restrict__ exports,
+                       double2* __restrict__ rpartials, Ctl* ctl) {
+  extern __shared__ float hs[];  // [8][tile nodes] post-collision, then [2][tile nodes] (a, q)
+  __shared__ double s_w[MAX_THREADS / 32][2];
+  __shared__ double s_tot[2];
+
+  const int nx = k.nx, ny = k.ny;
+  const size_t N = (size_t)k.N;
+  const int ntiles = gridDim.x;
+  const int tile = blockIdx.x;
+  const int tcol = tile % rg.ntx, trow = tile / rg.ntx;
+  TileGeom tg;
+  tg.tx0 = tcol * rg.TX;
+  tg.ty0 = trow * rg.TY;
+  tg.tw = min(rg.TX, nx - tg.tx0);
+  tg.th = min(rg.TY, ny - tg.ty0);
+  const int tn = tg.tw * tg.th;
+  const int parity = ld_cg(&ctl->parity);
+  float* __restrict__ hsrc = hbuf + (size_t)parity * NH * N;
+  const float qshift = k.neutralize ? ld_cg(&ctl->mean_q) : 0.0f;
+  const float vw_b = ld_cg(&ctl->vw_b), vw_t = ld_cg(&ctl->vw_t);
+  const double tol = ctl->tol;
+  const int min_iter = ctl->min_iter, max_iter = ctl->max_iter, fixed = ctl->fixed_iter;
+  const float om = k.omega_h;
+  const int pstride = 8 * rg.pmax;  // floats per tile and parity in the export area
+
+  float* ca = hs + 8 * tn;   // forcing coefficient a per node
+  float* cq = ca + tn;       // source q (minus the neutralising shift) per node
+
+  // load the state of my nodes
+  float h[NPT][8];
+#pragma unroll
+  for (int s = 0; s < NPT; ++s) {
+    const int j = threadIdx.x + s * blockDim.x;
+    if (j < tn) {
+      const int ly = j / tg.tw, lx = j - ly * tg.tw;
+      const int g = (tg.ty0 + ly) * nx + tg.tx0 + lx;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) h[s][i] = hsrc[i * N + g];
+      const float2 c = aq[g];
+      ca[j] = c.x;
+      cq[j] = c.y - qshift;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) h[s][i] = 0.0f;
+    }
+  }
+
+  unsigned gen = ld_cg(&ctl->bar_gen);
+  int it = 0;
+  double rel = 0.0;
+  int conv = 0;
+  for (;;) {
+    // 1. collide
+    float* exp_cur = exports + (size_t)(it & 1) * ntiles * pstride + (size_t)tile * pstride;
+#pragma unroll
+    for (int s = 0; s < NPT; ++s) {
+      const int j = threadIdx.x + s * blockDim.x;
+      if (j >= tn) continue;
+      float hsum = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) hsum += h[s][i];
+      const float varphi = hsum * (9.0f / 5.0f);
+      const float m1x = h[s][0] - h[s][2] + h[s][4] - h[s][5] - h[s][6] + h[s][7];
+      const float m1y = h[s][1] - h[s][3] + h[s][4] + h[s][5] - h[s][6] - h[s][7];
+      const float qs = 0.125f * cq[j];
+      const float a = ca[j];
+      const int ly = j / tg.tw, lx = j - ly * tg.tw;
+      const bool perim = lx == 0 || ly == 0 || lx == tg.tw - 1 || ly == tg.th - 1;
+      const int slot = perim ? perim_slot(lx, ly, tg.tw, tg.th) : 0;
+#pragma unroll
+      for (int i = 1; i < 9; ++i) {
+        const float w = wgt(i);
+        const float cm = cx(i) * m1x + cy(i) * m1y;
+        const float v = h[s][i - 1] - om * (h[s][i - 1] - w * varphi) + a * w * cm + qs;
+        hs[(i - 1) * tn + j] = v;
+        if (perim) exp_cur[(i - 1) * rg.pmax + slot] = v;
+      }
+    }
+    // 2. all tiles' post-collision populations are visible
+    if (!grid_barrier(ctl, ntiles, gen)) return;
+    // 3. stopping decision on the previous sub-iteration's sums
+    if (it > 0) {
+      if (threadIdx.x < 32) {
+        const double2* pp = rpartials + (size_t)((it - 1) & 1) * ntiles;
+        double a = 0.0, b = 0.0;
+        for (int t = threadIdx.x; t < ntiles; t += 32) {
+          const double2 v = __ldcg(pp + t);
+          a += v.x;
+          b += v.y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (threadIdx.x == 0) {
+          s_tot[0] = a;
+          s_tot[1] = b;
+        }
+      }
+      __syncthreads();
+      const double nm = s_tot[0], dn = s_tot[1];
+      if (nm == 0.0 && dn == 0.0)
+        rel = 0.0;
+      else if (dn == 0.0)
+        rel = __longlong_as_double(0x7ff0000000000000ll);
+      else
+        rel = sqrt(nm / dn);
+      bool done;
+      if (fixed > 0) {
+        done = it >= fixed;
+        conv = 1;
+      } else {
+        conv = (it >= min_iter) && (rel < tol);
+        done = conv || it >= max_iter;
+      }
+      if (done) break;
+    }
+    // 4. stream into my nodes
+    const float* exp_all = exports + (size_t)(it & 1) * ntiles * pstride;
+    float num = 0.0f, den = 0.0f;
+#pragma unroll
+    for (int s = 0; s < NPT; ++s) {
+      const int j = threadIdx.x + s * blockDim.x;
+      if (j >= tn) continue;
+      const int ly = j / tg.tw, lx = j - ly * tg.tw;
+      const int gx = tg.tx0 + lx, gy = tg.ty0 + ly;
+      float vold = 0.0f, vnew = 0.0f;
+#pragma unroll
+      for (int i = 1; i < 9; ++i) {
+        const int sxl = lx - cx(i), syl = ly - cy(i);
+        float v;
+        if (sxl >= 0 && sxl < tg.tw && syl >= 0 && syl < tg.th) {
+          v = hs[(i - 1) * tn + syl * tg.tw + sxl];
+        } else {
+          int sy = gy - cy(i);
+          if (k.walls && (sy < 0 || sy >= ny)) {
+            const float vw = sy < 0 ? vw_b : vw_t;
+            v = -hs[(opp(i) - 1) * tn + j] + 2.0f * wgt(i) * vw;
+          } else {
+            sy = wrap(sy, ny);
+            const int sx = wrap(gx - cx(i), nx);
+            const int otc = sx / rg.TX, otr = sy / rg.TY;
+            const int ox0 = otc * rg.TX, oy0 = otr * rg.TY;
+            const int ow = min(rg.TX, nx - ox0), oh = min(rg.TY, ny - oy0);
+            const int ot = otr * rg.ntx + otc;
+            if (ot == tile) {
+              v = hs[(i - 1) * tn + (sy - oy0) * ow + (sx - ox0)];
+            } else {
+              const int sl = perim_slot(sx - ox0, sy - oy0, ow, oh);
+              v = __ldcg(exp_all + (size_t)ot * pstride + (i - 1) * rg.pmax + sl);
+            }
+          }
+        }
+        vold += h[s][i - 1];
+        h[s][i - 1] = v;
+        vnew += v;
+      }
+      const float vn = vnew * (9.0f / 5.0f);
+      const float vo = vold * (9.0f / 5.0f);
+      const float d = vn - vo;
+      num += d * d;
+      den += vo * vo;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      num += __shfl_xor_sync(0xffffffffu, num, o);
+      den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      s_w[threadIdx.x >> 5][0] = (double)num;
+      s_w[threadIdx.x >> 5][1] = (double)den;
+    }
+    __syncthreads();  // shared populations consumed; warp sums visible
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        a += s_w[w][0];
+        b += s_w[w][1];
+      }
+      rpartials[(size_t)(it & 1) * ntiles + tile] = make_double2(a, b);
+    }
+    ++it;
+  }
+
+  // the registers hold the final state: write it back in place
+#pragma unroll
+  for (int s = 0; s < NPT; ++s) {
+    const int j = threadIdx.x + s * blockDim.x;
+    if (j >= tn) continue;
+    const int ly = j / tg.tw, lx = j - ly * tg.tw;
+    const int g = (tg.ty0 + ly) * nx + tg.tx0 + lx;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) hsrc[i * N + g] = h[s][i];
+  }
+  if (tile == 0 && threadIdx.x == 0) {
+    ctl->iter = it;
+    ctl->rel = rel;
+    ctl->converged = conv;
+    ctl->done = 1;
+  }
+}
+
+// Tile geometry for the resident loop, or false if the lattice does not fit on chip with
+// one tile per SM.
+bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* threads,
+                       size_t* smem) {
+  const int max_nodes = NPT * MAX_THREADS;
+  const long long N = (long long)kp.nx * kp.ny;
+  const int TX = kp.nx < 64 ? kp.nx : 64;
+  const int ntx = (kp.nx + TX - 1) / TX;
+  if (ntx > num_sms) return false;
+  // about 2048 nodes per tile, never more tiles than SMs
+  long long want = (N + 2047) / 2048;
+  if (want > num_sms) want = num_sms;
+  int nty = (int)(want / ntx);
+  if (nty < 1) nty = 1;
+  if (nty > num_sms / ntx) nty = num_sms / ntx;
+  int TY = (kp.ny + nty - 1) / nty;
+  if ((long long)TX * TY > max_nodes) return false;
+  nty = (kp.ny + TY - 1) / TY;
+  g->TX = TX;
+  g->TY = TY;
+  g->ntx = ntx;
+  g->nty = nty;
+  g->pmax = 2 * TX + 2 * TY;
+  const int tn = TX * TY;
+  int t = (tn + NPT - 1) / NPT;
+  t = (t + 31) / 32 * 32;
+  *threads = t < 32 ? 32 : t;
+  *smem = sizeof(float) * 10 * (size_t)tn;
+  return true;
+}
+
+int resident_nodes_per_thread() { return NPT; }
+
+const void* resident_kernel() { return (const void*)k_poisson_resident; }
+
+cudaError_t launch_poisson_resident(const KParams& kp, const ResidentGeom& g, int threads,
+                                    size_t smem, const Buffers& b, cudaStream_t st) {
+  KParams k = kp;
+  ResidentGeom gg = g;
+  float* h = b.h;
+  const float2* aq = b.aq;
+  float* ex = b.exports;
+  double2* rp = b.rpartials;
+  Ctl* ctl = b.ctl;
+  void* args[] = {&k, &gg, &h, &aq, &ex, &rp, &ctl};
+  return cudaLaunchCooperativeKernel((const void*)k_poisson_resident, dim3(g.ntx * g.nty),
+                                     dim3(threads), args, smem, st);
+}
+
+cudaError_t add_poisson_resident_node(cudaGraph_t graph, const cudaGraphNode_t* deps, size_t nd,
+                                      cudaGraphNode_t* out, const KParams& kp,
+                                      const ResidentGeom& g, int threads, size_t smem,
+                                      const Buffers& b) {
+  KParams k = kp;
+  ResidentGeom gg = g;
+  float* h = b.h;
+  const float2* aq = b.aq;
+  float* ex = b.exports;
+  double2* rp = b.rpartials;
+  Ctl* ctl = b.ctl;
+  void* args[] = {&k, &gg, &h, &aq, &ex, &rp, &ctl};
+  cudaKernelNodeParams p = {};
+  p.func = (void*)k_poisson_resident;
+  p.gridDim = dim3(g.ntx * g.nty);
+  p.blockDim = dim3(threads);
+  p.sharedMemBytes = (unsigned)smem;
+  p.kernelParams = args;
+  cudaError_t e = cudaGraphAddKernelNode(out, graph, deps, nd, &p);
+  if (e != cudaSuccess) return e;
+  cudaKernelNodeAttrValue v = {};
+  v.cooperative = 1;
+  return cudaGraphKernelNodeSetAttribute(*out, cudaLaunchAttributeCooperative, &v);
+}
+
+}  // namespace ehd

@@ -1,0 +1,293 @@
+"""Thin ctypes binding of the CUDA library libehd.so (C ABI in include/ehd.h).
+
+Argument marshalling only: every step of the method runs in the library's kernels.
+PyTorch, when used, only provides device memory (the workspace, device field buffers)
+and the CUDA stream.  There is no CPU fallback: without the built library every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libehd.so")
+
+EHD_OK = 0
+STATUS = {0: "EHD_OK", 1: "EHD_ERR_INVALID_ARG", 2: "EHD_ERR_UNSTABLE_PARAMS",
+          3: "EHD_ERR_NOMEM", 4: "EHD_ERR_NOT_CONVERGED", 5: "EHD_ERR_NONFINITE",
+          6: "EHD_ERR_BUSY", 7: "EHD_ERR_CUDA"}
+EHD_HOST, EHD_DEVICE = 0, 1
+FIELDS = ("phi", "q", "varphi", "Ex", "Ey", "ux", "uy", "p")
+
+
+class EhdError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("walls_y", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("rho_l", ctypes.c_double), ("rho_v", ctypes.c_double),
+        ("mu_l", ctypes.c_double), ("mu_v", ctypes.c_double),
+        ("sigma_l", ctypes.c_double), ("sigma_v", ctypes.c_double),
+        ("eps_l", ctypes.c_double), ("eps_v", ctypes.c_double), ("alpha", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("width", ctypes.c_double), ("mobility", ctypes.c_double),
+        ("theta_bottom_deg", ctypes.c_double), ("theta_top_deg", ctypes.c_double),
+        ("ew_bottom", ctypes.c_double), ("ew_sign", ctypes.c_double),
+        ("varphi_bottom", ctypes.c_double), ("varphi_top", ctypes.c_double),
+        ("ramp_steps", ctypes.c_int32), ("neutralize_charge", ctypes.c_int32),
+        ("body_gx", ctypes.c_double), ("body_gy", ctypes.c_double),
+        ("poisson_tol", ctypes.c_double), ("poisson_max_iter", ctypes.c_int32),
+        ("poisson_min_iter", ctypes.c_int32), ("poisson_fixed_iter", ctypes.c_int32),
+        ("poisson_loop", ctypes.c_int32), ("start_step", ctypes.c_int64),
+    ]
+
+    @classmethod
+    def from_dict(cls, d):
+        p = cls()
+        for name, _ in cls._fields_:
+            if name in d:
+                setattr(p, name, d[name])
+        return p
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("step", ctypes.c_int64), ("steps", ctypes.c_int32),
+        ("poisson_iters_total", ctypes.c_int32), ("poisson_iters_min", ctypes.c_int32),
+        ("poisson_iters_max", ctypes.c_int32), ("not_converged_steps", ctypes.c_int32),
+        ("nonfinite", ctypes.c_int32), ("last_rel_change", ctypes.c_double),
+        ("sum_phi", ctypes.c_double), ("sum_q", ctypes.c_double),
+        ("kernel_launches", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class KernelTimes(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 4), ("launches", ctypes.c_int64 * 4)]
+
+    KINDS = ("moments", "potential", "potential_idle", "coupled")
+
+    def as_dict(self):
+        return {k: {"ms": self.ms[j], "launches": self.launches[j]}
+                for j, k in enumerate(self.KINDS)}
+
+
+_lib = None
+
+# name -> (restype, argtypes); every function declared in include/ehd.h
+SIGNATURES = {
+    "ehd_workspace_bytes": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]),
+    "ehd_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_void_p, ctypes.c_size_t,
+                                  ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "ehd_set_fields": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 5 + [ctypes.c_int]),
+    "ehd_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Stats)]),
+    "ehd_read_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Stats)]),
+    "ehd_loop_kind": (ctypes.c_int, [ctypes.c_void_p]),
+    "ehd_solve_potential": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "ehd_read_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint,
+                                       ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
+    "ehd_state_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
+    "ehd_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "ehd_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "ehd_destroy": (None, [ctypes.c_void_p]),
+    "ehd_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ehd_version": (ctypes.c_char_p, []),
+    "ehd_abi_sizes": (ctypes.c_int, [ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.POINTER(ctypes.c_size_t)]),
+    "ehd_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "ehd_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(KernelTimes)]),
+}
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with `python -m paper_2407_01654_gb300.build`"
+                " (there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code, what):
+    if code != EHD_OK:
+        raise EhdError(code, what)
+
+
+def _host(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _is_torch_cuda(a):
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+class Sim:
+    """One simulation on the GPU.
+
+    params: dict of ehd_params fields (see paper_2407_01654_gb300.workloads).
+    workspace: "torch" (a torch uint8 tensor owned by this object), "library" (the
+    library allocates), or a torch tensor / (pointer, bytes) pair supplied by the caller.
+    stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None (torch's current
+    stream when torch is used, else the default stream).
+    """
+
+    def __init__(self, params, workspace="torch", stream=None):
+        L = lib()
+        self.params = dict(params)
+        self._p = Params.from_dict(self.params)
+        nb = ctypes.c_size_t()
+        _check(L.ehd_workspace_bytes(ctypes.byref(self._p), ctypes.byref(nb)), "ehd_workspace_bytes")
+        self.workspace_bytes = nb.value
+        self._ws_keep = None
+        ptr = None
+        if isinstance(workspace, str) and workspace == "torch":
+            import torch
+            self._ws_keep = torch.empty(nb.value + 256, dtype=torch.uint8, device="cuda")
+            ptr = (self._ws_keep.data_ptr() + 255) // 256 * 256
+        elif isinstance(workspace, str) and workspace == "library":
+            ptr = None
+        elif isinstance(workspace, tuple):
+            ptr = workspace[0]
+        elif workspace is not None:
+            self._ws_keep = workspace
+            ptr = workspace.data_ptr()
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = 0
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self.stream = int(stream)
+        h = ctypes.c_void_p()
+        _check(L.ehd_create(ctypes.byref(self._p), ptr, nb.value, self.stream, ctypes.byref(h)),
+               "ehd_create")
+        self._h = h
+        self.nx, self.ny = self.params["nx"], self.params["ny"]
+
+    # -- life cycle ----------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ehd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- calls -----------------------------------------------------------------------
+    def set_fields(self, phi, q, ux, uy, p=None):
+        """Host numpy arrays (converted to double) or CUDA float32 torch tensors."""
+        arrs = [phi, q, ux, uy] + ([p] if p is not None else [])
+        if _is_torch_cuda(phi):
+            keep = [a.contiguous() for a in arrs]
+            ptrs = [a.data_ptr() for a in keep]
+            mem = EHD_DEVICE
+        else:
+            keep = [_host(a) for a in arrs]
+            ptrs = [a.ctypes.data for a in keep]
+            mem = EHD_HOST
+        if p is None:
+            ptrs.append(None)
+        code = lib().ehd_set_fields(self._h, *ptrs, mem)
+        if code not in (EHD_OK, 4):
+            _check(code, "ehd_set_fields")
+        return code
+
+    def step(self, nsteps=1, stats=True):
+        st = Stats()
+        code = lib().ehd_step(self._h, int(nsteps), ctypes.byref(st) if stats else None)
+        if code not in (EHD_OK, 4, 5):
+            _check(code, "ehd_step")
+        out = st.as_dict() if stats else {}
+        out["status"] = code
+        return out
+
+    def uses_resident_loop(self):
+        """True when the potential loop runs on chip (one cooperative launch per solve)."""
+        return bool(lib().ehd_loop_kind(self._h) == 2)
+
+    def read_stats(self):
+        st = Stats()
+        code = lib().ehd_read_stats(self._h, ctypes.byref(st))
+        if code not in (EHD_OK, 4, 5):
+            _check(code, "ehd_read_stats")
+        out = st.as_dict()
+        out["status"] = code
+        return out
+
+    def solve_potential(self, tol=0.0, max_iter=0):
+        it = ctypes.c_int()
+        rel = ctypes.c_double()
+        code = lib().ehd_solve_potential(self._h, float(tol), int(max_iter), ctypes.byref(it),
+                                         ctypes.byref(rel))
+        if code not in (EHD_OK, 4):
+            _check(code, "ehd_solve_potential")
+        return it.value, rel.value, code
+
+    def read_fields(self, names=FIELDS, device=False):
+        """dict name -> numpy float64 array [ny, nx] (or torch float32 CUDA tensors)."""
+        mask = 0
+        for n in names:
+            mask |= 1 << FIELDS.index(n)
+        order = [n for n in FIELDS if mask & (1 << FIELDS.index(n))]
+        if device:
+            import torch
+            outs = [torch.empty((self.ny, self.nx), dtype=torch.float32, device="cuda")
+                    for _ in order]
+            ptrs = [o.data_ptr() for o in outs]
+            mem = EHD_DEVICE
+        else:
+            outs = [np.empty((self.ny, self.nx), dtype=np.float64) for _ in order]
+            ptrs = [o.ctypes.data for o in outs]
+            mem = EHD_HOST
+        arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+        _check(lib().ehd_read_fields(self._h, mask, arr, mem), "ehd_read_fields")
+        return dict(zip(order, outs))
+
+    def profile(self, enable=True):
+        _check(lib().ehd_profile(self._h, 1 if enable else 0), "ehd_profile")
+
+    def profile_read(self):
+        kt = KernelTimes()
+        _check(lib().ehd_profile_read(self._h, ctypes.byref(kt)), "ehd_profile_read")
+        return kt.as_dict()
+
+    def save_state(self):
+        nb = ctypes.c_size_t()
+        _check(lib().ehd_state_bytes(self._h, ctypes.byref(nb)), "ehd_state_bytes")
+        buf = ctypes.create_string_buffer(nb.value)
+        _check(lib().ehd_save_state(self._h, buf, nb.value), "ehd_save_state")
+        return buf.raw
+
+    def load_state(self, blob):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(lib().ehd_load_state(self._h, buf, len(blob)), "ehd_load_state")
