@@ -56,7 +56,7 @@ constexpr uint64_t STATE_MAGIC = 0x4548443153544154ull;  // "EHD1STAT"
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-  size_t ss, pops, h, hist, phi, aq, io, tmp, partials, ctl, stats, exports, rpartials, total;
+  size_t ss, pops, pops16, h, hist, phi, aq, io, tmp, partials, ctl, stats, exports, rpartials, total;
   size_t export_floats, rtiles;
 };
 
@@ -74,7 +74,13 @@ Layout layout_for(const ehd_params& P) {
     return at;
   };
   L.ss = take(sizeof(StepState) * 2);
-  L.pops = take(sizeof(float) * 2 * NPOP * (size_t)N);
+  if (P.precision == EHD_FP16DEV) {
+    L.pops = take(sizeof(float) * 2 * 3 * (size_t)N);
+    L.pops16 = take(sizeof(__half) * 2 * 24 * (size_t)N);
+  } else {
+    L.pops = take(sizeof(float) * 2 * NPOP * (size_t)N);
+    L.pops16 = take(256);
+  }
   L.h = take(sizeof(float) * 2 * NH * (size_t)N);
   L.hist = take(sizeof(float) * NHIST * (size_t)N);
   L.phi = take(sizeof(float) * (size_t)N);
@@ -113,7 +119,7 @@ bool sizes_ok(const ehd_params* p) {
 int validate(const ehd_params* p) {
   if (!p || !sizes_ok(p)) return EHD_ERR_INVALID_ARG;
   if (p->walls_y != 0 && p->walls_y != 1) return EHD_ERR_INVALID_ARG;
-  if (p->precision != EHD_FP32) return EHD_ERR_INVALID_ARG;
+  if (p->precision != EHD_FP32 && p->precision != EHD_FP16DEV) return EHD_ERR_INVALID_ARG;
   if (!(p->rho_l > 0 && p->rho_v > 0 && p->mu_l > 0 && p->mu_v > 0 && p->eps_l > 0 &&
         p->eps_v > 0 && p->sigma_l >= 0 && p->sigma_v >= 0 && p->alpha > 0 && p->gamma >= 0 &&
         p->width > 0 && p->mobility > 0))
@@ -179,6 +185,11 @@ KParams make_kparams(const ehd_params& P) {
   k.varphi_b = P.varphi_bottom;
   k.varphi_t = P.varphi_top;
   k.ramp_steps = P.ramp_steps;
+  k.half = P.precision == EHD_FP16DEV ? 1 : 0;
+  for (int f = 0; f < 3; ++f) {
+    k.psc[f] = 1.0f;
+    k.ipsc[f] = 1.0f;
+  }
   return k;
 }
 
@@ -306,20 +317,61 @@ void ensure_graphs(ehd_sim* s) {
   s->graphs_ok = true;
 }
 
-int stage_in(ehd_sim* s, const void* src, int slot, int mem) {
+// Copies one input field into the staging area; returns its largest magnitude in *amax
+// (used to choose the FP16 storage scales).
+int stage_in(ehd_sim* s, const void* src, int slot, int mem, double* amax) {
   const size_t N = (size_t)s->kp.N;
   float* dst = s->b.io + slot * N;
+  float* stage = s->h_stage + slot * N;
   if (mem == EHD_DEVICE) {
     EHD_CUDA(cudaMemcpyAsync(dst, src, N * sizeof(float), cudaMemcpyDeviceToDevice,
                              s->stream));
+    if (s->kp.half) {
+      EHD_CUDA(cudaMemcpyAsync(stage, src, N * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+      EHD_CUDA(cudaStreamSynchronize(s->stream));
+    }
   } else {
     const double* d = static_cast<const double*>(src);
-    float* stage = s->h_stage + slot * N;
     for (size_t i = 0; i < N; ++i) stage[i] = (float)d[i];
     EHD_CUDA(cudaMemcpyAsync(dst, stage, N * sizeof(float), cudaMemcpyHostToDevice,
                              s->stream));
   }
+  double m = 0.0;
+  if (s->kp.half)
+    for (size_t i = 0; i < N; ++i) {
+      const double a = std::fabs((double)stage[i]);
+      m = a > m ? a : m;
+    }
+  *amax = m;
   return EHD_OK;
+}
+
+// Power of two 2^floor(log2(1/ref)): the FP16 scale that maps a magnitude ref to [0.5, 1).
+float pow2_scale(double ref) {
+  int e;
+  std::frexp(1.0 / ref, &e);
+  return (float)std::ldexp(1.0, e - 1);
+}
+
+// FP16 storage scales from the parameters and the initial fields: g's moving populations
+// carry w_i hbar (hbar ~ beta), l's w_i q, f's w_i (3 p + 3 rho c.u).
+void choose_scales(ehd_sim* s, double qmax, double umax) {
+  const ehd_params& P = s->P;
+  const double beta = 12.0 * P.gamma / P.width;
+  const double eps_max = P.eps_l > P.eps_v ? P.eps_l : P.eps_v;
+  const double rho_max = P.rho_l > P.rho_v ? P.rho_l : P.rho_v;
+  double dphi = std::fabs(P.varphi_bottom - P.varphi_top);
+  dphi = std::fmax(dphi, std::fmax(std::fabs(P.varphi_bottom), std::fabs(P.varphi_top)));
+  const double L = (double)(P.nx < P.ny ? P.nx : P.ny);
+  const double g_ref = std::fmax(beta, 1e-6);
+  const double q_ref = std::fmax(std::fmax(qmax, eps_max * dphi / (L * L)), 1e-9);
+  const double f_ref = std::fmax(std::fmax(3.0 * rho_max * std::fmax(umax, 1e-3),
+                                           eps_max * (dphi / L) * (dphi / L)), 1e-9);
+  const double refs[3] = {g_ref, q_ref, f_ref};
+  for (int f = 0; f < 3; ++f) {
+    s->kp.psc[f] = pow2_scale(refs[f]);
+    s->kp.ipsc[f] = 1.0f / s->kp.psc[f];
+  }
 }
 
 }  // namespace
@@ -387,6 +439,7 @@ int ehd_create(const ehd_params* params, void* workspace, size_t workspace_bytes
   char* base = static_cast<char*>(s->ws);
   s->b.ss = reinterpret_cast<StepState*>(base + L.ss);
   s->b.pops = reinterpret_cast<float*>(base + L.pops);
+  s->b.pops16 = reinterpret_cast<__half*>(base + L.pops16);
   s->b.h = reinterpret_cast<float*>(base + L.h);
   s->b.hist = reinterpret_cast<float*>(base + L.hist);
   s->b.phi = reinterpret_cast<float*>(base + L.phi);
@@ -505,11 +558,18 @@ int ehd_set_fields(ehd_sim* s, const void* phi, const void* q, const void* ux, c
   if (!s || !phi || !q || !ux || !uy || (mem != EHD_HOST && mem != EHD_DEVICE))
     return EHD_ERR_INVALID_ARG;
   int st;
-  if ((st = stage_in(s, phi, 0, mem)) != EHD_OK) return st;
-  if ((st = stage_in(s, q, 1, mem)) != EHD_OK) return st;
-  if ((st = stage_in(s, ux, 2, mem)) != EHD_OK) return st;
-  if ((st = stage_in(s, uy, 3, mem)) != EHD_OK) return st;
-  if (p && (st = stage_in(s, p, 4, mem)) != EHD_OK) return st;
+  double m_phi, m_q, m_ux, m_uy, m_p;
+  if ((st = stage_in(s, phi, 0, mem, &m_phi)) != EHD_OK) return st;
+  if ((st = stage_in(s, q, 1, mem, &m_q)) != EHD_OK) return st;
+  if ((st = stage_in(s, ux, 2, mem, &m_ux)) != EHD_OK) return st;
+  if ((st = stage_in(s, uy, 3, mem, &m_uy)) != EHD_OK) return st;
+  if (p && (st = stage_in(s, p, 4, mem, &m_p)) != EHD_OK) return st;
+  if (s->kp.half) {
+    choose_scales(s, m_q, m_ux > m_uy ? m_ux : m_uy);
+    // the step graphs hold the coefficients: rebuild them with the new scales
+    destroy_graphs(s);
+    s->graphs_tried = false;
+  }
   s->n = s->P.start_step;
   s->history_valid = false;
   s->cur = 0;
@@ -652,11 +712,18 @@ struct StateHeader {
   int32_t nx, ny;
   int64_t n;
   int32_t history_valid, last_k;
+  int32_t precision, pad;
+  float psc[3], pad2;
 };
+
+size_t pop_bytes(const KParams& k) {
+  return k.half ? (sizeof(float) * 3 + sizeof(__half) * 24) * (size_t)k.N
+                : sizeof(float) * NPOP * (size_t)k.N;
+}
 
 int ehd_state_bytes(const ehd_sim* s, size_t* bytes) {
   if (!s || !bytes) return EHD_ERR_INVALID_ARG;
-  *bytes = sizeof(StateHeader) + sizeof(float) * (size_t)s->kp.N * (NPOP + NH + NHIST + 1);
+  *bytes = sizeof(StateHeader) + pop_bytes(s->kp) + sizeof(float) * (size_t)s->kp.N * (NH + NHIST + 1);
   return EHD_OK;
 }
 
@@ -667,14 +734,30 @@ int ehd_save_state(ehd_sim* s, void* buf, size_t bytes) {
   const size_t N = (size_t)s->kp.N;
   EHD_CUDA(cudaMemcpyAsync(s->h_ctl, s->b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
   EHD_CUDA(cudaStreamSynchronize(s->stream));
-  StateHeader hd{STATE_MAGIC, s->P.nx, s->P.ny, s->n, s->history_valid ? 1 : 0, s->last_k};
+  StateHeader hd{};
+  hd.magic = STATE_MAGIC;
+  hd.nx = s->P.nx;
+  hd.ny = s->P.ny;
+  hd.n = s->n;
+  hd.history_valid = s->history_valid ? 1 : 0;
+  hd.last_k = s->last_k;
+  hd.precision = s->P.precision;
+  for (int f = 0; f < 3; ++f) hd.psc[f] = s->kp.psc[f];
   char* p = static_cast<char*>(buf);
   std::memcpy(p, &hd, sizeof(hd));
   p += sizeof(hd);
-  const float* pops = s->b.pops + (size_t)s->cur * NPOP * N;
+  const Pops pc = pops_copy(s->kp, s->b, s->cur);
   const float* h = s->b.h + (size_t)s->h_ctl->parity * NH * N;
-  EHD_CUDA(cudaMemcpyAsync(p, pops, sizeof(float) * NPOP * N, cudaMemcpyDeviceToHost, s->stream));
-  p += sizeof(float) * NPOP * N;
+  if (s->kp.half) {
+    EHD_CUDA(cudaMemcpyAsync(p, pc.p32, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, s->stream));
+    p += sizeof(float) * 3 * N;
+    EHD_CUDA(cudaMemcpyAsync(p, pc.p16, sizeof(__half) * 24 * N, cudaMemcpyDeviceToHost, s->stream));
+    p += sizeof(__half) * 24 * N;
+  } else {
+    EHD_CUDA(cudaMemcpyAsync(p, pc.p32, sizeof(float) * NPOP * N, cudaMemcpyDeviceToHost,
+                             s->stream));
+    p += sizeof(float) * NPOP * N;
+  }
   EHD_CUDA(cudaMemcpyAsync(p, h, sizeof(float) * NH * N, cudaMemcpyDeviceToHost, s->stream));
   p += sizeof(float) * NH * N;
   EHD_CUDA(cudaMemcpyAsync(p, s->b.hist, sizeof(float) * NHIST * N, cudaMemcpyDeviceToHost,
@@ -691,13 +774,31 @@ int ehd_load_state(ehd_sim* s, const void* buf, size_t bytes) {
     return EHD_ERR_INVALID_ARG;
   StateHeader hd;
   std::memcpy(&hd, buf, sizeof(hd));
-  if (hd.magic != STATE_MAGIC || hd.nx != s->P.nx || hd.ny != s->P.ny) return EHD_ERR_INVALID_ARG;
+  if (hd.magic != STATE_MAGIC || hd.nx != s->P.nx || hd.ny != s->P.ny ||
+      hd.precision != s->P.precision)
+    return EHD_ERR_INVALID_ARG;
   const size_t N = (size_t)s->kp.N;
   const char* p = static_cast<const char*>(buf) + sizeof(hd);
   s->cur = 0;
-  EHD_CUDA(cudaMemcpyAsync(s->b.pops, p, sizeof(float) * NPOP * N, cudaMemcpyHostToDevice,
-                           s->stream));
-  p += sizeof(float) * NPOP * N;
+  if (s->kp.half) {
+    for (int f = 0; f < 3; ++f) {
+      s->kp.psc[f] = hd.psc[f];
+      s->kp.ipsc[f] = 1.0f / hd.psc[f];
+    }
+    destroy_graphs(s);
+    s->graphs_tried = false;
+  }
+  const Pops pc = pops_copy(s->kp, s->b, 0);
+  if (s->kp.half) {
+    EHD_CUDA(cudaMemcpyAsync(pc.p32, p, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, s->stream));
+    p += sizeof(float) * 3 * N;
+    EHD_CUDA(cudaMemcpyAsync(pc.p16, p, sizeof(__half) * 24 * N, cudaMemcpyHostToDevice, s->stream));
+    p += sizeof(__half) * 24 * N;
+  } else {
+    EHD_CUDA(cudaMemcpyAsync(pc.p32, p, sizeof(float) * NPOP * N, cudaMemcpyHostToDevice,
+                             s->stream));
+    p += sizeof(float) * NPOP * N;
+  }
   EHD_CUDA(cudaMemcpyAsync(s->b.h, p, sizeof(float) * NH * N, cudaMemcpyHostToDevice, s->stream));
   p += sizeof(float) * NH * N;
   EHD_CUDA(cudaMemcpyAsync(s->b.hist, p, sizeof(float) * NHIST * N, cudaMemcpyHostToDevice,

@@ -21,6 +21,7 @@
 //   ctl, stats      loop control and statistics (device structs below).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -74,7 +75,46 @@ struct KParams {
   double ew_signed;         // ew_sign * eta/d of the bottom wall
   double varphi_b, varphi_t;
   int ramp_steps;
+  // population storage: 0 FP32; 1 FP16 moving populations, stored as half(S_f p_i / w_i)
+  // per field f (g, l, f) with power-of-two scales S_f, rest populations FP32
+  int half;
+  float psc[3];             // S_f
+  float ipsc[3];            // 1 / S_f
 };
+
+// One copy of the g, l, f populations.  FP32: p32 = [27][N].  FP16: p32 = rest
+// populations [3][N], p16 = moving populations [24][N].
+struct Pops {
+  float* p32;
+  __half* p16;
+};
+
+__host__ __device__ constexpr float inv_wgt(int i) {
+  return i == 0 ? 9.0f / 4.0f : (i <= 4 ? 9.0f : 36.0f);
+}
+
+template <bool HALF>
+__device__ __forceinline__ float ld_pop(const KParams& k, const Pops& P, int field, int i,
+                                        size_t idx) {
+  const size_t N = (size_t)k.N;
+  if (!HALF) return __ldg(P.p32 + (size_t)(field * 9 + i) * N + idx);
+  if (i == 0) return __ldg(P.p32 + (size_t)field * N + idx);
+  const __half v = P.p16[(size_t)(field * 8 + i - 1) * N + idx];
+  return __half2float(v) * (k.ipsc[field] * wgt(i));
+}
+
+template <bool HALF>
+__device__ __forceinline__ void st_pop(const KParams& k, const Pops& P, int field, int i,
+                                       size_t idx, float v) {
+  const size_t N = (size_t)k.N;
+  if (!HALF) {
+    P.p32[(size_t)(field * 9 + i) * N + idx] = v;
+  } else if (i == 0) {
+    P.p32[(size_t)field * N + idx] = v;
+  } else {
+    P.p16[(size_t)(field * 8 + i - 1) * N + idx] = __float2half_rn(v * (k.psc[field] * inv_wgt(i)));
+  }
+}
 
 // Values that change from step to step, kept on the device so that a step needs no
 // host input: written for the next step by the coupled kernel (one thread), for the
@@ -168,7 +208,8 @@ __device__ __forceinline__ T ld_cg(const T* p) { return __ldcg(p); }
 namespace ehd {
 struct Buffers {
   StepState* ss;     // [2]
-  float* pops;       // [2][27][N]
+  float* pops;       // FP32: [2][27][N]; FP16: [2][3][N] rest populations
+  __half* pops16;    // FP16: [2][24][N] moving populations
   float* h;          // [2][8][N]
   float* hist;       // [6][N]
   float* phi;        // [N]
@@ -181,6 +222,18 @@ struct Buffers {
   float* exports;    // resident loop: [2][tiles][8][pmax]
   double2* rpartials;// resident loop: [2][tiles]
 };
+
+__host__ __device__ inline Pops pops_copy(const KParams& k, const Buffers& b, int c) {
+  Pops P;
+  if (k.half) {
+    P.p32 = b.pops + (size_t)c * 3 * k.N;
+    P.p16 = b.pops16 + (size_t)c * 24 * k.N;
+  } else {
+    P.p32 = b.pops + (size_t)c * NPOP * k.N;
+    P.p16 = nullptr;
+  }
+  return P;
+}
 
 // Resident potential loop (poisson_resident.cu).
 bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* threads,

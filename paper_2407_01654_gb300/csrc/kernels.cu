@@ -94,9 +94,9 @@ __device__ __forceinline__ float warp_sum(float v) {
 // ------------------------------------------------------------------------------------
 // Initialisation: populations at equilibrium (Eqs. weq40, weq46, weq54, weq61).
 // ------------------------------------------------------------------------------------
+template <bool HALF>
 __global__ void k_init(KParams k, const StepState* __restrict__ ss, const float* __restrict__ in,
-                       int have_p, float* __restrict__ pops, float* __restrict__ h,
-                       float* __restrict__ hist) {
+                       int have_p, Pops pops, float* __restrict__ h, float* __restrict__ hist) {
   const int N = k.N;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= N) return;
@@ -115,16 +115,13 @@ __global__ void k_init(KParams k, const StepState* __restrict__ ss, const float*
   const float mu = k.beta4 * phi * (phi - 0.5f) * (phi - 1.0f) - k.kappa * lap;
   const float rho = k.rho_v + k.drho * phi;
   const float uu = ux * ux + uy * uy;
-  float* g = pops;
-  float* l = pops + 9 * (size_t)N;
-  float* f = pops + 18 * (size_t)N;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const float cu = cx(i) * ux + cy(i) * uy;
     const float si = wgt(i) * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
-    g[i * (size_t)N + idx] = i == 0 ? phi - (1.0f - wgt(0)) * mu : wgt(i) * mu;
-    l[i * (size_t)N + idx] = wgt(i) * q * (1.0f + 3.0f * cu);
-    f[i * (size_t)N + idx] = (i == 0 ? (wgt(0) - 1.0f) : wgt(i)) * 3.0f * p + rho * si;
+    st_pop<HALF>(k, pops, 0, i, idx, i == 0 ? phi - (1.0f - wgt(0)) * mu : wgt(i) * mu);
+    st_pop<HALF>(k, pops, 1, i, idx, wgt(i) * q * (1.0f + 3.0f * cu));
+    st_pop<HALF>(k, pops, 2, i, idx, (i == 0 ? (wgt(0) - 1.0f) : wgt(i)) * 3.0f * p + rho * si);
   }
   // potential at equilibrium with the linear wall interpolation (0 when periodic)
   float vlin = 0.0f;
@@ -145,8 +142,9 @@ __global__ void k_step_set(KParams k, StepState* ss, long long n, int first) {
 // (Eq. weq62 with the lagged R of Algorithm 1).  Writes phi and the per-node potential
 // coefficients; FP64 sums of phi and q; the last CTA resets the potential loop.
 // ------------------------------------------------------------------------------------
+template <bool HALF>
 __global__ void __launch_bounds__(256) k_moments(KParams k, const StepState* __restrict__ ss,
-                                                 const float* __restrict__ pops,
+                                                 Pops pops,
                                                  const float* __restrict__ hist,
                                                  float* __restrict__ phi_out,
                                                  float2* __restrict__ aq,
@@ -158,12 +156,10 @@ __global__ void __launch_bounds__(256) k_moments(KParams k, const StepState* __r
   float phi = 0.0f, q = 0.0f;
   int bad = 0;
   if (idx < N) {
-    const float* g = pops;
-    const float* l = pops + 9 * (size_t)N;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      phi += __ldg(g + i * (size_t)N + idx);
-      q += __ldg(l + i * (size_t)N + idx);
+      phi += ld_pop<HALF>(k, pops, 0, i, idx);
+      q += ld_pop<HALF>(k, pops, 1, i, idx);
     }
     q += 0.5f * __ldg(hist + 3 * (size_t)N + idx);
     const float eh = eps_hat_of(k, phi);
@@ -241,9 +237,9 @@ __global__ void __launch_bounds__(256) k_moments(KParams k, const StepState* __r
 // g (Eq. weq45), l (Eq. weq58) and f (Eq. weq38) and the push to the neighbours with
 // half-way bounce-back; history for the next step.
 // ------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_coupled(KParams k, StepState* ss, int cur,
-                                                 const float* __restrict__ pin,
-                                                 float* __restrict__ pout,
+template <bool HALF>
+__global__ void __launch_bounds__(128) k_coupled(KParams k, StepState* ss, int cur, Pops pin,
+                                                 Pops pout,
                                                  const float* __restrict__ phi_f,
                                                  const float* __restrict__ hbuf,
                                                  float* __restrict__ hist, const Ctl* ctl,
@@ -280,14 +276,11 @@ __global__ void __launch_bounds__(128) k_coupled(KParams k, StepState* ss, int c
 
   // populations at this node (post-stream)
   float g[9], l[9], f[9];
-  const float* gp = pin;
-  const float* lp = pin + 9 * (size_t)N;
-  const float* fp = pin + 18 * (size_t)N;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    g[i] = __ldg(gp + i * (size_t)N + idx);
-    l[i] = __ldg(lp + i * (size_t)N + idx);
-    f[i] = __ldg(fp + i * (size_t)N + idx);
+    g[i] = ld_pop<HALF>(k, pin, 0, i, idx);
+    l[i] = ld_pop<HALF>(k, pin, 1, i, idx);
+    f[i] = ld_pop<HALF>(k, pin, 2, i, idx);
   }
   float hv[8];
 #pragma unroll
@@ -356,9 +349,6 @@ __global__ void __launch_bounds__(128) k_coupled(KParams k, StepState* ss, int c
   const float djx = 3.0f * (Jx - jx_prev), djy = 3.0f * (Jy - jy_prev);
   const float grx = k.drho * gphx, gry = k.drho * gphy;
 
-  float* go = pout;
-  float* lo = pout + 9 * (size_t)N;
-  float* fo = pout + 18 * (size_t)N;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const float w = wgt(i);
@@ -378,9 +368,9 @@ __global__ void __launch_bounds__(128) k_coupled(KParams k, StepState* ss, int c
     const float fn = f[i] - om_f * (f[i] - feq) + pref_f * w * 3.0f * (cF + cu * cg);
     int dir;
     const int t = push_target(k, x, y, i, dir);
-    go[dir * (size_t)N + t] = gn;
-    lo[dir * (size_t)N + t] = ln;
-    fo[dir * (size_t)N + t] = fn;
+    st_pop<HALF>(k, pout, 0, dir, t, gn);
+    st_pop<HALF>(k, pout, 1, dir, t, ln);
+    st_pop<HALF>(k, pout, 2, dir, t, fn);
   }
   hist[idx] = s_adv;
   hist[(size_t)N + idx] = Jx;
@@ -407,16 +397,18 @@ __global__ void k_stats_reset(DevStats* s) {
 // Output fields.  k_phi_now: phi of the current populations; k_fields: the requested
 // fields (order of the mask bits) into io[slot][N].
 // ------------------------------------------------------------------------------------
-__global__ void k_phi_now(KParams k, const float* __restrict__ pops, float* __restrict__ out) {
+template <bool HALF>
+__global__ void k_phi_now(KParams k, Pops pops, float* __restrict__ out) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= k.N) return;
   float s = 0.0f;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) s += __ldg(pops + i * (size_t)k.N + idx);
+  for (int i = 0; i < 9; ++i) s += ld_pop<HALF>(k, pops, 0, i, idx);
   out[idx] = s;
 }
 
-__global__ void k_fields(KParams k, const StepState* __restrict__ ss, const float* __restrict__ pops,
+template <bool HALF>
+__global__ void k_fields(KParams k, const StepState* __restrict__ ss, Pops pops,
                          const float* __restrict__ phi_now, const float* __restrict__ phi_solve,
                          const float* __restrict__ hbuf, const float* __restrict__ hist,
                          const Ctl* ctl, unsigned mask, float* __restrict__ io) {
@@ -432,12 +424,10 @@ __global__ void k_fields(KParams k, const StepState* __restrict__ ss, const floa
   grad_lap(st, gphx, gphy, lap);
   const float phi = st.c;
   float lsum = 0.0f, mx = 0.0f, my = 0.0f, fsum_nr = 0.0f;
-  const float* l = pops + 9 * (size_t)N;
-  const float* f = pops + 18 * (size_t)N;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const float fi = __ldg(f + i * (size_t)N + idx);
-    lsum += __ldg(l + i * (size_t)N + idx);
+    const float fi = ld_pop<HALF>(k, pops, 2, i, idx);
+    lsum += ld_pop<HALF>(k, pops, 1, i, idx);
     mx += cx(i) * fi;
     my += cy(i) * fi;
     if (i) fsum_nr += fi;
@@ -484,9 +474,13 @@ cudaError_t launch_step_set(const KParams& kp, const Buffers& b, int slot, long 
 
 cudaError_t launch_init(const KParams& kp, const Buffers& b, int cur, bool have_p,
                         cudaStream_t st) {
-  k_init<<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, b.ss + cur, b.io, have_p ? 1 : 0,
-                                                b.pops + (size_t)cur * NPOP * kp.N, b.h,
-                                                b.hist);
+  const Pops P = pops_copy(kp, b, cur);
+  if (kp.half)
+    k_init<true><<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, b.ss + cur, b.io, have_p ? 1 : 0, P,
+                                                       b.h, b.hist);
+  else
+    k_init<false><<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, b.ss + cur, b.io, have_p ? 1 : 0,
+                                                        P, b.h, b.hist);
   return cudaGetLastError();
 }
 
@@ -494,16 +488,24 @@ cudaError_t launch_moments(const KParams& kp, const Buffers& b, int cur, double 
                            int min_iter, int max_iter, int fixed_iter, cudaStream_t st) {
   const int nb = blocks_for(kp.N, 256);
   if (nb > MAX_PARTIALS) return cudaErrorInvalidValue;
-  k_moments<<<nb, 256, 0, st>>>(kp, b.ss + cur, b.pops + (size_t)cur * NPOP * kp.N, b.hist,
-                                b.phi, b.aq, b.partials, b.ctl, tol, min_iter, max_iter,
-                                fixed_iter);
+  const Pops P = pops_copy(kp, b, cur);
+  if (kp.half)
+    k_moments<true><<<nb, 256, 0, st>>>(kp, b.ss + cur, P, b.hist, b.phi, b.aq, b.partials,
+                                        b.ctl, tol, min_iter, max_iter, fixed_iter);
+  else
+    k_moments<false><<<nb, 256, 0, st>>>(kp, b.ss + cur, P, b.hist, b.phi, b.aq, b.partials,
+                                         b.ctl, tol, min_iter, max_iter, fixed_iter);
   return cudaGetLastError();
 }
 
 cudaError_t launch_coupled(const KParams& kp, const Buffers& b, int cur, cudaStream_t st) {
-  k_coupled<<<blocks_for(kp.N, 128), 128, 0, st>>>(
-      kp, b.ss, cur, b.pops + (size_t)cur * NPOP * kp.N,
-      b.pops + (size_t)(cur ^ 1) * NPOP * kp.N, b.phi, b.h, b.hist, b.ctl, b.stats);
+  const Pops Pi = pops_copy(kp, b, cur), Po = pops_copy(kp, b, cur ^ 1);
+  if (kp.half)
+    k_coupled<true><<<blocks_for(kp.N, 128), 128, 0, st>>>(kp, b.ss, cur, Pi, Po, b.phi, b.h,
+                                                           b.hist, b.ctl, b.stats);
+  else
+    k_coupled<false><<<blocks_for(kp.N, 128), 128, 0, st>>>(kp, b.ss, cur, Pi, Po, b.phi, b.h,
+                                                            b.hist, b.ctl, b.stats);
   return cudaGetLastError();
 }
 
@@ -514,10 +516,16 @@ cudaError_t launch_stats_reset(const Buffers& b, cudaStream_t st) {
 
 cudaError_t launch_fields(const KParams& kp, const Buffers& b, int cur, unsigned mask,
                           cudaStream_t st) {
-  const float* pops = b.pops + (size_t)cur * NPOP * kp.N;
-  k_phi_now<<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, pops, b.tmp);
-  k_fields<<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, b.ss + cur, pops, b.tmp, b.phi, b.h,
-                                                  b.hist, b.ctl, mask, b.io);
+  const Pops P = pops_copy(kp, b, cur);
+  if (kp.half) {
+    k_phi_now<true><<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, P, b.tmp);
+    k_fields<true><<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, b.ss + cur, P, b.tmp, b.phi, b.h,
+                                                          b.hist, b.ctl, mask, b.io);
+  } else {
+    k_phi_now<false><<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, P, b.tmp);
+    k_fields<false><<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, b.ss + cur, P, b.tmp, b.phi,
+                                                           b.h, b.hist, b.ctl, mask, b.io);
+  }
   return cudaGetLastError();
 }
 
@@ -527,7 +535,7 @@ cudaError_t add_moments_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t 
                              double tol, int min_iter, int max_iter, int fixed_iter) {
   KParams k = kp;
   const StepState* ss = b.ss + cur;
-  const float* pops = b.pops + (size_t)cur * NPOP * kp.N;
+  Pops pops = pops_copy(kp, b, cur);
   const float* hist = b.hist;
   float* phi = b.phi;
   float2* aq = b.aq;
@@ -536,7 +544,7 @@ cudaError_t add_moments_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t 
   void* args[] = {&k, &ss, &pops, &hist, &phi, &aq, &partials, &ctl, &tol, &min_iter, &max_iter,
                   &fixed_iter};
   cudaKernelNodeParams p = {};
-  p.func = (void*)k_moments;
+  p.func = kp.half ? (void*)k_moments<true> : (void*)k_moments<false>;
   p.gridDim = dim3(blocks_for(kp.N, 256));
   p.blockDim = dim3(256);
   p.kernelParams = args;
@@ -547,8 +555,8 @@ cudaError_t add_coupled_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t 
                              cudaGraphNode_t* out, const KParams& kp, const Buffers& b, int cur) {
   KParams k = kp;
   StepState* ss = b.ss;
-  const float* pin = b.pops + (size_t)cur * NPOP * kp.N;
-  float* pout = b.pops + (size_t)(cur ^ 1) * NPOP * kp.N;
+  Pops pin = pops_copy(kp, b, cur);
+  Pops pout = pops_copy(kp, b, cur ^ 1);
   const float* phi = b.phi;
   const float* h = b.h;
   float* hist = b.hist;
@@ -556,7 +564,7 @@ cudaError_t add_coupled_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t 
   DevStats* stats = b.stats;
   void* args[] = {&k, &ss, &cur, &pin, &pout, &phi, &h, &hist, &ctl, &stats};
   cudaKernelNodeParams p = {};
-  p.func = (void*)k_coupled;
+  p.func = kp.half ? (void*)k_coupled<true> : (void*)k_coupled<false>;
   p.gridDim = dim3(blocks_for(kp.N, 128));
   p.blockDim = dim3(128);
   p.kernelParams = args;

@@ -67,10 +67,6 @@ __device__ __forceinline__ bool grid_barrier(Ctl* sync, unsigned nblocks, unsign
   return s_ok != 0;
 }
 
-struct TileGeom {
-  int tx0, ty0, tw, th;  // origin and size of this tile
-};
-
 __device__ __forceinline__ int perim_slot(int lx, int ly, int w, int h) {
   if (ly == 0) return lx;
   if (ly == h - 1) return w + lx;
@@ -78,27 +74,39 @@ __device__ __forceinline__ int perim_slot(int lx, int ly, int w, int h) {
   return 2 * w + h + ly;  // lx == w - 1
 }
 
+// Tile width is fixed: node j of a tile sits at (j & 63, j >> 6).  Shared memory holds
+// the post-collision populations of the tile plus a one-node ring: [8][RY][RX].
+constexpr int TXR = 64;
+constexpr int RX = TXR + 2;
+
+// One of the 3 x 3 tiles around (and including) this one.
+struct Nb {
+  int id;      // tile index, -1 beyond a wall
+  int w, h;    // its size
+};
+
 }  // namespace
 
 __global__ void __launch_bounds__(MAX_THREADS, 1)
     k_poisson_resident(KParams k, ResidentGeom rg, float* __restrict__ hbuf,
                        const float2* __restrict__ aq, float* __restrict__ exports,
                        double2* __restrict__ rpartials, Ctl* ctl) {
-  extern __shared__ float hs[];  // [8][tile nodes] post-collision, then [2][tile nodes] (a, q)
+  extern __shared__ float sm[];  // [8][RY][RX] populations, then [TY*64] a, [TY*64] q
   __shared__ double s_w[MAX_THREADS / 32][2];
   __shared__ double s_tot[2];
+  __shared__ Nb s_nb[3][3];
 
   const int nx = k.nx, ny = k.ny;
   const size_t N = (size_t)k.N;
   const int ntiles = gridDim.x;
   const int tile = blockIdx.x;
   const int tcol = tile % rg.ntx, trow = tile / rg.ntx;
-  TileGeom tg;
-  tg.tx0 = tcol * rg.TX;
-  tg.ty0 = trow * rg.TY;
-  tg.tw = min(rg.TX, nx - tg.tx0);
-  tg.th = min(rg.TY, ny - tg.ty0);
-  const int tn = tg.tw * tg.th;
+  const int tx0 = tcol * TXR, ty0 = trow * rg.TY;
+  const int tw = min(TXR, nx - tx0), th = min(rg.TY, ny - ty0);
+  const int RY = rg.TY + 2;
+  const int plane = RY * RX;
+  float* ca = sm + 8 * plane;
+  float* cq = ca + rg.TY * TXR;
   const int parity = ld_cg(&ctl->parity);
   float* __restrict__ hsrc = hbuf + (size_t)parity * NH * N;
   const float qshift = k.neutralize ? ld_cg(&ctl->mean_q) : 0.0f;
@@ -106,19 +114,40 @@ __global__ void __launch_bounds__(MAX_THREADS, 1)
   const double tol = ctl->tol;
   const int min_iter = ctl->min_iter, max_iter = ctl->max_iter, fixed = ctl->fixed_iter;
   const float om = k.omega_h;
-  const int pstride = 8 * rg.pmax;  // floats per tile and parity in the export area
+  const int pstride = 8 * rg.pmax;
+  const int tnodes = TXR * th;  // node slots j < tnodes (lx < tw valid)
 
-  float* ca = hs + 8 * tn;   // forcing coefficient a per node
-  float* cq = ca + tn;       // source q (minus the neutralising shift) per node
+  if (threadIdx.x < 9) {
+    const int dx = (int)threadIdx.x % 3 - 1, dy = (int)threadIdx.x / 3 - 1;
+    const int c = (tcol + dx + rg.ntx) % rg.ntx;
+    int r = trow + dy;
+    Nb nb;
+    if (r < 0 || r >= rg.nty) {
+      if (k.walls) {
+        nb.id = -1;
+        nb.w = nb.h = 0;
+        s_nb[dy + 1][dx + 1] = nb;
+        r = -1;
+      } else {
+        r = (r + rg.nty) % rg.nty;
+      }
+    }
+    if (r >= 0) {
+      nb.id = r * rg.ntx + c;
+      nb.w = min(TXR, nx - c * TXR);
+      nb.h = min(rg.TY, ny - r * rg.TY);
+      s_nb[dy + 1][dx + 1] = nb;
+    }
+  }
 
-  // load the state of my nodes
+  // state of my nodes: registers; coefficients: shared memory
   float h[NPT][8];
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
     const int j = threadIdx.x + s * blockDim.x;
-    if (j < tn) {
-      const int ly = j / tg.tw, lx = j - ly * tg.tw;
-      const int g = (tg.ty0 + ly) * nx + tg.tx0 + lx;
+    const int lx = j & (TXR - 1), ly = j >> 6;
+    if (j < tnodes && lx < tw) {
+      const int g = (ty0 + ly) * nx + tx0 + lx;
 #pragma unroll
       for (int i = 0; i < 8; ++i) h[s][i] = hsrc[i * N + g];
       const float2 c = aq[g];
@@ -129,18 +158,20 @@ __global__ void __launch_bounds__(MAX_THREADS, 1)
       for (int i = 0; i < 8; ++i) h[s][i] = 0.0f;
     }
   }
+  __syncthreads();
 
   unsigned gen = ld_cg(&ctl->bar_gen);
   int it = 0;
   double rel = 0.0;
   int conv = 0;
   for (;;) {
-    // 1. collide
+    // 1. collide into the tile's shared populations; perimeter nodes also export
     float* exp_cur = exports + (size_t)(it & 1) * ntiles * pstride + (size_t)tile * pstride;
 #pragma unroll
     for (int s = 0; s < NPT; ++s) {
       const int j = threadIdx.x + s * blockDim.x;
-      if (j >= tn) continue;
+      const int lx = j & (TXR - 1), ly = j >> 6;
+      if (j >= tnodes || lx >= tw) continue;
       float hsum = 0.0f;
 #pragma unroll
       for (int i = 0; i < 8; ++i) hsum += h[s][i];
@@ -149,38 +180,38 @@ __global__ void __launch_bounds__(MAX_THREADS, 1)
       const float m1y = h[s][1] - h[s][3] + h[s][4] + h[s][5] - h[s][6] - h[s][7];
       const float qs = 0.125f * cq[j];
       const float a = ca[j];
-      const int ly = j / tg.tw, lx = j - ly * tg.tw;
-      const bool perim = lx == 0 || ly == 0 || lx == tg.tw - 1 || ly == tg.th - 1;
-      const int slot = perim ? perim_slot(lx, ly, tg.tw, tg.th) : 0;
+      const int at = (ly + 1) * RX + lx + 1;
+      const bool perim = lx == 0 || ly == 0 || lx == tw - 1 || ly == th - 1;
+      const int slot = perim ? perim_slot(lx, ly, tw, th) : 0;
 #pragma unroll
       for (int i = 1; i < 9; ++i) {
         const float w = wgt(i);
         const float cm = cx(i) * m1x + cy(i) * m1y;
         const float v = h[s][i - 1] - om * (h[s][i - 1] - w * varphi) + a * w * cm + qs;
-        hs[(i - 1) * tn + j] = v;
+        sm[(i - 1) * plane + at] = v;
         if (perim) exp_cur[(i - 1) * rg.pmax + slot] = v;
       }
     }
-    // 2. all tiles' post-collision populations are visible
+    // 2. all tiles' exports are visible
     if (!grid_barrier(ctl, ntiles, gen)) return;
     // 3. stopping decision on the previous sub-iteration's sums
     if (it > 0) {
       if (threadIdx.x < 32) {
         const double2* pp = rpartials + (size_t)((it - 1) & 1) * ntiles;
-        double a = 0.0, b = 0.0;
+        double sa = 0.0, sb = 0.0;
         for (int t = threadIdx.x; t < ntiles; t += 32) {
           const double2 v = __ldcg(pp + t);
-          a += v.x;
-          b += v.y;
+          sa += v.x;
+          sb += v.y;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(0xffffffffu, a, o);
-          b += __shfl_xor_sync(0xffffffffu, b, o);
+          sa += __shfl_xor_sync(0xffffffffu, sa, o);
+          sb += __shfl_xor_sync(0xffffffffu, sb, o);
         }
         if (threadIdx.x == 0) {
-          s_tot[0] = a;
-          s_tot[1] = b;
+          s_tot[0] = sa;
+          s_tot[1] = sb;
         }
       }
       __syncthreads();
@@ -201,42 +232,65 @@ __global__ void __launch_bounds__(MAX_THREADS, 1)
       }
       if (done) break;
     }
-    // 4. stream into my nodes
-    const float* exp_all = exports + (size_t)(it & 1) * ntiles * pstride;
+    // 4a. ring: for every boundary node and direction whose source lies outside the tile,
+    // put the source value where the uniform gather will read it
+    {
+      const float* exp_all = exports + (size_t)(it & 1) * ntiles * pstride;
+      const int nring = 6 * (tw + th);
+      for (int e = threadIdx.x; e < nring; e += blockDim.x) {
+        int lx, ly, i;
+        if (e < 3 * th) {                 // west boundary, directions with cx = +1
+          ly = e / 3; lx = 0;
+          const int kk = e - 3 * ly;
+          i = kk == 0 ? 1 : (kk == 1 ? 5 : 8);
+        } else if (e < 6 * th) {          // east boundary, cx = -1
+          const int f = e - 3 * th;
+          ly = f / 3; lx = tw - 1;
+          const int kk = f - 3 * ly;
+          i = kk == 0 ? 3 : (kk == 1 ? 6 : 7);
+        } else if (e < 6 * th + 3 * tw) { // south boundary, cy = +1
+          const int f = e - 6 * th;
+          lx = f / 3; ly = 0;
+          const int kk = f - 3 * lx;
+          i = kk == 0 ? 2 : (kk == 1 ? 5 : 6);
+        } else {                          // north boundary, cy = -1
+          const int f = e - 6 * th - 3 * tw;
+          lx = f / 3; ly = th - 1;
+          const int kk = f - 3 * lx;
+          i = kk == 0 ? 4 : (kk == 1 ? 7 : 8);
+        }
+        const int sxl = lx - cx(i), syl = ly - cy(i);
+        if (sxl >= 0 && sxl < tw && syl >= 0 && syl < th) continue;  // inside the tile
+        const int nbx = sxl < 0 ? 0 : (sxl >= tw ? 2 : 1);
+        const int nby = syl < 0 ? 0 : (syl >= th ? 2 : 1);
+        const Nb nb = s_nb[nby][nbx];
+        float v;
+        if (nb.id < 0) {
+          // beyond a wall: anti-bounce-back on the consuming node's own population
+          const float vw = nby == 0 ? vw_b : vw_t;
+          v = -sm[(opp(i) - 1) * plane + (ly + 1) * RX + lx + 1] + 2.0f * wgt(i) * vw;
+        } else {
+          const int olx = nbx == 0 ? nb.w - 1 : (nbx == 2 ? 0 : sxl);
+          const int oly = nby == 0 ? nb.h - 1 : (nby == 2 ? 0 : syl);
+          v = __ldcg(exp_all + (size_t)nb.id * pstride + (i - 1) * rg.pmax +
+                     perim_slot(olx, oly, nb.w, nb.h));
+        }
+        sm[(i - 1) * plane + (syl + 1) * RX + sxl + 1] = v;
+      }
+    }
+    __syncthreads();
+    // 4b. stream: every source is now in shared memory
     float num = 0.0f, den = 0.0f;
 #pragma unroll
     for (int s = 0; s < NPT; ++s) {
       const int j = threadIdx.x + s * blockDim.x;
-      if (j >= tn) continue;
-      const int ly = j / tg.tw, lx = j - ly * tg.tw;
-      const int gx = tg.tx0 + lx, gy = tg.ty0 + ly;
+      const int lx = j & (TXR - 1), ly = j >> 6;
+      if (j >= tnodes || lx >= tw) continue;
+      const int at = (ly + 1) * RX + lx + 1;
       float vold = 0.0f, vnew = 0.0f;
 #pragma unroll
       for (int i = 1; i < 9; ++i) {
-        const int sxl = lx - cx(i), syl = ly - cy(i);
-        float v;
-        if (sxl >= 0 && sxl < tg.tw && syl >= 0 && syl < tg.th) {
-          v = hs[(i - 1) * tn + syl * tg.tw + sxl];
-        } else {
-          int sy = gy - cy(i);
-          if (k.walls && (sy < 0 || sy >= ny)) {
-            const float vw = sy < 0 ? vw_b : vw_t;
-            v = -hs[(opp(i) - 1) * tn + j] + 2.0f * wgt(i) * vw;
-          } else {
-            sy = wrap(sy, ny);
-            const int sx = wrap(gx - cx(i), nx);
-            const int otc = sx / rg.TX, otr = sy / rg.TY;
-            const int ox0 = otc * rg.TX, oy0 = otr * rg.TY;
-            const int ow = min(rg.TX, nx - ox0), oh = min(rg.TY, ny - oy0);
-            const int ot = otr * rg.ntx + otc;
-            if (ot == tile) {
-              v = hs[(i - 1) * tn + (sy - oy0) * ow + (sx - ox0)];
-            } else {
-              const int sl = perim_slot(sx - ox0, sy - oy0, ow, oh);
-              v = __ldcg(exp_all + (size_t)ot * pstride + (i - 1) * rg.pmax + sl);
-            }
-          }
-        }
+        const float v = sm[(i - 1) * plane + at - cy(i) * RX - cx(i)];
         vold += h[s][i - 1];
         h[s][i - 1] = v;
         vnew += v;
@@ -258,12 +312,12 @@ __global__ void __launch_bounds__(MAX_THREADS, 1)
     }
     __syncthreads();  // shared populations consumed; warp sums visible
     if (threadIdx.x == 0) {
-      double a = 0.0, b = 0.0;
+      double sa = 0.0, sb = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        a += s_w[w][0];
-        b += s_w[w][1];
+        sa += s_w[w][0];
+        sb += s_w[w][1];
       }
-      rpartials[(size_t)(it & 1) * ntiles + tile] = make_double2(a, b);
+      rpartials[(size_t)(it & 1) * ntiles + tile] = make_double2(sa, sb);
     }
     ++it;
   }
@@ -272,9 +326,9 @@ __global__ void __launch_bounds__(MAX_THREADS, 1)
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
     const int j = threadIdx.x + s * blockDim.x;
-    if (j >= tn) continue;
-    const int ly = j / tg.tw, lx = j - ly * tg.tw;
-    const int g = (tg.ty0 + ly) * nx + tg.tx0 + lx;
+    const int lx = j & (TXR - 1), ly = j >> 6;
+    if (j >= tnodes || lx >= tw) continue;
+    const int g = (ty0 + ly) * nx + tx0 + lx;
 #pragma unroll
     for (int i = 0; i < 8; ++i) hsrc[i * N + g] = h[s][i];
   }
@@ -290,30 +344,27 @@ __global__ void __launch_bounds__(MAX_THREADS, 1)
 // one tile per SM.
 bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* threads,
                        size_t* smem) {
-  const int max_nodes = NPT * MAX_THREADS;
   const long long N = (long long)kp.nx * kp.ny;
-  const int TX = kp.nx < 64 ? kp.nx : 64;
-  const int ntx = (kp.nx + TX - 1) / TX;
+  const int ntx = (kp.nx + TXR - 1) / TXR;
   if (ntx > num_sms) return false;
-  // about 2048 nodes per tile, never more tiles than SMs
+  // about 2048 nodes per tile, never more tiles than SMs, tiles at most 64 x 64
   long long want = (N + 2047) / 2048;
   if (want > num_sms) want = num_sms;
   int nty = (int)(want / ntx);
   if (nty < 1) nty = 1;
   if (nty > num_sms / ntx) nty = num_sms / ntx;
   int TY = (kp.ny + nty - 1) / nty;
-  if ((long long)TX * TY > max_nodes) return false;
+  if (TY > TXR) return false;
   nty = (kp.ny + TY - 1) / TY;
-  g->TX = TX;
+  g->TX = TXR;
   g->TY = TY;
   g->ntx = ntx;
   g->nty = nty;
-  g->pmax = 2 * TX + 2 * TY;
-  const int tn = TX * TY;
-  int t = (tn + NPT - 1) / NPT;
+  g->pmax = 2 * TXR + 2 * TY;
+  int t = (TXR * TY + NPT - 1) / NPT;
   t = (t + 31) / 32 * 32;
   *threads = t < 32 ? 32 : t;
-  *smem = sizeof(float) * 10 * (size_t)tn;
+  *smem = sizeof(float) * (8 * (size_t)(TY + 2) * RX + 2 * (size_t)TY * TXR);
   return true;
 }
 

@@ -63,6 +63,7 @@ def test_strings_and_workspace_size(L):
 @pytest.mark.parametrize("change,code", [
     (dict(nx=0), 1),
     (dict(precision=7), 1),
+    (dict(poisson_loop=5), 1),
     (dict(mobility=1e-4), 2),          # tau_g too close to 1/2
     (dict(mu_v=1e-5), 2),              # tau_f too close to 1/2
     (dict(sigma_v=0.9, eps_v=1.0), 2), # sigma/eps above 0.5
