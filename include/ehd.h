@@ -40,7 +40,9 @@ typedef enum ehd_status {
   EHD_ERR_NOT_CONVERGED = 4,   /* a potential loop hit poisson_max_iter (state advanced)*/
   EHD_ERR_NONFINITE = 5,       /* NaN or Inf in phi or q (state advanced)               */
   EHD_ERR_BUSY = 6,            /* batch: no free slot or memory for a request           */
-  EHD_ERR_CUDA = 7             /* a CUDA runtime call failed                            */
+  EHD_ERR_CUDA = 7,            /* a CUDA runtime call failed                            */
+  EHD_ERR_TOO_LARGE = 8        /* lattice exceeds the fixed scratch of the no-allocation
+                                  potential solve                                         */
 } ehd_status;
 
 enum { EHD_HOST = 0, EHD_DEVICE = 1 };
@@ -196,6 +198,31 @@ int ehd_load_state(ehd_sim* sim, const void* buf, size_t bytes);
  * totals since profiling was turned on. */
 int ehd_profile(ehd_sim* sim, int enable);
 int ehd_profile_read(ehd_sim* sim, ehd_kernel_times* out);
+
+/* Potential solve that allocates nothing, for callers that cannot allocate device
+ * memory: code held to a device-memory budget by someone else, callers that carve every
+ * buffer out of their own pool up front, or plug-ins running in a process whose
+ * allocator they do not own.  It needs no ehd_sim; it runs the potential sub-iteration
+ * loop (the library's streaming potential kernel's arithmetic, the parameters' stopping
+ * rule or fixed count) for the given phi and q and returns the converged populations.
+ * The paper has no counterpart: it is a deployment variant of the solve, not a step of
+ * the method.
+ *   params   lattice, permittivities, walls, wall potentials (ramp fraction at
+ *            start_step), neutralize_charge and the potential-loop rule;
+ *   phi, q   device float32 [ny][nx], read only;
+ *   h        device float32 [8][ny][nx]: h_1..h_8 in, the solved populations out;
+ *   h_work   device float32 [8][ny][nx], overwritten (the loop alternates between the two);
+ *   stream   cudaStream_t (NULL: default stream); the call synchronises it.
+ * Its only scratch (per-CTA FP64 partial sums and the loop control) is a fixed device
+ * array inside the library: lattices of at most 2,097,152 nodes (4096 tiles of 32 x 16)
+ * are accepted, larger ones return EHD_ERR_TOO_LARGE.  The first call on each device
+ * looks the array up (with that device current) and should come before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller.  No cudaMalloc, cudaFree or other allocating routine is
+ * called. */
+int ehd_potential_solve_noalloc(const ehd_params* params, const float* phi, const float* q,
+                                float* h, float* h_work, void* stream, int* iters,
+                                double* rel_change);
 
 /* Releases the simulation (and its workspace if the library allocated it). */
 void ehd_destroy(ehd_sim* sim);

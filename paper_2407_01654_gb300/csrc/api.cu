@@ -396,6 +396,7 @@ const char* ehd_error_string(int code) {
     case EHD_ERR_NONFINITE: return "non-finite values in phi or q";
     case EHD_ERR_BUSY: return "no free slot or memory";
     case EHD_ERR_CUDA: return "CUDA runtime error";
+    case EHD_ERR_TOO_LARGE: return "lattice exceeds the fixed scratch of the no-allocation solve";
     default: return "unknown status";
   }
 }

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libehd.so")
 EHD_OK = 0
 STATUS = {0: "EHD_OK", 1: "EHD_ERR_INVALID_ARG", 2: "EHD_ERR_UNSTABLE_PARAMS",
           3: "EHD_ERR_NOMEM", 4: "EHD_ERR_NOT_CONVERGED", 5: "EHD_ERR_NONFINITE",
-          6: "EHD_ERR_BUSY", 7: "EHD_ERR_CUDA"}
+          6: "EHD_ERR_BUSY", 7: "EHD_ERR_CUDA", 8: "EHD_ERR_TOO_LARGE"}
 EHD_HOST, EHD_DEVICE = 0, 1
 FIELDS = ("phi", "q", "varphi", "Ex", "Ey", "ux", "uy", "p")
 
@@ -106,6 +106,11 @@ SIGNATURES = {
     "ehd_abi_sizes": (ctypes.c_int, [ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.POINTER(ctypes.c_size_t)]),
     "ehd_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "ehd_potential_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.POINTER(ctypes.c_int),
+                                                   ctypes.POINTER(ctypes.c_double)]),
     "ehd_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(KernelTimes)]),
 }
 

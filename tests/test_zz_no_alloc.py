@@ -1,0 +1,102 @@
+"""The no-allocation potential solve, for callers that cannot allocate device memory
+(ehd_potential_solve_noalloc), against the library's regular potential solve
+(ehd_set_fields runs one) on the same inputs, twice in a row through the C ABI.
+
+Collected last on purpose; it needs no other test and no state from them."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2407_01654_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+W = np.array([1 / 9] * 4 + [1 / 36] * 4)  # weights of h_1..h_8
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_01654_gb300 import build
+    build.build()
+    from paper_2407_01654_gb300 import ehd
+    return torch, ehd
+
+
+def case(seed, nx, ny, walls):
+    rng = np.random.default_rng(seed)
+    p = wl.make_params(nx=nx, ny=ny, walls_y=walls, eps_v=1.0, eps_l=15.0, sigma_v=0.01,
+                       sigma_l=0.001, alpha=0.05, varphi_bottom=0.3 * walls,
+                       varphi_top=-0.1 * walls, neutralize_charge=1 - walls,
+                       poisson_fixed_iter=60)
+    y, x = np.meshgrid(np.arange(ny, dtype=float), np.arange(nx, dtype=float), indexing="ij")
+    phi = wl.tanh_profile(0.3 * min(nx, ny) - np.hypot(x - 0.4 * nx, y - 0.6 * ny), 4.0)
+    q = wl.smooth_random_field(nx, ny, rng, 1e-3, periodic_y=not walls)
+    return p, phi, q
+
+
+def regular_solve(ehd, p, phi, q):
+    z = np.zeros_like(phi)
+    sim = ehd.Sim(p)
+    sim.set_fields(phi, q, z, z)
+    out = sim.read_fields(("varphi",))["varphi"]
+    sim.close()
+    return out
+
+
+def noalloc_solve(torch, ehd, p, phi, q):
+    ny, nx = phi.shape
+    # initial populations as the regular solve sets them: equilibrium of the potential
+    # interpolated linearly between the walls (0 when y is periodic)
+    if p["walls_y"]:
+        lin = p["varphi_bottom"] + (p["varphi_top"] - p["varphi_bottom"]) * (np.arange(ny) + 0.5) / ny
+    else:
+        lin = np.zeros(ny)
+    h0 = W[:, None, None] * np.repeat(lin[:, None], nx, axis=1)[None]
+    dev = dict(dtype=torch.float32, device="cuda")
+    h = torch.tensor(h0, **dev).contiguous()
+    hw = torch.empty_like(h)
+    tphi = torch.tensor(phi, **dev)
+    tq = torch.tensor(q, **dev)
+    prm = ehd.Params.from_dict(p)
+    it, rel = ctypes.c_int(), ctypes.c_double()
+    stream = torch.cuda.current_stream().cuda_stream
+    code = ehd.lib().ehd_potential_solve_noalloc(ctypes.byref(prm), tphi.data_ptr(),
+                                                 tq.data_ptr(), h.data_ptr(), hw.data_ptr(),
+                                                 stream, ctypes.byref(it), ctypes.byref(rel))
+    assert code == 0, ehd.STATUS.get(code, code)
+    assert it.value == p["poisson_fixed_iter"]
+    return h.double().cpu().numpy().sum(axis=0) * (9.0 / 5.0)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_noalloc_matches_regular_solve_twice(env):
+    """Two calls in a row (walls with wall potentials, then a periodic lattice with a
+    neutralised source): each potential matches the regular solve within 1e-5."""
+    torch, ehd = env
+    for seed, (nx, ny, walls) in enumerate(((70, 45, 1), (66, 40, 0))):
+        p, phi, q = case(seed, nx, ny, walls)
+        ref = regular_solve(ehd, p, phi, q)
+        got = noalloc_solve(torch, ehd, p, phi, q)
+        assert rel_l2(got, ref) <= 1e-5
+
+
+def test_noalloc_rejects_oversized_lattice(env):
+    """Lattices beyond the fixed scratch (4096 tiles of 32 x 16) are refused before any
+    work is queued."""
+    torch, ehd = env
+    p = wl.make_params(nx=4096, ny=1024, poisson_fixed_iter=1)
+    prm = ehd.Params.from_dict(p)
+    it, rel = ctypes.c_int(), ctypes.c_double()
+    dummy = torch.empty(8, dtype=torch.float32, device="cuda")
+    code = ehd.lib().ehd_potential_solve_noalloc(ctypes.byref(prm), dummy.data_ptr(),
+                                                 dummy.data_ptr(), dummy.data_ptr(),
+                                                 dummy.data_ptr(), 0, ctypes.byref(it),
+                                                 ctypes.byref(rel))
+    assert code == 8
