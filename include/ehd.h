@@ -227,6 +227,65 @@ int ehd_potential_solve_noalloc(const ehd_params* params, const float* phi, cons
 /* Releases the simulation (and its workspace if the library allocated it). */
 void ehd_destroy(ehd_sim* sim);
 
+/* ---------------------------------------------------------------------------------------
+ * Serving: many simulations resident on one GPU, advanced together.
+ *
+ * A batch owns a device-memory arena of hbm_budget bytes (allocated by the library, or
+ * given by the caller as `arena`, 256-byte aligned).  Each admitted request is a slot: a
+ * simulation whose workspace is carved from the arena.  ehd_batch_run advances every live
+ * slot by nsteps coupled steps with one CUDA graph per step in which the potential loops of
+ * all slots share ONE cooperative launch (a tile work-list across slots); each slot keeps
+ * its own stopping rule and reaches exactly the state it would reach alone.  After the
+ * steps, each slot's relative L2 change of phi and of u since the previous run call is
+ * measured; a slot is steady when both are below steady_tol.  Requests that arrive while
+ * others run are admitted between run calls as slots and memory free up (continuous
+ * batching); the scheduling policy is the caller's.
+ * --------------------------------------------------------------------------------------- */
+typedef struct ehd_batch ehd_batch;
+
+typedef struct ehd_slot_status {
+  int32_t slot;
+  int32_t live;
+  int64_t request_id;        /* the caller's id given at admission                     */
+  int64_t steps;             /* steps made since admission                             */
+  int64_t poisson_iters;     /* potential sub-iterations since admission               */
+  int32_t steady;            /* 1: both relative changes below steady_tol              */
+  int32_t capped;            /* 1: steps reached the batch's step cap                  */
+  int32_t status;            /* status of the last run for this slot                   */
+  int32_t pad;
+  double rel_change_phi;     /* relative L2 change of phi over the last run call       */
+  double rel_change_u;       /* relative L2 change of u over the last run call (a flow
+                                slower than 1e-6 lattice units counts as rest)         */
+} ehd_slot_status;
+
+typedef struct ehd_batch_info_t {
+  int32_t live_slots, max_slots;
+  size_t arena_bytes, arena_used;
+  int32_t tiles_used, tile_capacity;  /* on-chip tiles of the shared potential launch   */
+  int64_t steps_run;
+  int64_t kernel_launches;            /* kernels launched by run calls                  */
+} ehd_batch_info_t;
+
+/* Creates a batch.  max_slots >= 1; hbm_budget >= 1 MiB; steady_tol > 0; step_cap >= 1.
+ * Errors: EHD_ERR_INVALID_ARG, EHD_ERR_NOMEM, EHD_ERR_CUDA (no cooperative launch). */
+int ehd_batch_create(size_t hbm_budget, int max_slots, double steady_tol, int64_t step_cap,
+                     void* arena, void* stream, ehd_batch** out);
+/* Admits a request (host double fields [ny][nx], as ehd_set_fields).  EHD_ERR_BUSY when no
+ * slot, arena space or on-chip tile capacity is free; the batch is then unchanged. */
+int ehd_batch_admit(ehd_batch* b, const ehd_params* params, const double* phi, const double* q,
+                    const double* ux, const double* uy, int64_t request_id, int* slot);
+/* Advances every live slot by nsteps steps, then measures steadiness and statistics
+ * (synchronises the stream). */
+int ehd_batch_run(ehd_batch* b, int nsteps);
+/* Status of the live slots: up to `max` entries into `out`, their number into *n. */
+int ehd_batch_poll(ehd_batch* b, ehd_slot_status* out, int max, int* n);
+/* Fields of a live slot, as ehd_read_fields. */
+int ehd_batch_read_fields(ehd_batch* b, int slot, unsigned mask, void* const* out, int mem);
+/* Ends a slot (finished, cancelled or capped) and frees its arena space. */
+int ehd_batch_retire(ehd_batch* b, int slot);
+int ehd_batch_info(ehd_batch* b, ehd_batch_info_t* info);
+void ehd_batch_destroy(ehd_batch* b);
+
 /* Static description of a status code. */
 const char* ehd_error_string(int code);
 

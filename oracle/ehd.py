@@ -417,8 +417,8 @@ def varphi_of(h):
 def grad_varphi_local(P, h, eps_hat):
     """Local potential gradient (Eq. eqA.16):
     grad varphi = - sum_i c_i h_i / (eps_hat + c_s^2 tau_h dt)."""
-    mx = np.tensordot(CX, h, axes=(0, 0))
-    my = np.tensordot(CY, h, axes=(0, 0))
+    mx = sum(CX[i] * h[i] for i in range(9))
+    my = sum(CY[i] * h[i] for i in range(9))
     den = eps_hat + CS2 * P.tau_h
     return -mx / den, -my / den
 
@@ -576,8 +576,8 @@ class Sim:
         phi = self.g.sum(axis=0)
         q = self.l.sum(axis=0) + 0.5 * self.R_prev
         rho = rho_of(P, phi)
-        ux = (np.tensordot(CX, self.f, axes=(0, 0)) + 0.5 * self.Fx_prev) / rho
-        uy = (np.tensordot(CY, self.f, axes=(0, 0)) + 0.5 * self.Fy_prev) / rho
+        ux = (sum(CX[i] * self.f[i] for i in range(9)) + 0.5 * self.Fx_prev) / rho
+        uy = (sum(CY[i] * self.f[i] for i in range(9)) + 0.5 * self.Fy_prev) / rho
         return phi, q, rho, ux, uy
 
     def _pressure(self, phi, rho, ux, uy, gphi_x, gphi_y):

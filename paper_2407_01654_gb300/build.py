@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libehd.so")
-SOURCES = ["kernels.cu", "poisson.cu", "poisson_resident.cu", "noalloc.cu", "api.cu"]
+SOURCES = ["kernels.cu", "poisson.cu", "poisson_resident.cu", "noalloc.cu", "batch.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
@@ -43,7 +43,8 @@ def build(verbose=False, ptxas_info=False, force=False):
     """Compiles the library if a source is newer than it (or force).  Returns its path."""
     os.makedirs(BUILD_DIR, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, "ehd_internal.cuh"), os.path.join(ROOT, "include", "ehd.h")]
+    deps = srcs + [os.path.join(CSRC, "ehd_internal.cuh"), os.path.join(CSRC, "sim_internal.h"),
+                   os.path.join(ROOT, "include", "ehd.h")]
     if (not force and os.path.exists(LIB)
             and all(os.path.getmtime(LIB) >= os.path.getmtime(d) for d in deps)):
         return LIB

@@ -10,43 +10,7 @@
 
 using namespace ehd;
 
-struct ehd_sim {
-  ehd_params P;
-  KParams kp;
-  Buffers b;
-  void* ws = nullptr;
-  size_t ws_bytes = 0;
-  bool own_ws = false;
-  cudaStream_t stream = nullptr;
-  int cur = 0;              // which population copy is current
-  int64_t n = 0;            // step counter
-  bool history_valid = false;
-  int last_k = 1;           // sub-iterations of the last potential solve
-  Ctl* h_ctl = nullptr;     // pinned mirror of the loop control
-  DevStats* h_stats = nullptr;
-  float* h_stage = nullptr; // pinned staging for host field I/O, NIO * N floats
-  int64_t launches = 0;     // kernel launches queued since the statistics were cleared
-  int64_t graph_steps = 0;  // steps run as graphs since then
-  int64_t host_iters = 0;   // potential sub-iterations run from the host loop since then
-  bool stats_live = false;  // device statistics are accumulating
-  // per-launch event timing
-  bool profiling = false;
-  std::vector<cudaEvent_t> ev;     // start/stop pairs
-  std::vector<int> ev_kind;        // kind per pair
-  size_t ev_used = 0;              // pairs recorded and not yet accumulated
-  double prof_ms[4] = {0, 0, 0, 0};
-  int64_t prof_n[4] = {0, 0, 0, 0};
-  // one step graph per population copy (moments -> while{potential} -> coupled)
-  bool graphs_tried = false;
-  bool graphs_ok = false;
-  cudaGraph_t graph[2] = {nullptr, nullptr};
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};
-  // resident (on-chip) potential loop, when the lattice fits
-  bool resident_ok = false;
-  ResidentGeom rg{};
-  int rthreads = 0;
-  size_t rsmem = 0;
-};
+#include "sim_internal.h"
 
 namespace {
 
@@ -64,7 +28,7 @@ struct Layout {
 // fewer SMs the tiles are larger and fewer, which needs less export space.
 constexpr int DESIGN_SMS = 152;
 
-Layout layout_for(const ehd_params& P) {
+Layout layout_for(const ehd_params& P, int fixed_ty = 0) {
   const int64_t N = (int64_t)P.nx * P.ny;
   Layout L{};
   size_t o = 0;
@@ -98,12 +62,12 @@ Layout layout_for(const ehd_params& P) {
   kp.ny = P.ny;
   L.export_floats = 0;
   L.rtiles = 0;
-  if (resident_geometry(kp, DESIGN_SMS, &g, &th, &sm)) {
+  if (resident_geometry(kp, DESIGN_SMS, &g, &th, &sm, fixed_ty)) {
     L.rtiles = (size_t)g.ntx * g.nty;
     L.export_floats = 2 * L.rtiles * 8 * (size_t)g.pmax;
   }
   L.exports = take(sizeof(float) * (L.export_floats ? L.export_floats : 1));
-  L.rpartials = take(sizeof(double2) * 2 * (L.rtiles > 0 ? DESIGN_SMS : 1));
+  L.rpartials = take(sizeof(double2) * 2 * (L.rtiles > 0 ? L.rtiles : 1));
   L.total = o;
   return L;
 }
@@ -407,14 +371,20 @@ int ehd_workspace_bytes(const ehd_params* params, size_t* bytes) {
   return EHD_OK;
 }
 
-int ehd_create(const ehd_params* params, void* workspace, size_t workspace_bytes, void* stream,
-               ehd_sim** out) {
+}  // extern "C"
+
+size_t sim_workspace_bytes(const ehd_params* params, int fixed_ty) {
+  return layout_for(*params, fixed_ty).total;
+}
+
+int sim_create(const ehd_params* params, void* workspace, size_t workspace_bytes, void* stream,
+               int fixed_ty, ehd_sim** out) {
   if (!out) return EHD_ERR_INVALID_ARG;
   *out = nullptr;
   const int v = validate(params);
   if (v != EHD_OK) return v;
   const int64_t N = (int64_t)params->nx * params->ny;
-  const Layout L = layout_for(*params);
+  const Layout L = layout_for(*params, fixed_ty);
   ehd_sim* s = new (std::nothrow) ehd_sim();
   if (!s) return EHD_ERR_NOMEM;
   s->P = *params;
@@ -464,9 +434,9 @@ int ehd_create(const ehd_params* params, void* workspace, size_t workspace_bytes
       ResidentGeom g;
       int th;
       size_t sm;
-      if (resident_geometry(s->kp, use_sms, &g, &th, &sm) &&
+      if (resident_geometry(s->kp, use_sms, &g, &th, &sm, fixed_ty) &&
           2 * (size_t)g.ntx * g.nty * 8 * g.pmax <= L.export_floats &&
-          (size_t)g.ntx * g.nty <= (size_t)DESIGN_SMS &&
+          (size_t)g.ntx * g.nty <= L.rtiles &&
           cudaFuncSetAttribute(resident_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)sm) == cudaSuccess) {
         int per_sm = 0;
@@ -501,6 +471,13 @@ int ehd_create(const ehd_params* params, void* workspace, size_t workspace_bytes
   }
   *out = s;
   return EHD_OK;
+}
+
+extern "C" {
+
+int ehd_create(const ehd_params* params, void* workspace, size_t workspace_bytes, void* stream,
+               ehd_sim** out) {
+  return sim_create(params, workspace, workspace_bytes, stream, 0, out);
 }
 
 int ehd_profile(ehd_sim* s, int enable) {
@@ -573,8 +550,7 @@ int ehd_set_fields(ehd_sim* s, const void* phi, const void* q, const void* ux, c
   }
   s->n = s->P.start_step;
   s->history_valid = false;
-  s->cur = 0;
-  // the potential distribution restarts in copy 0
+  // the populations are written into the current copy; the potential restarts in copy 0
   EHD_CUDA(cudaMemsetAsync(&s->b.ctl->parity, 0, sizeof(int), s->stream));
   EHD_CUDA(cudaMemsetAsync(&s->b.ctl->nonfinite, 0, sizeof(int), s->stream));
   s->launches += 1;

@@ -235,10 +235,22 @@ __host__ __device__ inline Pops pops_copy(const KParams& k, const Buffers& b, in
   return P;
 }
 
-// Resident potential loop (poisson_resident.cu).
+// Everything the resident loop of one simulation needs (batch launches keep a table).
+struct ResidentSlot {
+  KParams k;
+  ResidentGeom rg;
+  float* h;
+  const float2* aq;
+  float* exports;
+  double2* rpartials;
+  Ctl* ctl;
+};
+
+// Resident potential loop (poisson_resident.cu).  fixed_ty > 0: tiles of 64 x fixed_ty.
 bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* threads,
-                       size_t* smem);
+                       size_t* smem, int fixed_ty = 0);
 const void* resident_kernel();
+const void* resident_batch_kernel();
 cudaError_t launch_poisson_resident(const KParams& kp, const ResidentGeom& g, int threads,
                                     size_t smem, const Buffers& b, cudaStream_t st);
 cudaError_t add_poisson_resident_node(cudaGraph_t graph, const cudaGraphNode_t* deps, size_t nd,
@@ -257,6 +269,13 @@ cudaError_t launch_coupled(const KParams& kp, const Buffers& b, int cur, cudaStr
 cudaError_t launch_stats_reset(const Buffers& b, cudaStream_t st);
 cudaError_t launch_fields(const KParams& kp, const Buffers& b, int cur, unsigned mask,
                           cudaStream_t st);
+
+// Graph nodes of the per-step kernels (argument values are copied into the node).
+cudaError_t add_moments_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
+                             cudaGraphNode_t* out, const KParams& kp, const Buffers& b, int cur,
+                             double tol, int min_iter, int max_iter, int fixed_iter);
+cudaError_t add_coupled_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
+                             cudaGraphNode_t* out, const KParams& kp, const Buffers& b, int cur);
 
 // Graph of one time step for population copy `cur`: moments -> while(loop not done)
 // { potential sub-iteration } -> coupled pass.  All arguments live on the device, so the

@@ -87,10 +87,13 @@ struct Nb {
 
 }  // namespace
 
-__global__ void __launch_bounds__(MAX_THREADS, 1)
-    k_poisson_resident(KParams k, ResidentGeom rg, float* __restrict__ hbuf,
-                       const float2* __restrict__ aq, float* __restrict__ exports,
-                       double2* __restrict__ rpartials, Ctl* ctl) {
+// The loop for one tile of one simulation; `tile` of `ntiles` tiles of that simulation.
+__device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGeom& rg,
+                                              float* __restrict__ hbuf,
+                                              const float2* __restrict__ aq,
+                                              float* __restrict__ exports,
+                                              double2* __restrict__ rpartials, Ctl* ctl,
+                                              const int tile, const int ntiles) {
   extern __shared__ float sm[];  // [8][RY][RX] populations, then [TY*64] a, [TY*64] q
   __shared__ double s_w[MAX_THREADS / 32][2];
   __shared__ double s_tot[2];
@@ -98,8 +101,6 @@ __global__ void __launch_bounds__(MAX_THREADS, 1)
 
   const int nx = k.nx, ny = k.ny;
   const size_t N = (size_t)k.N;
-  const int ntiles = gridDim.x;
-  const int tile = blockIdx.x;
   const int tcol = tile % rg.ntx, trow = tile / rg.ntx;
   const int tx0 = tcol * TXR, ty0 = trow * rg.TY;
   const int tw = min(TXR, nx - tx0), th = min(rg.TY, ny - ty0);
@@ -165,75 +166,70 @@ __global__ void __launch_bounds__(MAX_THREADS, 1)
   double rel = 0.0;
   int conv = 0;
   for (;;) {
-    // 1. collide into the tile's shared populations; perimeter nodes also export
-    float* exp_cur = exports + (size_t)(it & 1) * ntiles * pstride + (size_t)tile * pstride;
+    // 1. collide into the tile's shared populations; keep varphi^k per node
+    float vold[NPT];
 #pragma unroll
     for (int s = 0; s < NPT; ++s) {
       const int j = threadIdx.x + s * blockDim.x;
       const int lx = j & (TXR - 1), ly = j >> 6;
+      vold[s] = 0.0f;
       if (j >= tnodes || lx >= tw) continue;
       float hsum = 0.0f;
 #pragma unroll
       for (int i = 0; i < 8; ++i) hsum += h[s][i];
       const float varphi = hsum * (9.0f / 5.0f);
+      vold[s] = varphi;
       const float m1x = h[s][0] - h[s][2] + h[s][4] - h[s][5] - h[s][6] + h[s][7];
       const float m1y = h[s][1] - h[s][3] + h[s][4] + h[s][5] - h[s][6] - h[s][7];
       const float qs = 0.125f * cq[j];
       const float a = ca[j];
       const int at = (ly + 1) * RX + lx + 1;
-      const bool perim = lx == 0 || ly == 0 || lx == tw - 1 || ly == th - 1;
-      const int slot = perim ? perim_slot(lx, ly, tw, th) : 0;
 #pragma unroll
       for (int i = 1; i < 9; ++i) {
         const float w = wgt(i);
         const float cm = cx(i) * m1x + cy(i) * m1y;
         const float v = h[s][i - 1] - om * (h[s][i - 1] - w * varphi) + a * w * cm + qs;
         sm[(i - 1) * plane + at] = v;
-        if (perim) exp_cur[(i - 1) * rg.pmax + slot] = v;
+      }
+    }
+    __syncthreads();
+    // perimeter nodes export their post-collision populations for the neighbour tiles
+    {
+      float* exp_cur = exports + (size_t)(it & 1) * ntiles * pstride + (size_t)tile * pstride;
+      const int np = 2 * tw + 2 * th;
+      for (int e = threadIdx.x; e < 8 * np; e += blockDim.x) {
+        const int i = e / np + 1, sl = e - (i - 1) * np;
+        int lx, ly;
+        if (sl < tw) { lx = sl; ly = 0; }
+        else if (sl < 2 * tw) { lx = sl - tw; ly = th - 1; }
+        else if (sl < 2 * tw + th) { lx = 0; ly = sl - 2 * tw; }
+        else { lx = tw - 1; ly = sl - 2 * tw - th; }
+        exp_cur[(i - 1) * rg.pmax + sl] = sm[(i - 1) * plane + (ly + 1) * RX + lx + 1];
       }
     }
     // 2. all tiles' exports are visible
     if (!grid_barrier(ctl, ntiles, gen)) return;
-    // 3. stopping decision on the previous sub-iteration's sums
-    if (it > 0) {
-      if (threadIdx.x < 32) {
-        const double2* pp = rpartials + (size_t)((it - 1) & 1) * ntiles;
-        double sa = 0.0, sb = 0.0;
-        for (int t = threadIdx.x; t < ntiles; t += 32) {
-          const double2 v = __ldcg(pp + t);
-          sa += v.x;
-          sb += v.y;
-        }
+    // 3+4a. one warp reads the previous sub-iteration's sums while the CTA fills the ring
+    // (for every boundary node and direction whose source lies outside the tile, put the
+    // source value where the uniform gather will read it)
+    if (it > 0 && threadIdx.x < 32) {
+      const double2* pp = rpartials + (size_t)((it - 1) & 1) * ntiles;
+      double sa = 0.0, sb = 0.0;
+      for (int t = threadIdx.x; t < ntiles; t += 32) {
+        const double2 v = __ldcg(pp + t);
+        sa += v.x;
+        sb += v.y;
+      }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          sa += __shfl_xor_sync(0xffffffffu, sa, o);
-          sb += __shfl_xor_sync(0xffffffffu, sb, o);
-        }
-        if (threadIdx.x == 0) {
-          s_tot[0] = sa;
-          s_tot[1] = sb;
-        }
+      for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
       }
-      __syncthreads();
-      const double nm = s_tot[0], dn = s_tot[1];
-      if (nm == 0.0 && dn == 0.0)
-        rel = 0.0;
-      else if (dn == 0.0)
-        rel = __longlong_as_double(0x7ff0000000000000ll);
-      else
-        rel = sqrt(nm / dn);
-      bool done;
-      if (fixed > 0) {
-        done = it >= fixed;
-        conv = 1;
-      } else {
-        conv = (it >= min_iter) && (rel < tol);
-        done = conv || it >= max_iter;
+      if (threadIdx.x == 0) {
+        s_tot[0] = sa;
+        s_tot[1] = sb;
       }
-      if (done) break;
     }
-    // 4a. ring: for every boundary node and direction whose source lies outside the tile,
-    // put the source value where the uniform gather will read it
     {
       const float* exp_all = exports + (size_t)(it & 1) * ntiles * pstride;
       const int nring = 6 * (tw + th);
@@ -279,6 +275,26 @@ __global__ void __launch_bounds__(MAX_THREADS, 1)
       }
     }
     __syncthreads();
+    // stopping decision on the previous sub-iteration's sums (the registers still hold
+    // the state it produced)
+    if (it > 0) {
+      const double nm = s_tot[0], dn = s_tot[1];
+      if (nm == 0.0 && dn == 0.0)
+        rel = 0.0;
+      else if (dn == 0.0)
+        rel = __longlong_as_double(0x7ff0000000000000ll);
+      else
+        rel = sqrt(nm / dn);
+      bool done;
+      if (fixed > 0) {
+        done = it >= fixed;
+        conv = 1;
+      } else {
+        conv = (it >= min_iter) && (rel < tol);
+        done = conv || it >= max_iter;
+      }
+      if (done) break;
+    }
     // 4b. stream: every source is now in shared memory
     float num = 0.0f, den = 0.0f;
 #pragma unroll
@@ -287,16 +303,15 @@ __global__ void __launch_bounds__(MAX_THREADS, 1)
       const int lx = j & (TXR - 1), ly = j >> 6;
       if (j >= tnodes || lx >= tw) continue;
       const int at = (ly + 1) * RX + lx + 1;
-      float vold = 0.0f, vnew = 0.0f;
+      float vnew = 0.0f;
 #pragma unroll
       for (int i = 1; i < 9; ++i) {
         const float v = sm[(i - 1) * plane + at - cy(i) * RX - cx(i)];
-        vold += h[s][i - 1];
         h[s][i - 1] = v;
         vnew += v;
       }
       const float vn = vnew * (9.0f / 5.0f);
-      const float vo = vold * (9.0f / 5.0f);
+      const float vo = vold[s];
       const float d = vn - vo;
       num += d * d;
       den += vo * vo;
@@ -340,22 +355,48 @@ __global__ void __launch_bounds__(MAX_THREADS, 1)
   }
 }
 
+__global__ void __launch_bounds__(MAX_THREADS, 1)
+    k_poisson_resident(KParams k, ResidentGeom rg, float* __restrict__ hbuf,
+                       const float2* __restrict__ aq, float* __restrict__ exports,
+                       double2* __restrict__ rpartials, Ctl* ctl) {
+  resident_loop(k, rg, hbuf, aq, exports, rpartials, ctl, blockIdx.x, gridDim.x);
+}
+
+// Several simulations in one cooperative launch: CTA b runs tile work[b].y of simulation
+// work[b].x.  Simulations exchange nothing, so each synchronises only its own tiles (its
+// own barrier counter and partial sums) and stops at its own sub-iteration count.
+__global__ void __launch_bounds__(MAX_THREADS, 1)
+    k_poisson_resident_batch(const ResidentSlot* __restrict__ slots,
+                             const int2* __restrict__ work) {
+  const int2 w = work[blockIdx.x];
+  const ResidentSlot& S = slots[w.x];
+  resident_loop(S.k, S.rg, S.h, S.aq, S.exports, S.rpartials, S.ctl, w.y,
+                S.rg.ntx * S.rg.nty);
+}
+
 // Tile geometry for the resident loop, or false if the lattice does not fit on chip with
 // one tile per SM.
 bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* threads,
-                       size_t* smem) {
+                       size_t* smem, int fixed_ty) {
   const long long N = (long long)kp.nx * kp.ny;
   const int ntx = (kp.nx + TXR - 1) / TXR;
-  if (ntx > num_sms) return false;
-  // about 2048 nodes per tile, never more tiles than SMs, tiles at most 64 x 64
-  long long want = (N + 2047) / 2048;
-  if (want > num_sms) want = num_sms;
-  int nty = (int)(want / ntx);
-  if (nty < 1) nty = 1;
-  if (nty > num_sms / ntx) nty = num_sms / ntx;
-  int TY = (kp.ny + nty - 1) / nty;
-  if (TY > TXR) return false;
-  nty = (kp.ny + TY - 1) / TY;
+  int TY, nty;
+  if (fixed_ty > 0) {
+    // fixed 64 x fixed_ty tiles (batches: a simulation tiles the same way in any mix)
+    TY = fixed_ty;
+    nty = (kp.ny + TY - 1) / TY;
+  } else {
+    if (ntx > num_sms) return false;
+    // about 2048 nodes per tile, never more tiles than SMs, tiles at most 64 x 64
+    long long want = (N + 2047) / 2048;
+    if (want > num_sms) want = num_sms;
+    nty = (int)(want / ntx);
+    if (nty < 1) nty = 1;
+    if (nty > num_sms / ntx) nty = num_sms / ntx;
+    TY = (kp.ny + nty - 1) / nty;
+    if (TY > TXR) return false;
+    nty = (kp.ny + TY - 1) / TY;
+  }
   g->TX = TXR;
   g->TY = TY;
   g->ntx = ntx;
@@ -371,6 +412,7 @@ bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* thr
 int resident_nodes_per_thread() { return NPT; }
 
 const void* resident_kernel() { return (const void*)k_poisson_resident; }
+const void* resident_batch_kernel() { return (const void*)k_poisson_resident_batch; }
 
 cudaError_t launch_poisson_resident(const KParams& kp, const ResidentGeom& g, int threads,
                                     size_t smem, const Buffers& b, cudaStream_t st) {

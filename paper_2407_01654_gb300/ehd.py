@@ -81,6 +81,31 @@ class KernelTimes(ctypes.Structure):
                 for j, k in enumerate(self.KINDS)}
 
 
+class SlotStatus(ctypes.Structure):
+    _fields_ = [
+        ("slot", ctypes.c_int32), ("live", ctypes.c_int32), ("request_id", ctypes.c_int64),
+        ("steps", ctypes.c_int64), ("poisson_iters", ctypes.c_int64),
+        ("steady", ctypes.c_int32), ("capped", ctypes.c_int32), ("status", ctypes.c_int32),
+        ("pad", ctypes.c_int32), ("rel_change_phi", ctypes.c_double),
+        ("rel_change_u", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "pad"}
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [
+        ("live_slots", ctypes.c_int32), ("max_slots", ctypes.c_int32),
+        ("arena_bytes", ctypes.c_size_t), ("arena_used", ctypes.c_size_t),
+        ("tiles_used", ctypes.c_int32), ("tile_capacity", ctypes.c_int32),
+        ("steps_run", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 _lib = None
 
 # name -> (restype, argtypes); every function declared in include/ehd.h
@@ -106,6 +131,19 @@ SIGNATURES = {
     "ehd_abi_sizes": (ctypes.c_int, [ctypes.POINTER(ctypes.c_size_t),
                                      ctypes.POINTER(ctypes.c_size_t)]),
     "ehd_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "ehd_batch_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "ehd_batch_admit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Params)]
+                        + [ctypes.c_void_p] * 4 + [ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]),
+    "ehd_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "ehd_batch_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SlotStatus), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "ehd_batch_read_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_uint,
+                                             ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
+    "ehd_batch_retire": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "ehd_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(BatchInfo)]),
+    "ehd_batch_destroy": (None, [ctypes.c_void_p]),
     "ehd_potential_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_void_p,
                                                    ctypes.c_void_p, ctypes.c_void_p,
                                                    ctypes.c_void_p, ctypes.c_void_p,
@@ -296,3 +334,95 @@ class Sim:
     def load_state(self, blob):
         buf = ctypes.create_string_buffer(blob, len(blob))
         _check(lib().ehd_load_state(self._h, buf, len(blob)), "ehd_load_state")
+
+
+class Batch:
+    """Many simulations resident in one device-memory arena (the ehd_batch_* calls).
+
+    hbm_budget: bytes of the arena; max_slots: concurrent requests; steady_tol: relative L2
+    change of phi and u over one run call below which a slot is steady; step_cap: steps
+    after which a slot is reported capped.  arena: "torch" (a torch uint8 tensor owned by
+    this object) or "library"."""
+
+    def __init__(self, hbm_budget, max_slots=64, steady_tol=1e-6, step_cap=300000,
+                 arena="torch", stream=None):
+        L = lib()
+        self._keep = None
+        ptr = None
+        if arena == "torch":
+            import torch
+            self._keep = torch.empty(int(hbm_budget) + 256, dtype=torch.uint8, device="cuda")
+            ptr = (self._keep.data_ptr() + 255) // 256 * 256
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            except Exception:
+                stream = 0
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        h = ctypes.c_void_p()
+        _check(L.ehd_batch_create(int(hbm_budget), int(max_slots), float(steady_tol),
+                                  int(step_cap), ptr, int(stream), ctypes.byref(h)),
+               "ehd_batch_create")
+        self._h = h
+        self.max_slots = max_slots
+        self.shapes = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ehd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def admit(self, params, fields, request_id=0):
+        """Returns the slot index, or None when the batch is full (EHD_ERR_BUSY)."""
+        p = Params.from_dict(params)
+        arrs = [_host(fields[k]) for k in ("phi", "q", "ux", "uy")]
+        slot = ctypes.c_int(-1)
+        code = lib().ehd_batch_admit(self._h, ctypes.byref(p), *[a.ctypes.data for a in arrs],
+                                     int(request_id), ctypes.byref(slot))
+        if code == 6:
+            return None
+        if code not in (EHD_OK, 4):
+            _check(code, "ehd_batch_admit")
+        self.shapes[slot.value] = (params["ny"], params["nx"])
+        return slot.value
+
+    def run(self, nsteps):
+        code = lib().ehd_batch_run(self._h, int(nsteps))
+        if code not in (EHD_OK, 4, 5):
+            _check(code, "ehd_batch_run")
+        return code
+
+    def poll(self):
+        arr = (SlotStatus * self.max_slots)()
+        n = ctypes.c_int()
+        _check(lib().ehd_batch_poll(self._h, arr, self.max_slots, ctypes.byref(n)), "ehd_batch_poll")
+        return [arr[i].as_dict() for i in range(n.value)]
+
+    def read_fields(self, slot, names=FIELDS):
+        mask = 0
+        for n in names:
+            mask |= 1 << FIELDS.index(n)
+        order = [n for n in FIELDS if mask & (1 << FIELDS.index(n))]
+        shape = self.shapes[slot]
+        outs = [np.empty(shape, dtype=np.float64) for _ in order]
+        ptrs = (ctypes.c_void_p * len(outs))(*[o.ctypes.data for o in outs])
+        _check(lib().ehd_batch_read_fields(self._h, int(slot), mask, ptrs, EHD_HOST),
+               "ehd_batch_read_fields")
+        return dict(zip(order, outs))
+
+    def retire(self, slot):
+        _check(lib().ehd_batch_retire(self._h, int(slot)), "ehd_batch_retire")
+        self.shapes.pop(slot, None)
+
+    def info(self):
+        bi = BatchInfo()
+        _check(lib().ehd_batch_info(self._h, ctypes.byref(bi)), "ehd_batch_info")
+        return bi.as_dict()

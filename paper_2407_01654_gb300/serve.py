@@ -1,0 +1,229 @@
+"""Serving loop: simulation requests arrive over time, are admitted into a batch of
+resident simulations as slots and device memory free up, advance together, and leave when
+steady (or at the step cap).  Continuous batching: a request that arrives while others are
+running is admitted at the next window boundary if it fits, without waiting for the batch
+to drain.
+
+The scheduler talks to a backend with four calls -- admit(params, fields, id) -> slot or
+None, run(nsteps), poll() -> [slot status], retire(slot) -- and reads time from a clock,
+so the policy can be exercised on the CPU with a fake backend and a fake clock.
+
+    python -m paper_2407_01654_gb300.serve --requests 48 --budget-gb 2
+"""
+from __future__ import annotations
+
+import argparse
+import heapq
+import json
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import workloads as wl
+
+
+@dataclass
+class Request:
+    id: int
+    arrival: float              # seconds after the start of the run
+    params: dict
+    fields: dict
+    admitted: float = math.nan
+    finished: float = math.nan
+    steps: int = 0
+    steady: bool = False
+    capped: bool = False
+    rel_change: tuple = (math.nan, math.nan)
+
+
+def make_requests(n, seed=0, sizes=(64, 128, 256, 512), rate=1.0, fp16_fraction=0.5):
+    """Droplet-deformation requests (Sec. 7.1 set-up): grid drawn uniformly from `sizes`
+    with r = 0.156 N, (R, S, Ca_E) seeded as for the single-droplet workload, half of them
+    with FP16-deviation storage; Poisson arrivals at `rate` per second."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+        N = int(rng.choice(sizes))
+        R, S, Ca = wl.droplet_ratios(seed * 100003 + i)
+        p, f, _ = wl.droplet(N=N, r=0.156 * N, R=R, S=S, Ca=Ca,
+                             precision=int(rng.uniform() < fp16_fraction))
+        out.append(Request(id=i, arrival=t, params=p, fields=f))
+    return out
+
+
+class WallClock:
+    def __init__(self):
+        self.t0 = time.perf_counter()
+
+    def now(self):
+        return time.perf_counter() - self.t0
+
+    def sleep_until(self, t):
+        d = t - self.now()
+        if d > 0:
+            time.sleep(d)
+
+
+def serve(backend, requests, clock, window=500, on_finish=None):
+    """Runs the requests through the backend; returns them with admission and finish
+    times filled.  Admission is first fit over the queue in arrival order (a request that
+    does not fit does not block smaller ones behind it)."""
+    pending = sorted(requests, key=lambda r: r.arrival)
+    queue = []
+    live = {}
+    done = []
+    i = 0
+    while i < len(pending) or queue or live:
+        now = clock.now()
+        while i < len(pending) and pending[i].arrival <= now:
+            queue.append(pending[i])
+            i += 1
+        still = []
+        for r in queue:
+            slot = backend.admit(r.params, r.fields, r.id)
+            if slot is None:
+                still.append(r)
+            else:
+                r.admitted = clock.now()
+                live[slot] = r
+        queue = still
+        if not live:
+            if i < len(pending):
+                clock.sleep_until(pending[i].arrival)
+                continue
+            if queue:
+                raise RuntimeError("a queued request can never be admitted (larger than the batch)")
+            break
+        backend.run(window)
+        for st in backend.poll():
+            r = live.get(st["slot"])
+            if r is None:
+                continue
+            r.steps = st["steps"]
+            r.rel_change = (st["rel_change_phi"], st["rel_change_u"])
+            if st["steady"] or st["capped"] or st["status"] == 5:
+                r.steady = bool(st["steady"])
+                r.capped = bool(st["capped"]) and not r.steady
+                r.finished = clock.now()
+                if on_finish is not None:
+                    on_finish(backend, st["slot"], r)
+                backend.retire(st["slot"])
+                del live[st["slot"]]
+                done.append(r)
+    return done
+
+
+def summarize(done, wall):
+    lat = np.array([r.finished - r.arrival for r in done])
+    run = np.array([r.finished - r.admitted for r in done])
+    return {
+        "requests": len(done),
+        "steady": int(sum(r.steady for r in done)),
+        "capped": int(sum(r.capped for r in done)),
+        "wall_s": wall,
+        "sims_per_hour": len(done) / wall * 3600.0 if wall > 0 else math.nan,
+        "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else math.nan,
+        "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else math.nan,
+        "p50_admit_to_steady_s": float(np.percentile(run, 50)) if len(run) else math.nan,
+        "p99_admit_to_steady_s": float(np.percentile(run, 99)) if len(run) else math.nan,
+        "steps_total": int(sum(r.steps for r in done)),
+    }
+
+
+class OneAtATime:
+    """Backend that runs one request at a time on its own simulation (no batching); with
+    plain=True it also uses the straightforward path: the streaming potential kernel with
+    the loop driven from the host (no graphs)."""
+
+    def __init__(self, steady_tol=1e-6, step_cap=300000, plain=True):
+        from . import ehd
+        self.ehd = ehd
+        self.tol = steady_tol
+        self.cap = step_cap
+        self.plain = plain
+        self.sim = None
+        self.req = None
+        self.steps = 0
+        self.prev = None
+        self.rel = (math.inf, math.inf)
+
+    def admit(self, params, fields, rid):
+        if self.sim is not None:
+            return None
+        p = dict(params)
+        if self.plain:
+            p["poisson_loop"] = 1
+        self.sim = self.ehd.Sim(p)
+        if self.plain:
+            self.sim.profile(True)  # the host-driven loop, kernel by kernel
+        self.sim.set_fields(fields["phi"], fields["q"], fields["ux"], fields["uy"])
+        self.rid = rid
+        self.steps = 0
+        self.prev = None
+        self.rel = (math.inf, math.inf)
+        return 0
+
+    def _snap(self):
+        F = self.sim.read_fields(("phi", "ux", "uy"))
+        return F["phi"], np.stack([F["ux"], F["uy"]])
+
+    def run(self, n):
+        if self.sim is None:
+            return 0
+        self.sim.step(n, stats=False)
+        self.steps += n
+        phi, u = self._snap()
+        if self.prev is not None:
+            p0, u0 = self.prev
+            self.rel = (float(np.linalg.norm(phi - p0) / max(np.linalg.norm(phi), 1e-300)),
+                        float(np.linalg.norm(u - u0) / max(np.linalg.norm(u), 1e-300)))
+        self.prev = (phi, u)
+        return 0
+
+    def poll(self):
+        if self.sim is None:
+            return []
+        steady = self.rel[0] < self.tol and self.rel[1] < self.tol
+        return [dict(slot=0, live=1, request_id=self.rid, steps=self.steps, poisson_iters=0,
+                     steady=int(steady), capped=int(self.steps >= self.cap), status=0,
+                     rel_change_phi=self.rel[0], rel_change_u=self.rel[1])]
+
+    def retire(self, slot):
+        self.sim.close()
+        self.sim = None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--sizes", default="64,128,256,512")
+    ap.add_argument("--rate", type=float, default=4.0)
+    ap.add_argument("--budget-gb", type=float, default=2.0)
+    ap.add_argument("--slots", type=int, default=64)
+    ap.add_argument("--window", type=int, default=500)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--cap", type=int, default=20000)
+    ap.add_argument("--baseline", action="store_true")
+    args = ap.parse_args()
+    from . import ehd
+    sizes = tuple(int(x) for x in args.sizes.split(","))
+    reqs = make_requests(args.requests, sizes=sizes, rate=args.rate)
+    clock = WallClock()
+    b = ehd.Batch(int(args.budget_gb * (1 << 30)), max_slots=args.slots, steady_tol=args.tol,
+                  step_cap=args.cap)
+    done = serve(b, reqs, clock, window=args.window)
+    out = {"batched": summarize(done, clock.now())}
+    if args.baseline:
+        reqs = make_requests(args.requests, sizes=sizes, rate=args.rate)
+        clock = WallClock()
+        done = serve(OneAtATime(args.tol, args.cap), reqs, clock, window=args.window)
+        out["one_at_a_time_plain"] = summarize(done, clock.now())
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,129 @@
+"""The batch (serving) layer on the GPU: many simulations resident in one arena, one
+shared cooperative launch for all potential loops, continuous admission."""
+import numpy as np
+import pytest
+
+from paper_2407_01654_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("phi", "q", "varphi", "Ex", "Ey", "ux", "uy", "p")
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_01654_gb300 import build
+    build.build()
+    from paper_2407_01654_gb300 import ehd
+    return ehd
+
+
+def request(N, seed, **over):
+    R, S, Ca = wl.droplet_ratios(seed)
+    p, f, _ = wl.droplet(N=N, r=0.156 * N, R=R, S=S, Ca=Ca, **over)
+    return p, wl.perturbed(p, f, seed=seed, u_amp=1e-3, q_amp=1e-4)
+
+
+def test_alone_equals_in_mix(gpu):
+    """A request gives bit-identical fields alone in a batch and in a mix of requests of
+    other sizes and parameters admitted at different times (stopping rule on)."""
+    pa, fa = request(96, 1)
+    alone = gpu.Batch(256 << 20, max_slots=4)
+    s = alone.admit(pa, fa, 1)
+    for _ in range(4):
+        alone.run(60)
+    ref = alone.read_fields(s)
+    mix = gpu.Batch(512 << 20, max_slots=8)
+    pb, fb = request(64, 2)
+    pc, fc = request(128, 3, precision=1)
+    sb = mix.admit(pb, fb, 2)
+    mix.run(60)                     # b runs alone for a while
+    sa = mix.admit(pa, fa, 1)       # a joins while b is live
+    sc = mix.admit(pc, fc, 3)
+    for _ in range(3):
+        mix.run(60)
+    mix.retire(sb)                  # b leaves mid-way
+    mix.run(60)
+    got = mix.read_fields(sa)
+    for k in FIELDS:
+        assert np.array_equal(got[k], ref[k]), k
+
+
+def test_batch_slot_matches_single_simulation(gpu):
+    """With a fixed sub-iteration count a batch slot and a plain simulation run the same
+    arithmetic: bitwise equal fields (their potential tilings differ)."""
+    p, f = request(80, 4, poisson_fixed_iter=4)
+    b = gpu.Batch(128 << 20, max_slots=2)
+    s = b.admit(p, f, 0)
+    b.run(50)
+    g = gpu.Sim(p)
+    g.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
+    g.step(50)
+    got, ref = b.read_fields(s), g.read_fields()
+    for k in FIELDS:
+        assert np.array_equal(got[k], ref[k]), k
+
+
+def test_admission_refusals_and_retire(gpu):
+    """Admission is refused (the batch unchanged) when the arena, the slot count or the
+    on-chip tile capacity would overflow; retiring frees the room again."""
+    p, f = request(128, 5)
+    ws_small = gpu.Batch(2 << 20, max_slots=4)          # arena too small for the request
+    assert ws_small.admit(p, f, 0) is None and ws_small.info()["live_slots"] == 0
+    b = gpu.Batch(64 << 20, max_slots=2)
+    base = b.info()["arena_used"]
+    s0 = b.admit(p, f, 0)
+    s1 = b.admit(p, f, 1)
+    assert s0 is not None and s1 is not None
+    assert b.admit(p, f, 2) is None                      # no free slot
+    b.run(20)
+    b.retire(s0)
+    assert b.info()["live_slots"] == 1
+    s2 = b.admit(p, f, 2)
+    assert s2 == s0
+    b.retire(s1)
+    b.retire(s2)
+    assert b.info()["arena_used"] == base and b.info()["tiles_used"] == 0
+    big = gpu.Batch(16 << 30, max_slots=4)
+    cap = big.info()["tile_capacity"]
+    pb, fb = request(512, 6)
+    admitted = [big.admit(pb, fb, i) for i in range(4)]  # 128 tiles each
+    assert sum(a is not None for a in admitted) == cap // 128
+
+
+def test_step_cap_and_steadiness(gpu):
+    """Status reporting: channel flow started at its steady profile is steady (relative
+    change of u over a window well below 1e-3); a droplet request that is still moving is
+    not; every slot reports its step count, the cap and its request id."""
+    ny, nu, g = 32, 0.1, 1e-6
+    p = wl.make_params(nx=64, ny=ny, walls_y=1, mu_l=nu, mu_v=nu, body_gx=g)
+    y = np.arange(ny, dtype=float)
+    ua = np.repeat((g / (2 * nu) * (y + 0.5) * (ny - 0.5 - y))[:, None], 64, axis=1)
+    z = np.zeros((ny, 64))
+    b = gpu.Batch(64 << 20, max_slots=2, steady_tol=1e-3, step_cap=800)
+    s = b.admit(p, dict(phi=z, q=z, ux=ua, uy=z), 7)
+    pd, fd = request(64, 9)
+    sd = b.admit(pd, fd, 8)
+    b.run(400)
+    b.run(400)
+    st = {x["slot"]: x for x in b.poll()}
+    assert st[s]["steps"] == 800 and st[s]["capped"] == 1 and st[s]["request_id"] == 7
+    assert st[s]["steady"] == 1 and st[s]["rel_change_u"] < 1e-3
+    assert st[sd]["steady"] == 0 and st[sd]["rel_change_u"] > 1e-3
+
+
+def test_serving_loop_runs_requests(gpu):
+    """End-to-end serving on a small stream of requests: every request finishes, admission
+    overlaps them on the device, latencies are recorded."""
+    from paper_2407_01654_gb300 import serve
+    reqs = serve.make_requests(6, seed=11, sizes=(32, 64), rate=200.0)
+    b = gpu.Batch(256 << 20, max_slots=8, steady_tol=1e-4, step_cap=1500)
+    clock = serve.WallClock()
+    done = serve.serve(b, reqs, clock, window=250)
+    assert len(done) == 6
+    s = serve.summarize(done, clock.now())
+    assert s["sims_per_hour"] > 0 and s["p99_latency_s"] >= s["p50_latency_s"]
+    assert all(r.arrival <= r.admitted <= r.finished for r in done)

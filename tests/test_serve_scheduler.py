@@ -1,0 +1,118 @@
+"""The serving scheduler's policy on the CPU, with a fake batch backend and a fake clock:
+continuous admission, first-fit over the queue, retirement on steady or cap, latency
+bookkeeping, and host-side fault cases (a request that can never fit, a cancelled or
+capped request freeing its slot)."""
+import math
+
+import pytest
+
+from paper_2407_01654_gb300 import serve
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def now(self):
+        return self.t
+
+    def sleep_until(self, t):
+        self.t = max(self.t, t)
+
+
+class FakeBatch:
+    """Capacity in nodes; a run of n steps costs n * (live nodes) * 1e-9 s + 1e-4 s; a
+    request is steady after `need[id]` steps."""
+
+    def __init__(self, clock, capacity, need, cap=10 ** 9, slots=8):
+        self.clock, self.capacity, self.need, self.cap, self.slots = clock, capacity, need, cap, slots
+        self.live = {}
+        self.used = 0
+        self.max_live = 0
+
+    def admit(self, params, fields, rid):
+        n = params["nx"] * params["ny"]
+        if self.used + n > self.capacity or len(self.live) >= self.slots:
+            return None
+        slot = min(set(range(self.slots)) - set(self.live))
+        self.live[slot] = [rid, n, 0]
+        self.used += n
+        self.max_live = max(self.max_live, len(self.live))
+        return slot
+
+    def run(self, steps):
+        self.clock.t += steps * sum(v[1] for v in self.live.values()) * 1e-9 + 1e-4
+        for v in self.live.values():
+            v[2] += steps
+
+    def poll(self):
+        return [dict(slot=s, steps=v[2], steady=int(v[2] >= self.need[v[0]]),
+                     capped=int(v[2] >= self.cap), status=0, rel_change_phi=0.0,
+                     rel_change_u=0.0) for s, v in self.live.items()]
+
+    def retire(self, slot):
+        self.used -= self.live.pop(slot)[1]
+
+
+def req(i, t, n):
+    return serve.Request(id=i, arrival=t, params=dict(nx=n, ny=n), fields={})
+
+
+def test_all_requests_finish_with_consistent_times():
+    clock = FakeClock()
+    reqs = [req(i, 0.01 * i, 64 if i % 2 else 128) for i in range(20)]
+    be = FakeBatch(clock, capacity=4 * 128 * 128, need={i: 1000 + 500 * (i % 3) for i in range(20)})
+    done = serve.serve(be, reqs, clock, window=500)
+    assert len(done) == 20 and all(r.steady for r in done)
+    for r in done:
+        assert r.arrival <= r.admitted <= r.finished
+        assert r.steps >= be.need[r.id]
+    s = serve.summarize(done, clock.now())
+    assert s["p50_latency_s"] <= s["p99_latency_s"] and s["sims_per_hour"] > 0
+    assert be.max_live > 1  # requests overlapped on the device
+
+
+def test_continuous_admission_while_others_run():
+    """A request arriving while a long one runs is admitted before the long one ends."""
+    clock = FakeClock()
+    reqs = [req(0, 0.0, 128), req(1, 1e-3, 64)]
+    be = FakeBatch(clock, capacity=10 ** 6, need={0: 100000, 1: 1000})
+    done = {r.id: r for r in serve.serve(be, reqs, clock, window=500)}
+    assert done[1].admitted < done[0].finished
+    assert done[1].finished < done[0].finished
+
+
+def test_first_fit_does_not_block_small_requests():
+    """A request too large for the free space waits; a smaller one behind it is admitted."""
+    clock = FakeClock()
+    reqs = [req(0, 0.0, 100), req(1, 1e-4, 100), req(2, 2e-4, 10)]
+    be = FakeBatch(clock, capacity=100 * 100 + 10 * 10, need={0: 5000, 1: 1000, 2: 1000})
+    done = {r.id: r for r in serve.serve(be, reqs, clock, window=500)}
+    assert done[2].admitted < done[0].finished          # the small one went past the big one
+    assert done[1].admitted >= done[0].finished          # the big one waited for room
+
+
+def test_capped_request_frees_its_slot():
+    clock = FakeClock()
+    reqs = [req(0, 0.0, 64), req(1, 0.0, 64)]
+    be = FakeBatch(clock, capacity=64 * 64, need={0: 10 ** 9, 1: 1000}, cap=3000)
+    done = {r.id: r for r in serve.serve(be, reqs, clock, window=500)}
+    assert done[0].capped and not done[0].steady and done[0].steps >= 3000
+    assert done[1].steady and done[1].admitted >= done[0].finished
+    assert be.used == 0 and not be.live
+
+
+def test_request_larger_than_the_batch_is_an_error():
+    clock = FakeClock()
+    be = FakeBatch(clock, capacity=64 * 64, need={0: 1000})
+    with pytest.raises(RuntimeError):
+        serve.serve(be, [req(0, 0.0, 128)], clock, window=500)
+
+
+def test_request_generator_is_seeded():
+    a = serve.make_requests(6, seed=3, sizes=(16, 32), rate=2.0)
+    b = serve.make_requests(6, seed=3, sizes=(16, 32), rate=2.0)
+    assert [r.arrival for r in a] == [r.arrival for r in b]
+    assert [r.params["nx"] for r in a] == [r.params["nx"] for r in b]
+    assert all(r.params["nx"] in (16, 32) for r in a)
+    assert a[-1].arrival > a[0].arrival > 0
