@@ -67,7 +67,7 @@ Layout layout_for(const ehd_params& P, int fixed_ty = 0) {
     L.export_floats = 2 * L.rtiles * 8 * (size_t)g.pmax;
   }
   L.exports = take(sizeof(float) * (L.export_floats ? L.export_floats : 1));
-  L.rpartials = take(sizeof(double2) * 2 * (L.rtiles > 0 ? L.rtiles : 1));
+  L.rpartials = take(sizeof(float2) * 2 * (L.rtiles > 0 ? L.rtiles : 1));
   L.total = o;
   return L;
 }
@@ -421,7 +421,7 @@ int sim_create(const ehd_params* params, void* workspace, size_t workspace_bytes
   s->b.ctl = reinterpret_cast<Ctl*>(base + L.ctl);
   s->b.stats = reinterpret_cast<DevStats*>(base + L.stats);
   s->b.exports = reinterpret_cast<float*>(base + L.exports);
-  s->b.rpartials = reinterpret_cast<double2*>(base + L.rpartials);
+  s->b.rpartials = reinterpret_cast<float2*>(base + L.rpartials);
   // resident potential loop: needs cooperative launch, one tile per SM on this device,
   // and an export area within the reserved space
   {

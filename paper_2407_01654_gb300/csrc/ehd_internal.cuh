@@ -168,10 +168,9 @@ struct Ctl {
   unsigned ticket_m;        // CTA arrival counters of the two reductions
   unsigned ticket_p;
   float vw_b, vw_t;         // wall potentials of the current solve
-  unsigned bar_count;       // grid barrier of the resident potential loop
-  unsigned bar_gen;
+  unsigned bar_count;       // grid barrier of the resident potential loop: arrivals in
+                            // the current solve (reset with the loop control)
   int bar_error;            // a barrier wait timed out (sticky)
-  int pad2;
 };
 
 // Tiling of the resident potential loop: ntx x nty tiles of TX x TY nodes (the last
@@ -220,7 +219,7 @@ struct Buffers {
   Ctl* ctl;
   DevStats* stats;
   float* exports;    // resident loop: [2][tiles][8][pmax]
-  double2* rpartials;// resident loop: [2][tiles]
+  float2* rpartials; // resident loop: [2][tiles]
 };
 
 __host__ __device__ inline Pops pops_copy(const KParams& k, const Buffers& b, int c) {
@@ -242,7 +241,7 @@ struct ResidentSlot {
   float* h;
   const float2* aq;
   float* exports;
-  double2* rpartials;
+  float2* rpartials;
   Ctl* ctl;
 };
 

@@ -227,6 +227,7 @@ __global__ void __launch_bounds__(256) k_moments(KParams k, const StepState* __r
     ctl->vw_b = ss->vw_b;
     ctl->vw_t = ss->vw_t;
     ctl->ticket_m = 0u;
+    ctl->bar_count = 0u;
     __threadfence();
   }
 }

@@ -7,9 +7,10 @@
 //   1. collide the tile's nodes; post-collision populations go to shared memory, and
 //      those of perimeter nodes also to a per-tile export area in global memory;
 //   2. grid barrier;
-//   3. decide: every CTA reduces the previous sub-iteration's FP64 partial sums in the
-//      same fixed order and applies the stopping rule identically; if the loop is done the
-//      registers hold exactly the paper's final state, which is written back;
+//   3. decide: one lane reduces the previous sub-iteration's per-tile partial sums in a
+//      fixed order and applies the stopping rule, so every CTA takes the same decision;
+//      if the loop is done the registers hold exactly the paper's final state, which is
+//      written back;
 //   4. stream: gather h_i(x) = h*_i(x - c_i) from shared memory, from a neighbour tile's
 //      export area, or from the anti-bounce-back wall rule; form varphi^{k+1} and the
 //      partial sums of sum (varphi^{k+1} - varphi^k)^2 and sum (varphi^k)^2.
@@ -17,9 +18,18 @@
 // barrier per sub-iteration suffices.  The collision made just before the loop stops
 // never leaves the chip.
 //
-// The grid barrier spins on a generation counter with a time limit; a CTA that waits
-// longer than the limit sets an error flag and the kernel returns (with a cooperative
-// launch all CTAs are co-resident, so the limit is never reached in normal operation).
+// The stopping sums are FP32 throughout (per node, per warp, per tile, across tiles, each
+// in a fixed order).  varphi^{k+1} - varphi^k is itself an FP32 difference of two nearly
+// equal FP32 values, so the summand carries a relative error near 1e-7 / (relative
+// change); FP32 accumulation (relative error below 1e-6 for these tree depths) adds
+// nothing visible to the decision, and the FP64 units of this part are slow enough that
+// FP64 sums here cost more than the rest of a sub-iteration.
+//
+// The grid barrier counts arrivals in the loop control (reset for each solve by the
+// moments kernel): a CTA adds one with release semantics and waits, with acquire loads
+// and a time limit, until the count reaches its target; on timeout it sets an error flag
+// and the kernel returns (with a cooperative launch all CTAs are co-resident, so the
+// limit is never reached in normal operation).
 #include "ehd_internal.cuh"
 
 namespace ehd {
@@ -36,34 +46,35 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Grid barrier for co-resident CTAs.  Returns false on timeout (error flag set).
-__device__ __forceinline__ bool grid_barrier(Ctl* sync, unsigned nblocks, unsigned& gen) {
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier for co-resident CTAs.  `target` counts the arrivals this CTA waits for;
+// returns false on timeout (error flag set).
+__device__ __forceinline__ bool grid_barrier(Ctl* sync, unsigned nblocks, unsigned& target) {
   __shared__ int s_ok;
-  __syncthreads();
+  __syncthreads();  // the CTA's writes happen before thread 0's release
+  target += nblocks;
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned g = gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&sync->bar_count, 1u);
-    if (arrived == nblocks - 1u) {
-      sync->bar_count = 0u;
-      __threadfence();
-      atomicExch(&sync->bar_gen, g + 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      while (*((volatile unsigned*)&sync->bar_gen) == g) {
-        if (global_ns() - t0 > BARRIER_TIMEOUT_NS) {
-          atomicOr(&sync->bar_error, 1);
-          ok = 0;
-          break;
-        }
+    red_release_add(&sync->bar_count, 1u);
+    const unsigned long long t0 = global_ns();
+    while ((int)(ld_acquire(&sync->bar_count) - target) < 0) {
+      if (global_ns() - t0 > BARRIER_TIMEOUT_NS) {
+        atomicOr(&sync->bar_error, 1);
+        ok = 0;
+        break;
       }
     }
-    __threadfence();
-    s_ok = ok && !*((volatile int*)&sync->bar_error);
+    s_ok = ok;
   }
   __syncthreads();
-  gen += 1u;
   return s_ok != 0;
 }
 
@@ -92,11 +103,11 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
                                               float* __restrict__ hbuf,
                                               const float2* __restrict__ aq,
                                               float* __restrict__ exports,
-                                              double2* __restrict__ rpartials, Ctl* ctl,
+                                              float2* __restrict__ rpartials, Ctl* ctl,
                                               const int tile, const int ntiles) {
   extern __shared__ float sm[];  // [8][RY][RX] populations, then [TY*64] a, [TY*64] q
-  __shared__ double s_w[MAX_THREADS / 32][2];
-  __shared__ double s_tot[2];
+  __shared__ float2 s_w[MAX_THREADS / 32];
+  __shared__ int s_done;
   __shared__ Nb s_nb[3][3];
 
   const int nx = k.nx, ny = k.ny;
@@ -161,10 +172,12 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
   }
   __syncthreads();
 
-  unsigned gen = ld_cg(&ctl->bar_gen);
+  unsigned target = 0;
   int it = 0;
-  double rel = 0.0;
+  float rel = 0.0f;
   int conv = 0;
+  const int nwarps = (int)(blockDim.x >> 5);
+  const int dwarp = nwarps - 1;  // the warp that reduces the tiles' sums and decides
   for (;;) {
     // 1. collide into the tile's shared populations; keep varphi^k per node
     float vold[NPT];
@@ -197,26 +210,27 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
     {
       float* exp_cur = exports + (size_t)(it & 1) * ntiles * pstride + (size_t)tile * pstride;
       const int np = 2 * tw + 2 * th;
-      for (int e = threadIdx.x; e < 8 * np; e += blockDim.x) {
-        const int i = e / np + 1, sl = e - (i - 1) * np;
+      for (int sl = threadIdx.x; sl < np; sl += blockDim.x) {
         int lx, ly;
         if (sl < tw) { lx = sl; ly = 0; }
         else if (sl < 2 * tw) { lx = sl - tw; ly = th - 1; }
         else if (sl < 2 * tw + th) { lx = 0; ly = sl - 2 * tw; }
         else { lx = tw - 1; ly = sl - 2 * tw - th; }
-        exp_cur[(i - 1) * rg.pmax + sl] = sm[(i - 1) * plane + (ly + 1) * RX + lx + 1];
+        const int at = (ly + 1) * RX + lx + 1;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) exp_cur[i * rg.pmax + sl] = sm[i * plane + at];
       }
     }
-    // 2. all tiles' exports are visible
-    if (!grid_barrier(ctl, ntiles, gen)) return;
-    // 3+4a. one warp reads the previous sub-iteration's sums while the CTA fills the ring
-    // (for every boundary node and direction whose source lies outside the tile, put the
-    // source value where the uniform gather will read it)
-    if (it > 0 && threadIdx.x < 32) {
-      const double2* pp = rpartials + (size_t)((it - 1) & 1) * ntiles;
-      double sa = 0.0, sb = 0.0;
-      for (int t = threadIdx.x; t < ntiles; t += 32) {
-        const double2 v = __ldcg(pp + t);
+    // 2. all tiles' exports (and the previous sub-iteration's partial sums) are visible
+    if (!grid_barrier(ctl, ntiles, target)) return;
+    // 3. the deciding warp reduces the previous sub-iteration's sums (tiles in a fixed
+    // order) and one lane applies the stopping rule, while the other warps fill the ring
+    if (it > 0 && (int)(threadIdx.x >> 5) == dwarp) {
+      const int lane = threadIdx.x & 31;
+      const float2* pp = rpartials + (size_t)((it - 1) & 1) * ntiles;
+      float sa = 0.0f, sb = 0.0f;
+      for (int t = lane; t < ntiles; t += 32) {
+        const float2 v = __ldcg(pp + t);
         sa += v.x;
         sb += v.y;
       }
@@ -225,11 +239,26 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
         sa += __shfl_xor_sync(0xffffffffu, sa, o);
         sb += __shfl_xor_sync(0xffffffffu, sb, o);
       }
-      if (threadIdx.x == 0) {
-        s_tot[0] = sa;
-        s_tot[1] = sb;
+      if (lane == 0) {
+        if (sa == 0.0f && sb == 0.0f)
+          rel = 0.0f;
+        else if (sb == 0.0f)
+          rel = __int_as_float(0x7f800000);
+        else
+          rel = sqrtf(sa / sb);
+        bool done;
+        if (fixed > 0) {
+          done = it >= fixed;
+          conv = 1;
+        } else {
+          conv = (it >= min_iter) && ((double)rel < tol);
+          done = conv || it >= max_iter;
+        }
+        s_done = done;
       }
     }
+    // 4a. ring: for every boundary node and direction whose source lies outside the tile,
+    // put the source value where the uniform gather will read it
     {
       const float* exp_all = exports + (size_t)(it & 1) * ntiles * pstride;
       const int nring = 6 * (tw + th);
@@ -275,26 +304,8 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
       }
     }
     __syncthreads();
-    // stopping decision on the previous sub-iteration's sums (the registers still hold
-    // the state it produced)
-    if (it > 0) {
-      const double nm = s_tot[0], dn = s_tot[1];
-      if (nm == 0.0 && dn == 0.0)
-        rel = 0.0;
-      else if (dn == 0.0)
-        rel = __longlong_as_double(0x7ff0000000000000ll);
-      else
-        rel = sqrt(nm / dn);
-      bool done;
-      if (fixed > 0) {
-        done = it >= fixed;
-        conv = 1;
-      } else {
-        conv = (it >= min_iter) && (rel < tol);
-        done = conv || it >= max_iter;
-      }
-      if (done) break;
-    }
+    // the registers still hold the state the decision was about
+    if (it > 0 && s_done) break;
     // 4b. stream: every source is now in shared memory
     float num = 0.0f, den = 0.0f;
 #pragma unroll
@@ -321,18 +332,16 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
       num += __shfl_xor_sync(0xffffffffu, num, o);
       den += __shfl_xor_sync(0xffffffffu, den, o);
     }
-    if ((threadIdx.x & 31) == 0) {
-      s_w[threadIdx.x >> 5][0] = (double)num;
-      s_w[threadIdx.x >> 5][1] = (double)den;
-    }
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = make_float2(num, den);
     __syncthreads();  // shared populations consumed; warp sums visible
-    if (threadIdx.x == 0) {
-      double sa = 0.0, sb = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        sa += s_w[w][0];
-        sb += s_w[w][1];
+    if (threadIdx.x < 32) {
+      float2 v = (int)threadIdx.x < nwarps ? s_w[threadIdx.x] : make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
       }
-      rpartials[(size_t)(it & 1) * ntiles + tile] = make_double2(sa, sb);
+      if (threadIdx.x == 0) rpartials[(size_t)(it & 1) * ntiles + tile] = v;
     }
     ++it;
   }
@@ -347,9 +356,9 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
 #pragma unroll
     for (int i = 0; i < 8; ++i) hsrc[i * N + g] = h[s][i];
   }
-  if (tile == 0 && threadIdx.x == 0) {
+  if (tile == 0 && (int)threadIdx.x == dwarp * 32) {
     ctl->iter = it;
-    ctl->rel = rel;
+    ctl->rel = (double)rel;
     ctl->converged = conv;
     ctl->done = 1;
   }
@@ -358,7 +367,7 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
 __global__ void __launch_bounds__(MAX_THREADS, 1)
     k_poisson_resident(KParams k, ResidentGeom rg, float* __restrict__ hbuf,
                        const float2* __restrict__ aq, float* __restrict__ exports,
-                       double2* __restrict__ rpartials, Ctl* ctl) {
+                       float2* __restrict__ rpartials, Ctl* ctl) {
   resident_loop(k, rg, hbuf, aq, exports, rpartials, ctl, blockIdx.x, gridDim.x);
 }
 
@@ -421,7 +430,7 @@ cudaError_t launch_poisson_resident(const KParams& kp, const ResidentGeom& g, in
   float* h = b.h;
   const float2* aq = b.aq;
   float* ex = b.exports;
-  double2* rp = b.rpartials;
+  float2* rp = b.rpartials;
   Ctl* ctl = b.ctl;
   void* args[] = {&k, &gg, &h, &aq, &ex, &rp, &ctl};
   return cudaLaunchCooperativeKernel((const void*)k_poisson_resident, dim3(g.ntx * g.nty),
@@ -437,7 +446,7 @@ cudaError_t add_poisson_resident_node(cudaGraph_t graph, const cudaGraphNode_t* 
   float* h = b.h;
   const float2* aq = b.aq;
   float* ex = b.exports;
-  double2* rp = b.rpartials;
+  float2* rp = b.rpartials;
   Ctl* ctl = b.ctl;
   void* args[] = {&k, &gg, &h, &aq, &ex, &rp, &ctl};
   cudaKernelNodeParams p = {};
