@@ -21,6 +21,11 @@ SOURCES = ["kernels.cu", "poisson.cu", "poisson_resident.cu", "noalloc.cu", "bat
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
+# kernels.cu holds each pass twice, as a one-simulation kernel and as a batched kernel that
+# reads its parameters from a table; with multiply-add contraction left to the compiler the
+# two can round differently.  Without contraction both compute the same bits.  (The
+# potential loop kernels write their roundings explicitly instead.)
+FILE_FLAGS = {"kernels.cu": ["-fmad=false"]}
 
 
 def nvcc():
@@ -44,7 +49,7 @@ def build(verbose=False, ptxas_info=False, force=False):
     os.makedirs(BUILD_DIR, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     deps = srcs + [os.path.join(CSRC, "ehd_internal.cuh"), os.path.join(CSRC, "sim_internal.h"),
-                   os.path.join(ROOT, "include", "ehd.h")]
+                   os.path.join(ROOT, "include", "ehd.h"), os.path.abspath(__file__)]
     if (not force and os.path.exists(LIB)
             and all(os.path.getmtime(LIB) >= os.path.getmtime(d) for d in deps)):
         return LIB
@@ -54,7 +59,8 @@ def build(verbose=False, ptxas_info=False, force=False):
     for s in srcs:
         o = os.path.join(BUILD_DIR, os.path.basename(s).replace(".cu", ".o"))
         objs.append(o)
-        cmds.append([nvcc(), *ARCH, *FLAGS, *extra, "-c", s, "-o", o])
+        cmds.append([nvcc(), *ARCH, *FLAGS, *FILE_FLAGS.get(os.path.basename(s), []), *extra,
+                     "-c", s, "-o", o])
     with cf.ThreadPoolExecutor(max_workers=len(cmds)) as ex:
         outs = list(ex.map(lambda c: _run(c, verbose), cmds))
     if ptxas_info:

@@ -2,11 +2,13 @@
 //
 // Each admitted request becomes a simulation (slot) whose workspace, steady-state
 // snapshot and check partials are carved from the batch's arena (first fit).  A batch
-// step is one CUDA graph: every slot's moments kernel, then ONE cooperative launch that
-// runs the potential loops of all slots on chip (a tile work-list across slots; each slot
-// synchronises only its own tiles and stops at its own sub-iteration count), then every
-// slot's coupled pass.  Slots tile their potential loop with fixed 64 x 32 tiles, so a
-// request computes exactly the same numbers alone and in any mix.
+// step is three launches whatever the number of slots, each over a work-list spanning all
+// slots: the moments of every slot; ONE cooperative launch that runs the potential loops
+// of all slots on chip (each slot synchronises only its own tiles and stops at its own
+// sub-iteration count); the coupled pass of every slot.  The steps are captured in CUDA
+// graphs of STEPS_PER_GRAPH steps.  Slots tile their potential loop with fixed 64 x 32
+// tiles and get the blocks of their own launches, so a request computes exactly the same
+// numbers alone and in any mix.
 //
 // Admission needs a free slot, room in the arena and room in the co-resident tile
 // capacity of the shared launch; otherwise EHD_ERR_BUSY and nothing changes.  Requests that
@@ -26,6 +28,7 @@ namespace {
 
 constexpr int BATCH_TY = 32;
 constexpr int STEADY_THREADS = 256;
+constexpr int STEPS_PER_GRAPH = 16;  // even: a multi-step graph ends on the copy it began with
 
 size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 
@@ -120,10 +123,14 @@ struct ehd_batch {
   size_t rsmem = 0;
   int tiles_used = 0;
   bool dirty = true;
-  cudaGraph_t graph[2] = {nullptr, nullptr};
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};    // one step from copy c
+  cudaGraphExec_t execm[2] = {nullptr, nullptr};   // STEPS_PER_GRAPH steps from copy c
   ResidentSlot* d_slots = nullptr;       // [max_slots]
   int2* d_work = nullptr;                // [tile_capacity]
+  StepSlot* d_step = nullptr;            // [max_slots]
+  int2* d_mwork = nullptr;               // [mwork_cap]: moments blocks of all slots
+  int2* d_cwork = nullptr;               // [cwork_cap]: coupled blocks of all slots
+  int mwork_cap = 0, cwork_cap = 0;
   int64_t steps_run = 0;
   int64_t launches = 0;
 };
@@ -147,13 +154,67 @@ void arena_free(ehd_batch* b, size_t off) { b->used.erase(off); }
 void destroy_batch_graphs(ehd_batch* b) {
   for (int c = 0; c < 2; ++c) {
     if (b->exec[c]) cudaGraphExecDestroy(b->exec[c]);
-    if (b->graph[c]) cudaGraphDestroy(b->graph[c]);
+    if (b->execm[c]) cudaGraphExecDestroy(b->execm[c]);
     b->exec[c] = nullptr;
-    b->graph[c] = nullptr;
+    b->execm[c] = nullptr;
   }
 }
 
-// Builds both step graphs for the current set of live slots.
+struct BatchLaunch {
+  void* rfunc;
+  int ntiles, rthreads;
+  size_t rsmem;
+  ResidentSlot* slots;
+  int2* work;
+  StepSlot* step;
+  int2* mwork;
+  int2* cwork;
+  int nm, nc;
+};
+
+// Appends one batch step from copy `cur` after `dep` (null: no dependency); its last node
+// goes to `last`.
+cudaError_t add_batch_step(cudaGraph_t g, const BatchLaunch& L, int cur,
+                           const cudaGraphNode_t* dep, cudaGraphNode_t* last) {
+  cudaGraphNode_t mn, rn;
+  cudaError_t e = add_moments_batch_node(g, dep, dep ? 1 : 0, &mn, L.step, L.mwork, L.nm, cur);
+  if (e != cudaSuccess) return e;
+  ResidentSlot* slots = L.slots;
+  int2* wk = L.work;
+  void* args[] = {&slots, &wk};
+  cudaKernelNodeParams p = {};
+  p.func = L.rfunc;
+  p.gridDim = dim3((unsigned)L.ntiles);
+  p.blockDim = dim3(L.rthreads);
+  p.sharedMemBytes = (unsigned)L.rsmem;
+  p.kernelParams = args;
+  if ((e = cudaGraphAddKernelNode(&rn, g, &mn, 1, &p)) != cudaSuccess) return e;
+  cudaKernelNodeAttrValue v = {};
+  v.cooperative = 1;
+  if ((e = cudaGraphKernelNodeSetAttribute(rn, cudaLaunchAttributeCooperative, &v)) !=
+      cudaSuccess)
+    return e;
+  return add_coupled_batch_node(g, &rn, 1, last, L.step, L.cwork, L.nc, cur);
+}
+
+// A graph of `nsteps` batch steps starting from copy `cur`, instantiated.
+int build_batch_graph(const BatchLaunch& L, int cur, int nsteps, cudaGraphExec_t* out) {
+  cudaGraph_t g;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return EHD_ERR_CUDA;
+  cudaGraphNode_t last = nullptr;
+  for (int k = 0; k < nsteps; ++k) {
+    cudaGraphNode_t prev = last;
+    if (add_batch_step(g, L, (cur + k) & 1, k ? &prev : nullptr, &last) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return EHD_ERR_CUDA;
+    }
+  }
+  const cudaError_t e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return e == cudaSuccess ? EHD_OK : EHD_ERR_CUDA;
+}
+
+// Builds the step graphs for the current set of live slots.
 int rebuild(ehd_batch* b) {
   destroy_batch_graphs(b);
   b->dirty = false;
@@ -161,10 +222,11 @@ int rebuild(ehd_batch* b) {
   for (int i = 0; i < (int)b->slots.size(); ++i)
     if (b->slots[i].live) live.push_back(i);
   if (live.empty()) return EHD_OK;
-  // device tables: one ResidentSlot per live slot (per copy, since the states alternate
-  // between copies but the potential populations do not) and the tile work-list
+  // device tables: per live slot its resident-loop view and its step view, and the work
+  // lists of the three launches
   std::vector<ResidentSlot> rs(live.size());
-  std::vector<int2> work;
+  std::vector<StepSlot> ss(live.size());
+  std::vector<int2> work, mwork, cwork;
   for (size_t j = 0; j < live.size(); ++j) {
     ehd_sim* s = b->slots[live[j]].sim;
     ResidentSlot& r = rs[j];
@@ -177,47 +239,53 @@ int rebuild(ehd_batch* b) {
     r.ctl = s->b.ctl;
     const int nt = s->rg.ntx * s->rg.nty;
     for (int t = 0; t < nt; ++t) work.push_back(make_int2((int)j, t));
+    StepSlot& q = ss[j];
+    q.k = s->kp;
+    q.b = s->b;
+    q.tol = s->P.poisson_tol;
+    q.min_iter = s->P.poisson_min_iter;
+    q.max_iter = s->P.poisson_max_iter;
+    q.fixed_iter = s->P.poisson_fixed_iter;
+    q.mblocks = (s->kp.N + 255) / 256;
+    for (int t = 0; t < q.mblocks; ++t) mwork.push_back(make_int2((int)j, t));
+    const int cb = (s->kp.N + 127) / 128;
+    for (int t = 0; t < cb; ++t) cwork.push_back(make_int2((int)j, t));
   }
-  if ((int)work.size() > b->tile_capacity) return EHD_ERR_BUSY;
+  if ((int)work.size() > b->tile_capacity || (int)mwork.size() > b->mwork_cap ||
+      (int)cwork.size() > b->cwork_cap)
+    return EHD_ERR_BUSY;
   if (cudaMemcpyAsync(b->d_slots, rs.data(), sizeof(ResidentSlot) * rs.size(),
                       cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
       cudaMemcpyAsync(b->d_work, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice,
                       b->stream) != cudaSuccess ||
+      cudaMemcpyAsync(b->d_step, ss.data(), sizeof(StepSlot) * ss.size(), cudaMemcpyHostToDevice,
+                      b->stream) != cudaSuccess ||
+      cudaMemcpyAsync(b->d_mwork, mwork.data(), sizeof(int2) * mwork.size(),
+                      cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+      cudaMemcpyAsync(b->d_cwork, cwork.data(), sizeof(int2) * cwork.size(),
+                      cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
       cudaStreamSynchronize(b->stream) != cudaSuccess)
     return EHD_ERR_CUDA;
+  BatchLaunch L;
+  L.rfunc = (void*)resident_batch_kernel();
+  L.ntiles = (int)work.size();
+  L.rthreads = b->rthreads;
+  L.rsmem = b->rsmem;
+  L.slots = b->d_slots;
+  L.work = b->d_work;
+  L.step = b->d_step;
+  L.mwork = b->d_mwork;
+  L.cwork = b->d_cwork;
+  L.nm = (int)mwork.size();
+  L.nc = (int)cwork.size();
   for (int c = 0; c < 2; ++c) {
-    cudaGraph_t g;
-    if (cudaGraphCreate(&g, 0) != cudaSuccess) return EHD_ERR_CUDA;
-    b->graph[c] = g;
-    std::vector<cudaGraphNode_t> mn(live.size()), cn(live.size());
-    for (size_t j = 0; j < live.size(); ++j) {
-      ehd_sim* s = b->slots[live[j]].sim;
-      const ehd_params& P = s->P;
-      if (add_moments_node(g, nullptr, 0, &mn[j], s->kp, s->b, c, P.poisson_tol,
-                           P.poisson_min_iter, P.poisson_max_iter, P.poisson_fixed_iter) !=
-          cudaSuccess)
-        return EHD_ERR_CUDA;
+    int st = build_batch_graph(L, c, 1, &b->exec[c]);
+    if (st == EHD_OK) st = build_batch_graph(L, c, STEPS_PER_GRAPH, &b->execm[c]);
+    if (st != EHD_OK) {
+      destroy_batch_graphs(b);
+      b->dirty = true;
+      return st;
     }
-    ResidentSlot* slots = b->d_slots;
-    int2* wk = b->d_work;
-    void* args[] = {&slots, &wk};
-    cudaKernelNodeParams p = {};
-    p.func = (void*)resident_batch_kernel();
-    p.gridDim = dim3((unsigned)work.size());
-    p.blockDim = dim3(b->rthreads);
-    p.sharedMemBytes = (unsigned)b->rsmem;
-    p.kernelParams = args;
-    cudaGraphNode_t rn;
-    if (cudaGraphAddKernelNode(&rn, g, mn.data(), mn.size(), &p) != cudaSuccess) return EHD_ERR_CUDA;
-    cudaKernelNodeAttrValue v = {};
-    v.cooperative = 1;
-    if (cudaGraphKernelNodeSetAttribute(rn, cudaLaunchAttributeCooperative, &v) != cudaSuccess)
-      return EHD_ERR_CUDA;
-    for (size_t j = 0; j < live.size(); ++j) {
-      ehd_sim* s = b->slots[live[j]].sim;
-      if (add_coupled_node(g, &rn, 1, &cn[j], s->kp, s->b, c) != cudaSuccess) return EHD_ERR_CUDA;
-    }
-    if (cudaGraphInstantiate(&b->exec[c], g, 0) != cudaSuccess) return EHD_ERR_CUDA;
   }
   return EHD_OK;
 }
@@ -274,16 +342,26 @@ int ehd_batch_create(size_t hbm_budget, int max_slots, double steady_tol, int64_
     b->own_arena = true;
   }
   b->arena_bytes = hbm_budget;
-  // device tables at the start of the arena
+  // device tables at the start of the arena; a slot's nodes never exceed its tiles x 2048,
+  // which bounds the work lists of the moments (256 nodes a block) and coupled (128) passes
+  const size_t max_nodes = (size_t)b->tile_capacity * 64 * BATCH_TY;
+  b->mwork_cap = (int)(max_nodes / 256) + max_slots;
+  b->cwork_cap = (int)(max_nodes / 128) + max_slots;
   const size_t t1 = al256(sizeof(ResidentSlot) * (size_t)max_slots);
   const size_t t2 = al256(sizeof(int2) * (size_t)b->tile_capacity);
-  if (t1 + t2 >= hbm_budget) {
+  const size_t t3 = al256(sizeof(StepSlot) * (size_t)max_slots);
+  const size_t t4 = al256(sizeof(int2) * (size_t)b->mwork_cap);
+  const size_t t5 = al256(sizeof(int2) * (size_t)b->cwork_cap);
+  if (t1 + t2 + t3 + t4 + t5 >= hbm_budget) {
     ehd_batch_destroy(b);
     return EHD_ERR_NOMEM;
   }
   b->d_slots = reinterpret_cast<ResidentSlot*>(b->arena);
   b->d_work = reinterpret_cast<int2*>(b->arena + t1);
-  b->heap_start = t1 + t2;
+  b->d_step = reinterpret_cast<StepSlot*>(b->arena + t1 + t2);
+  b->d_mwork = reinterpret_cast<int2*>(b->arena + t1 + t2 + t3);
+  b->d_cwork = reinterpret_cast<int2*>(b->arena + t1 + t2 + t3 + t4);
+  b->heap_start = t1 + t2 + t3 + t4 + t5;
   *out = b;
   return EHD_OK;
 }
@@ -363,14 +441,19 @@ int ehd_batch_run(ehd_batch* b, int nsteps) {
       }
     }
   if (!any) return EHD_OK;
-  for (int k = 0; k < nsteps; ++k) {
+  int k = 0;
+  for (; k + STEPS_PER_GRAPH <= nsteps; k += STEPS_PER_GRAPH)
+    if (cudaGraphLaunch(b->execm[b->cur], b->stream) != cudaSuccess) return EHD_ERR_CUDA;
+  for (; k < nsteps; ++k) {
     if (cudaGraphLaunch(b->exec[b->cur], b->stream) != cudaSuccess) return EHD_ERR_CUDA;
     b->cur ^= 1;
   }
   b->steps_run += nsteps;
-  // bring each slot's bookkeeping along, check steadiness, collect statistics
-  int status = EHD_OK;
-  for (Slot& sl : b->slots) {
+  b->launches += 3 * (int64_t)nsteps;
+  // bring each slot's bookkeeping along and queue its steadiness check; one wait for all
+  std::vector<std::vector<double>> parts(b->slots.size());
+  for (size_t i = 0; i < b->slots.size(); ++i) {
+    Slot& sl = b->slots[i];
     if (!sl.live) continue;
     ehd_sim* s = sl.sim;
     s->cur = b->cur;
@@ -378,7 +461,6 @@ int ehd_batch_run(ehd_batch* b, int nsteps) {
     s->history_valid = true;
     s->graph_steps += nsteps;
     sl.steps += nsteps;
-    b->launches += 2 * nsteps;
     const Pops P = pops_copy(s->kp, s->b, s->cur);
     if (s->kp.half)
       k_steady<true><<<sl.nblocks, STEADY_THREADS, 0, b->stream>>>(s->kp, P, s->b.hist, sl.snap,
@@ -387,14 +469,21 @@ int ehd_batch_run(ehd_batch* b, int nsteps) {
       k_steady<false><<<sl.nblocks, STEADY_THREADS, 0, b->stream>>>(s->kp, P, s->b.hist, sl.snap,
                                                                    sl.have_snap, sl.dpart);
     if (cudaGetLastError() != cudaSuccess) return EHD_ERR_CUDA;
-    std::vector<double> part((size_t)sl.nblocks * 4);
-    if (cudaMemcpyAsync(part.data(), sl.dpart, sizeof(double) * part.size(), cudaMemcpyDeviceToHost,
-                        b->stream) != cudaSuccess ||
-        cudaStreamSynchronize(b->stream) != cudaSuccess)
+    b->launches += 1;
+    parts[i].resize((size_t)sl.nblocks * 4);
+    if (cudaMemcpyAsync(parts[i].data(), sl.dpart, sizeof(double) * parts[i].size(),
+                        cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
       return EHD_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return EHD_ERR_CUDA;
+  int status = EHD_OK;
+  for (size_t i = 0; i < b->slots.size(); ++i) {
+    Slot& sl = b->slots[i];
+    if (!sl.live) continue;
+    ehd_sim* s = sl.sim;
     double t[4] = {0, 0, 0, 0};
-    for (int i = 0; i < sl.nblocks; ++i)
-      for (int j = 0; j < 4; ++j) t[j] += part[(size_t)i * 4 + j];
+    for (int j = 0; j < sl.nblocks; ++j)
+      for (int c = 0; c < 4; ++c) t[c] += parts[i][(size_t)j * 4 + c];
     if (sl.have_snap) {
       sl.rel_phi = t[1] > 0 ? std::sqrt(t[0] / t[1]) : (t[0] > 0 ? INFINITY : 0.0);
       // velocities below 1e-6 (lattice units) count as rest in the denominator
@@ -406,7 +495,6 @@ int ehd_batch_run(ehd_batch* b, int nsteps) {
     ehd_stats es;
     const int st = ehd_read_stats(s, &es);
     sl.iters += es.poisson_iters_total;
-    b->launches += s->resident_ok ? nsteps : es.poisson_iters_total;
     sl.status = st;
     if (st == EHD_ERR_NONFINITE || st == EHD_ERR_CUDA) status = st;
   }

@@ -201,6 +201,48 @@ __device__ __forceinline__ int wrap(int v, int n) {
 template <typename T>
 __device__ __forceinline__ T ld_cg(const T* p) { return __ldcg(p); }
 
+// Potential sub-iteration arithmetic (Eq. weq53 with the forcing of Eq. eqA.16 written
+// through the local first moment), shared by every kernel that runs the potential loop.
+// Each rounding is explicit (no multiply-add contraction by the compiler), so the
+// streaming, resident and batched loops compute the same bits for the same state.
+//
+// varphi = (sum_{i>0} h_i) / (1 - w_0) = 9/5 sum h_i (Eq. weq55); m1 = sum c_i h_i.
+__device__ __forceinline__ float h_sum8(const float (&h)[8]) {
+  float s = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) s = __fadd_rn(s, h[i]);
+  return s;
+}
+__device__ __forceinline__ float h_varphi(float hsum) { return __fmul_rn(hsum, 9.0f / 5.0f); }
+__device__ __forceinline__ void h_moment1(const float (&h)[8], float& m1x, float& m1y) {
+  m1x = __fadd_rn(__fsub_rn(__fsub_rn(__fadd_rn(__fsub_rn(h[0], h[2]), h[4]), h[5]), h[6]),
+                  h[7]);
+  m1y = __fsub_rn(__fsub_rn(__fadd_rn(__fadd_rn(__fsub_rn(h[1], h[3]), h[4]), h[5]), h[6]),
+                  h[7]);
+}
+// Post-collision h_i* (i = 1..8): h_i - (h_i - w_i varphi)/tau_h + a w_i c_i.m1 + q/8, with
+// a = eps_hat / (c_s^2 tau_h (eps_hat + c_s^2 tau_h)) and q/8 the source share.
+__device__ __forceinline__ float h_star(int i, float hi, float om, float varphi, float a,
+                                        float m1x, float m1y, float qs) {
+  const float w = wgt(i);
+  const float cm = (cx(i) != 0 && cy(i) != 0) ? __fadd_rn(cx(i) * m1x, cy(i) * m1y)
+                                               : (cx(i) != 0 ? cx(i) * m1x : cy(i) * m1y);
+  float v = __fmaf_rn(-w, varphi, hi);
+  v = __fmaf_rn(-om, v, hi);
+  v = __fmaf_rn(__fmul_rn(a, w), cm, v);
+  return __fadd_rn(v, qs);
+}
+// Anti-bounce-back at a Dirichlet wall of potential vw: -h_opp* + 2 w_i vw.
+__device__ __forceinline__ float h_wall(int i, float h_opp_star, float vw) {
+  return __fmaf_rn(2.0f * wgt(i), vw, -h_opp_star);
+}
+// Stopping sums: (varphi^{k+1} - varphi^k)^2 and (varphi^k)^2 added to num, den.
+__device__ __forceinline__ void h_change(float vnew, float vold, float& num, float& den) {
+  const float d = __fsub_rn(vnew, vold);
+  num = __fmaf_rn(d, d, num);
+  den = __fmaf_rn(vold, vold, den);
+}
+
 }  // namespace ehd
 
 // Launch functions implemented in the .cu files (host side).
@@ -244,6 +286,23 @@ struct ResidentSlot {
   float2* rpartials;
   Ctl* ctl;
 };
+
+// One simulation of a batch as the batched moments and coupled kernels see it.
+struct StepSlot {
+  KParams k;
+  Buffers b;
+  double tol;
+  int min_iter, max_iter, fixed_iter;
+  int mblocks;       // moments blocks of this simulation (256 nodes each)
+};
+
+// Batched moments / coupled passes: one launch over work[] = (slot, block of that slot).
+cudaError_t add_moments_batch_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
+                                   cudaGraphNode_t* out, const StepSlot* slots, const int2* work,
+                                   int nwork, int cur);
+cudaError_t add_coupled_batch_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
+                                   cudaGraphNode_t* out, const StepSlot* slots, const int2* work,
+                                   int nwork, int cur);
 
 // Resident potential loop (poisson_resident.cu).  fixed_ty > 0: tiles of 64 x fixed_ty.
 bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* threads,

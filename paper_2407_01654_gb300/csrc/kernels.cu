@@ -142,17 +142,17 @@ __global__ void k_step_set(KParams k, StepState* ss, long long n, int first) {
 // (Eq. weq62 with the lagged R of Algorithm 1).  Writes phi and the per-node potential
 // coefficients; FP64 sums of phi and q; the last CTA resets the potential loop.
 // ------------------------------------------------------------------------------------
+// Block `bid` of `nblk` blocks of 256 threads over one simulation.
 template <bool HALF>
-__global__ void __launch_bounds__(256) k_moments(KParams k, const StepState* __restrict__ ss,
-                                                 Pops pops,
-                                                 const float* __restrict__ hist,
-                                                 float* __restrict__ phi_out,
-                                                 float2* __restrict__ aq,
-                                                 double2* __restrict__ partials, Ctl* ctl,
-                                                 double tol, int min_iter, int max_iter,
-                                                 int fixed_iter) {
+__device__ __forceinline__ void moments_body(const KParams& k, const StepState* __restrict__ ss,
+                                             const Pops& pops, const float* __restrict__ hist,
+                                             float* __restrict__ phi_out,
+                                             float2* __restrict__ aq,
+                                             double2* __restrict__ partials, Ctl* ctl,
+                                             double tol, int min_iter, int max_iter,
+                                             int fixed_iter, int bid, int nblk) {
   const int N = k.N;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = bid * blockDim.x + threadIdx.x;
   float phi = 0.0f, q = 0.0f;
   int bad = 0;
   if (idx < N) {
@@ -186,10 +186,10 @@ __global__ void __launch_bounds__(256) k_moments(KParams k, const StepState* __r
       a += s_sum[w][0];
       b += s_sum[w][1];
     }
-    partials[blockIdx.x] = make_double2(a, b);
+    partials[bid] = make_double2(a, b);
     __threadfence();
     const unsigned t = atomicAdd(&ctl->ticket_m, 1u);
-    s_last = (t == gridDim.x - 1);
+    s_last = (t == (unsigned)nblk - 1u);
   }
   __syncthreads();
   if (!s_last) return;
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(256) k_moments(KParams k, const StepState* __r
   // last CTA: fixed-order FP64 reduction of the per-CTA partials
   __shared__ double s_red[256][2];
   double a = 0.0, b = 0.0;
-  for (int j = threadIdx.x; j < (int)gridDim.x; j += blockDim.x) {
+  for (int j = threadIdx.x; j < nblk; j += blockDim.x) {
     const double2 v = __ldcg(partials + j);
     a += v.x;
     b += v.y;
@@ -232,23 +232,37 @@ __global__ void __launch_bounds__(256) k_moments(KParams k, const StepState* __r
   }
 }
 
+template <bool HALF>
+__global__ void __launch_bounds__(256) k_moments(KParams k, const StepState* __restrict__ ss,
+                                                 Pops pops,
+                                                 const float* __restrict__ hist,
+                                                 float* __restrict__ phi_out,
+                                                 float2* __restrict__ aq,
+                                                 double2* __restrict__ partials, Ctl* ctl,
+                                                 double tol, int min_iter, int max_iter,
+                                                 int fixed_iter) {
+  moments_body<HALF>(k, ss, pops, hist, phi_out, aq, partials, ctl, tol, min_iter, max_iter,
+                     fixed_iter, blockIdx.x, gridDim.x);
+}
+
 // ------------------------------------------------------------------------------------
 // The fused coupled pass (a1, a2, a4-a9): stencils on phi, field from the converged
 // potential populations, chemical potential, forces, charge source, then collision of
 // g (Eq. weq45), l (Eq. weq58) and f (Eq. weq38) and the push to the neighbours with
 // half-way bounce-back; history for the next step.
 // ------------------------------------------------------------------------------------
+// Block `bid` of blocks of 128 threads over one simulation.
 template <bool HALF>
-__global__ void __launch_bounds__(128) k_coupled(KParams k, StepState* ss, int cur, Pops pin,
-                                                 Pops pout,
-                                                 const float* __restrict__ phi_f,
-                                                 const float* __restrict__ hbuf,
-                                                 float* __restrict__ hist, const Ctl* ctl,
-                                                 DevStats* stats) {
+__device__ __forceinline__ void coupled_body(const KParams& k, StepState* ss, int cur,
+                                             const Pops& pin, const Pops& pout,
+                                             const float* __restrict__ phi_f,
+                                             const float* __restrict__ hbuf,
+                                             float* __restrict__ hist, const Ctl* ctl,
+                                             DevStats* stats, int bid) {
   const int N = k.N;
   const int parity = ld_cg(&ctl->parity);
   const StepState sa = ss[cur];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (bid == 0 && threadIdx.x == 0) {
     // values of the next step, in the other slot (this step's slot is being read)
     ss[cur ^ 1] = make_step(k, sa.n + 1, 0);
     // the potential loop of this step has finished: record its statistics
@@ -264,7 +278,7 @@ __global__ void __launch_bounds__(128) k_coupled(KParams k, StepState* ss, int c
     stats->barrier_error |= ld_cg(&ctl->bar_error);
     stats->steps += 1;
   }
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = bid * blockDim.x + threadIdx.x;
   if (idx >= N) return;
   const int y = idx / k.nx, x = idx - y * k.nx;
   const float* hs = hbuf + (size_t)parity * NH * N;
@@ -379,6 +393,47 @@ __global__ void __launch_bounds__(128) k_coupled(KParams k, StepState* ss, int c
   hist[3 * (size_t)N + idx] = R;
   hist[4 * (size_t)N + idx] = Fx;
   hist[5 * (size_t)N + idx] = Fy;
+}
+
+template <bool HALF>
+__global__ void __launch_bounds__(128) k_coupled(KParams k, StepState* ss, int cur, Pops pin,
+                                                 Pops pout,
+                                                 const float* __restrict__ phi_f,
+                                                 const float* __restrict__ hbuf,
+                                                 float* __restrict__ hist, const Ctl* ctl,
+                                                 DevStats* stats) {
+  coupled_body<HALF>(k, ss, cur, pin, pout, phi_f, hbuf, hist, ctl, stats, blockIdx.x);
+}
+
+// ------------------------------------------------------------------------------------
+// Batched forms: one launch over the blocks of several simulations.  work[b] = (slot,
+// block of that slot); every simulation gets exactly the blocks and arithmetic of its own
+// launch, so its results do not depend on the others.
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_moments_batch(const StepSlot* __restrict__ slots,
+                                                       const int2* __restrict__ work, int cur) {
+  const int2 w = work[blockIdx.x];
+  const StepSlot& S = slots[w.x];
+  const Pops P = pops_copy(S.k, S.b, cur);
+  if (S.k.half)
+    moments_body<true>(S.k, S.b.ss + cur, P, S.b.hist, S.b.phi, S.b.aq, S.b.partials, S.b.ctl,
+                       S.tol, S.min_iter, S.max_iter, S.fixed_iter, w.y, S.mblocks);
+  else
+    moments_body<false>(S.k, S.b.ss + cur, P, S.b.hist, S.b.phi, S.b.aq, S.b.partials, S.b.ctl,
+                        S.tol, S.min_iter, S.max_iter, S.fixed_iter, w.y, S.mblocks);
+}
+
+__global__ void __launch_bounds__(128) k_coupled_batch(const StepSlot* __restrict__ slots,
+                                                       const int2* __restrict__ work, int cur) {
+  const int2 w = work[blockIdx.x];
+  const StepSlot& S = slots[w.x];
+  const Pops Pi = pops_copy(S.k, S.b, cur), Po = pops_copy(S.k, S.b, cur ^ 1);
+  if (S.k.half)
+    coupled_body<true>(S.k, S.b.ss, cur, Pi, Po, S.b.phi, S.b.h, S.b.hist, S.b.ctl, S.b.stats,
+                       w.y);
+  else
+    coupled_body<false>(S.k, S.b.ss, cur, Pi, Po, S.b.phi, S.b.h, S.b.hist, S.b.ctl, S.b.stats,
+                        w.y);
 }
 
 __global__ void k_stats_reset(DevStats* s) {
@@ -570,6 +625,30 @@ cudaError_t add_coupled_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t 
   p.blockDim = dim3(128);
   p.kernelParams = args;
   return cudaGraphAddKernelNode(out, g, deps, nd, &p);
+}
+
+static cudaError_t add_batch_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
+                                  cudaGraphNode_t* out, void* func, int threads,
+                                  const StepSlot* slots, const int2* work, int nwork, int cur) {
+  void* args[] = {&slots, &work, &cur};
+  cudaKernelNodeParams p = {};
+  p.func = func;
+  p.gridDim = dim3(nwork);
+  p.blockDim = dim3(threads);
+  p.kernelParams = args;
+  return cudaGraphAddKernelNode(out, g, deps, nd, &p);
+}
+
+cudaError_t add_moments_batch_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
+                                   cudaGraphNode_t* out, const StepSlot* slots, const int2* work,
+                                   int nwork, int cur) {
+  return add_batch_node(g, deps, nd, out, (void*)k_moments_batch, 256, slots, work, nwork, cur);
+}
+
+cudaError_t add_coupled_batch_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
+                                   cudaGraphNode_t* out, const StepSlot* slots, const int2* work,
+                                   int nwork, int cur) {
+  return add_batch_node(g, deps, nd, out, (void*)k_coupled_batch, 128, slots, work, nwork, cur);
 }
 
 cudaError_t add_poisson_node(cudaGraph_t g, cudaGraphNode_t* out, const KParams& kp,

@@ -134,19 +134,12 @@ __global__ void __launch_bounds__(NA_THREADS) k_poisson_noalloc(
     const float ph = __ldg(phi + idx);
     const float eh = eps_hat_of(k, ph);
     const float a = eh / (k.cs2tauh * (eh + k.cs2tauh));
-    float hs = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) hs += h[i];
-    const float varphi = hs * (9.0f / 5.0f);
-    const float m1x = h[0] - h[2] + h[4] - h[5] - h[6] + h[7];
-    const float m1y = h[1] - h[3] + h[4] + h[5] - h[6] - h[7];
+    const float varphi = h_varphi(h_sum8(h));
+    float m1x, m1y;
+    h_moment1(h, m1x, m1y);
     const float qs = 0.125f * (__ldg(q + idx) - qshift);
 #pragma unroll
-    for (int i = 1; i < 9; ++i) {
-      const float w = wgt(i);
-      const float cm = cx(i) * m1x + cy(i) * m1y;
-      sm[i - 1][ly][lx] = h[i - 1] - om * (h[i - 1] - w * varphi) + a * w * cm + qs;
-    }
+    for (int i = 1; i < 9; ++i) sm[i - 1][ly][lx] = h_star(i, h[i - 1], om, varphi, a, m1x, m1y, qs);
     if (lx >= 1 && lx <= NA_TX && ly >= 1 && ly <= NA_TY) sphi[ly - 1][lx - 1] = varphi;
   }
   __syncthreads();
@@ -157,25 +150,20 @@ __global__ void __launch_bounds__(NA_THREADS) k_poisson_noalloc(
     const int gx = x0 + lx, gy = y0 + ly;
     if (gx >= nx || gy >= ny) continue;
     const size_t idx = (size_t)gy * nx + gx;
-    float hs = 0.0f;
+    float hn[8];
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
       const int sy = gy - cy(i);
       float v;
       if (k.walls && (sy < 0 || sy >= ny)) {
-        const float vw = sy < 0 ? vw_b : vw_t;
-        v = -sm[opp(i) - 1][ly + 1][lx + 1] + 2.0f * wgt(i) * vw;
+        v = h_wall(i, sm[opp(i) - 1][ly + 1][lx + 1], sy < 0 ? vw_b : vw_t);
       } else {
         v = sm[i - 1][ly + 1 - cy(i)][lx + 1 - cx(i)];
       }
       dst[(i - 1) * N + idx] = v;
-      hs += v;
+      hn[i - 1] = v;
     }
-    const float vnew = hs * (9.0f / 5.0f);
-    const float vold = sphi[ly][lx];
-    const float d = vnew - vold;
-    num += d * d;
-    den += vold * vold;
+    h_change(h_varphi(h_sum8(hn)), sphi[ly][lx], num, den);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {

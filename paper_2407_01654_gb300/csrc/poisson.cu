@@ -65,19 +65,12 @@ __global__ void __launch_bounds__(THREADS) k_poisson(KParams k, float* __restric
 #pragma unroll
     for (int i = 0; i < 8; ++i) h[i] = __ldg(src + i * N + idx);
     const float2 c = __ldg(aq + idx);
-    float hs = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) hs += h[i];
-    const float varphi = hs * (9.0f / 5.0f);
-    const float m1x = h[0] - h[2] + h[4] - h[5] - h[6] + h[7];
-    const float m1y = h[1] - h[3] + h[4] + h[5] - h[6] - h[7];
+    const float varphi = h_varphi(h_sum8(h));
+    float m1x, m1y;
+    h_moment1(h, m1x, m1y);
     const float qs = 0.125f * (c.y - qshift);
 #pragma unroll
-    for (int i = 1; i < 9; ++i) {
-      const float w = wgt(i);
-      const float cm = cx(i) * m1x + cy(i) * m1y;
-      sm[i - 1][ly][lx] = h[i - 1] - om * (h[i - 1] - w * varphi) + c.x * w * cm + qs;
-    }
+    for (int i = 1; i < 9; ++i) sm[i - 1][ly][lx] = h_star(i, h[i - 1], om, varphi, c.x, m1x, m1y, qs);
     if (lx >= 1 && lx <= TX && ly >= 1 && ly <= TY) sphi[ly - 1][lx - 1] = varphi;
   }
   __syncthreads();
@@ -89,26 +82,21 @@ __global__ void __launch_bounds__(THREADS) k_poisson(KParams k, float* __restric
     const int gx = x0 + lx, gy = y0 + ly;
     if (gx >= nx || gy >= ny) continue;
     const size_t idx = (size_t)gy * nx + gx;
-    float hs = 0.0f;
+    float hn[8];
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
       const int sy = gy - cy(i);
       float v;
       if (k.walls && (sy < 0 || sy >= ny)) {
         // anti-bounce-back at the wall the population came from
-        const float vw = sy < 0 ? vw_b : vw_t;
-        v = -sm[opp(i) - 1][ly + 1][lx + 1] + 2.0f * wgt(i) * vw;
+        v = h_wall(i, sm[opp(i) - 1][ly + 1][lx + 1], sy < 0 ? vw_b : vw_t);
       } else {
         v = sm[i - 1][ly + 1 - cy(i)][lx + 1 - cx(i)];
       }
       dst[(i - 1) * N + idx] = v;
-      hs += v;
+      hn[i - 1] = v;
     }
-    const float vnew = hs * (9.0f / 5.0f);
-    const float vold = sphi[ly][lx];
-    const float d = vnew - vold;
-    num += d * d;
-    den += vold * vold;
+    h_change(h_varphi(h_sum8(hn)), sphi[ly][lx], num, den);
   }
 
   // reduction: FP32 in a warp, FP64 across warps and CTAs

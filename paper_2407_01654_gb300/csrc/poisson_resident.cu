@@ -187,23 +187,16 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
       const int lx = j & (TXR - 1), ly = j >> 6;
       vold[s] = 0.0f;
       if (j >= tnodes || lx >= tw) continue;
-      float hsum = 0.0f;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) hsum += h[s][i];
-      const float varphi = hsum * (9.0f / 5.0f);
+      const float varphi = h_varphi(h_sum8(h[s]));
       vold[s] = varphi;
-      const float m1x = h[s][0] - h[s][2] + h[s][4] - h[s][5] - h[s][6] + h[s][7];
-      const float m1y = h[s][1] - h[s][3] + h[s][4] + h[s][5] - h[s][6] - h[s][7];
+      float m1x, m1y;
+      h_moment1(h[s], m1x, m1y);
       const float qs = 0.125f * cq[j];
       const float a = ca[j];
       const int at = (ly + 1) * RX + lx + 1;
 #pragma unroll
-      for (int i = 1; i < 9; ++i) {
-        const float w = wgt(i);
-        const float cm = cx(i) * m1x + cy(i) * m1y;
-        const float v = h[s][i - 1] - om * (h[s][i - 1] - w * varphi) + a * w * cm + qs;
-        sm[(i - 1) * plane + at] = v;
-      }
+      for (int i = 1; i < 9; ++i)
+        sm[(i - 1) * plane + at] = h_star(i, h[s][i - 1], om, varphi, a, m1x, m1y, qs);
     }
     __syncthreads();
     // perimeter nodes export their post-collision populations for the neighbour tiles
@@ -293,7 +286,7 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
         if (nb.id < 0) {
           // beyond a wall: anti-bounce-back on the consuming node's own population
           const float vw = nby == 0 ? vw_b : vw_t;
-          v = -sm[(opp(i) - 1) * plane + (ly + 1) * RX + lx + 1] + 2.0f * wgt(i) * vw;
+          v = h_wall(i, sm[(opp(i) - 1) * plane + (ly + 1) * RX + lx + 1], vw);
         } else {
           const int olx = nbx == 0 ? nb.w - 1 : (nbx == 2 ? 0 : sxl);
           const int oly = nby == 0 ? nb.h - 1 : (nby == 2 ? 0 : syl);
@@ -314,18 +307,9 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
       const int lx = j & (TXR - 1), ly = j >> 6;
       if (j >= tnodes || lx >= tw) continue;
       const int at = (ly + 1) * RX + lx + 1;
-      float vnew = 0.0f;
 #pragma unroll
-      for (int i = 1; i < 9; ++i) {
-        const float v = sm[(i - 1) * plane + at - cy(i) * RX - cx(i)];
-        h[s][i - 1] = v;
-        vnew += v;
-      }
-      const float vn = vnew * (9.0f / 5.0f);
-      const float vo = vold[s];
-      const float d = vn - vo;
-      num += d * d;
-      den += vo * vo;
+      for (int i = 1; i < 9; ++i) h[s][i - 1] = sm[(i - 1) * plane + at - cy(i) * RX - cx(i)];
+      h_change(h_varphi(h_sum8(h[s])), vold[s], num, den);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

@@ -33,6 +33,7 @@ class Request:
     admitted: float = math.nan
     finished: float = math.nan
     steps: int = 0
+    iters: int = 0
     steady: bool = False
     capped: bool = False
     rel_change: tuple = (math.nan, math.nan)
@@ -77,6 +78,8 @@ def serve(backend, requests, clock, window=500, on_finish=None):
     live = {}
     done = []
     i = 0
+    spent = {"admit": 0.0, "run": 0.0, "poll": 0.0, "retire": 0.0}
+    serve.spent = spent
     while i < len(pending) or queue or live:
         now = clock.now()
         while i < len(pending) and pending[i].arrival <= now:
@@ -84,7 +87,9 @@ def serve(backend, requests, clock, window=500, on_finish=None):
             i += 1
         still = []
         for r in queue:
+            t0 = clock.now()
             slot = backend.admit(r.params, r.fields, r.id)
+            spent["admit"] += clock.now() - t0
             if slot is None:
                 still.append(r)
             else:
@@ -98,12 +103,18 @@ def serve(backend, requests, clock, window=500, on_finish=None):
             if queue:
                 raise RuntimeError("a queued request can never be admitted (larger than the batch)")
             break
+        t0 = clock.now()
         backend.run(window)
-        for st in backend.poll():
+        t1 = clock.now()
+        status = backend.poll()
+        spent["run"] += t1 - t0
+        spent["poll"] += clock.now() - t1
+        for st in status:
             r = live.get(st["slot"])
             if r is None:
                 continue
             r.steps = st["steps"]
+            r.iters = st.get("poisson_iters", 0)
             r.rel_change = (st["rel_change_phi"], st["rel_change_u"])
             if st["steady"] or st["capped"] or st["status"] == 5:
                 r.steady = bool(st["steady"])
@@ -111,7 +122,9 @@ def serve(backend, requests, clock, window=500, on_finish=None):
                 r.finished = clock.now()
                 if on_finish is not None:
                     on_finish(backend, st["slot"], r)
+                t0 = clock.now()
                 backend.retire(st["slot"])
+                spent["retire"] += clock.now() - t0
                 del live[st["slot"]]
                 done.append(r)
     return done
@@ -131,13 +144,16 @@ def summarize(done, wall):
         "p50_admit_to_steady_s": float(np.percentile(run, 50)) if len(run) else math.nan,
         "p99_admit_to_steady_s": float(np.percentile(run, 99)) if len(run) else math.nan,
         "steps_total": int(sum(r.steps for r in done)),
+        "node_steps_total": int(sum(r.steps * r.params["nx"] * r.params["ny"] for r in done)),
+        "poisson_iters_per_step": (float(sum(r.iters for r in done)) /
+                                   max(1, sum(r.steps for r in done))),
     }
 
 
 class OneAtATime:
     """Backend that runs one request at a time on its own simulation (no batching); with
-    plain=True it also uses the straightforward path: the streaming potential kernel with
-    the loop driven from the host (no graphs)."""
+    plain=True it also uses the straightforward path: FP32 populations, the streaming
+    potential kernel with the loop driven from the host (no graphs)."""
 
     def __init__(self, steady_tol=1e-6, step_cap=300000, plain=True):
         from . import ehd
@@ -157,12 +173,14 @@ class OneAtATime:
         p = dict(params)
         if self.plain:
             p["poisson_loop"] = 1
+            p["precision"] = 0
         self.sim = self.ehd.Sim(p)
         if self.plain:
             self.sim.profile(True)  # the host-driven loop, kernel by kernel
         self.sim.set_fields(fields["phi"], fields["q"], fields["ux"], fields["uy"])
         self.rid = rid
         self.steps = 0
+        self.iters = 0
         self.prev = None
         self.rel = (math.inf, math.inf)
         return 0
@@ -174,7 +192,8 @@ class OneAtATime:
     def run(self, n):
         if self.sim is None:
             return 0
-        self.sim.step(n, stats=False)
+        st = self.sim.step(n, stats=True)
+        self.iters += st.get("poisson_iters_total", 0)
         self.steps += n
         phi, u = self._snap()
         if self.prev is not None:
@@ -188,13 +207,22 @@ class OneAtATime:
         if self.sim is None:
             return []
         steady = self.rel[0] < self.tol and self.rel[1] < self.tol
-        return [dict(slot=0, live=1, request_id=self.rid, steps=self.steps, poisson_iters=0,
+        return [dict(slot=0, live=1, request_id=self.rid, steps=self.steps, poisson_iters=self.iters,
                      steady=int(steady), capped=int(self.steps >= self.cap), status=0,
                      rel_change_phi=self.rel[0], rel_change_u=self.rel[1])]
 
     def retire(self, slot):
         self.sim.close()
         self.sim = None
+
+
+def warm_up(backend):
+    """One tiny request through the backend before any clock starts (device context,
+    module loading, first graph instantiation)."""
+    p, f, _ = wl.droplet(N=32, r=5.0, R=1.0, S=1.0, Ca=0.1)
+    slot = backend.admit(p, f, -1)
+    backend.run(2)
+    backend.retire(slot)
 
 
 def main():
@@ -212,16 +240,21 @@ def main():
     from . import ehd
     sizes = tuple(int(x) for x in args.sizes.split(","))
     reqs = make_requests(args.requests, sizes=sizes, rate=args.rate)
-    clock = WallClock()
     b = ehd.Batch(int(args.budget_gb * (1 << 30)), max_slots=args.slots, steady_tol=args.tol,
                   step_cap=args.cap)
+    warm_up(b)
+    clock = WallClock()
     done = serve(b, reqs, clock, window=args.window)
     out = {"batched": summarize(done, clock.now())}
+    out["batched"]["seconds_in"] = dict(serve.spent)
     if args.baseline:
         reqs = make_requests(args.requests, sizes=sizes, rate=args.rate)
+        plain = OneAtATime(args.tol, args.cap)
+        warm_up(plain)
         clock = WallClock()
-        done = serve(OneAtATime(args.tol, args.cap), reqs, clock, window=args.window)
+        done = serve(plain, reqs, clock, window=args.window)
         out["one_at_a_time_plain"] = summarize(done, clock.now())
+        out["one_at_a_time_plain"]["seconds_in"] = dict(serve.spent)
     print(json.dumps(out))
 
 
