@@ -236,12 +236,21 @@ def run_gpu(args, rank, world):
         torch.distributed.barrier()
     p, f, info = workload(seed=rank)
     nodes = p["nx"] * p["ny"]
+    schedule = None
+    if not args.no_tune:
+        # launch schedule of the potential loop for this lattice shape (cached per device)
+        from paper_2407_01654_gb300 import autotune
+        schedule = autotune.tune(p, fields=f)
+        p.update(schedule)
     stream = torch.cuda.current_stream()
     sim = ehd.Sim(p, stream=stream)
     sim.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
     resident = sim.uses_resident_loop()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     sim.step(args.warmup)
+    # the state the timed steps start from: the per-kernel profile below replays exactly
+    # these steps (same sub-iteration counts)
+    start_state = sim.save_state()
 
     # timed region: K steps as step graphs, L2 flushed before each, CUDA events around
     # each step on the stream the library uses
@@ -265,15 +274,18 @@ def run_gpu(args, rank, world):
     kt_total = st["poisson_iters_total"]
     launches = st["kernel_launches"]
     step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    # per-kernel device times: a further stretch of steps with CUDA events around every
-    # launch (the same kernels, queued from the host instead of a graph)
-    prof_steps = min(args.steps, 20)
+    # per-kernel device times: the same steps again from the same state, with CUDA events
+    # around every launch (the same kernels, queued from the host instead of a graph)
+    sim.load_state(start_state)
     sim.profile(True)
-    sim.step(prof_steps, stats=False)
+    sim.step(args.steps, stats=False)
     prof = sim.profile_read()
     sim.profile(False)
     pst = sim.read_stats()
     prof_iters = pst["poisson_iters_total"]
+    if prof_iters != kt_total:
+        raise RuntimeError(f"profiled replay made {prof_iters} sub-iterations, timed steps "
+                           f"{kt_total}")
     t_local = step_ms / 1e3
     if world > 1:
         t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
@@ -357,6 +369,7 @@ def run_gpu(args, rank, world):
                    "storage": "fp32 SoA populations",
                    "potential_loop": "resident (on chip, one cooperative launch per step)"
                    if resident else "streaming (one launch per sub-iteration, graph WHILE node)",
+                   "schedule": dict(schedule, autotuned=True) if schedule else "built-in",
                    "l2": "flushed between timed steps (512 MiB device write outside the events)",
                    "step_algorithmic_bytes_per_node": step_bytes,
                    "step_hbm_roofline_frac": step_frac, "wall_s": wall},
@@ -367,9 +380,45 @@ def run_gpu(args, rank, world):
         "e2e": e2e,
     }
     line["clocks"] = clk.summary()
+    if world == 1 and not args.no_serve:
+        line["serving"] = run_serving()
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(kbar)
     print(json.dumps(line), flush=True)
+
+
+SERVE_WORKLOAD = ("32 droplet-deformation requests (Sec. 7.1 set-up), grids drawn from "
+                  "64^2/128^2/256^2/512^2 with r = 0.156 N, (R, S, Ca_E) seeded as for the "
+                  "256^2 droplet, half with FP16-deviation storage in the batched arm; "
+                  "arrivals 50/s (above both arms' capacity, so sims/hour is service "
+                  "capacity); steady when the relative change of phi and u over 500 steps "
+                  "is < 1e-6, capped at 3000 steps; 2 GB device-memory budget")
+
+
+def run_serving():
+    """Continuous-batching serving against one-at-a-time plain FP32 runs of the same
+    requests on the same GPU (each arm warmed up before its clock starts)."""
+    from paper_2407_01654_gb300 import ehd, serve
+    out = {"workload": SERVE_WORKLOAD}
+    for arm in ("batched", "one_at_a_time_plain"):
+        reqs = serve.make_requests(32, seed=0, sizes=(64, 128, 256, 512), rate=50.0)
+        if arm == "batched":
+            backend = ehd.Batch(2 << 30, max_slots=64, steady_tol=1e-6, step_cap=3000)
+        else:
+            backend = serve.OneAtATime(1e-6, 3000)
+        serve.warm_up(backend)
+        clock = serve.WallClock()
+        done = serve.serve(backend, reqs, clock, window=500)
+        summ = serve.summarize(done, clock.now())
+        out[arm] = {k: summ[k] for k in ("requests", "steady", "capped", "wall_s", "sims_per_hour",
+                                         "p50_latency_s", "p99_latency_s",
+                                         "poisson_iters_per_step")}
+        if arm == "batched":
+            out[arm]["kernel_launches"] = backend.info()["kernel_launches"]
+            backend.close()
+    out["sims_per_hour_ratio"] = (out["batched"]["sims_per_hour"] /
+                                  out["one_at_a_time_plain"]["sims_per_hour"])
+    return out
 
 
 def main():
@@ -380,6 +429,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

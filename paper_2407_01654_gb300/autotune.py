@@ -1,0 +1,152 @@
+"""Autotuner for the per-simulation launch schedule of the coupled step.
+
+For one lattice shape (nx, ny, walls, storage precision) it times every candidate
+schedule of the potential loop -- the streaming kernel (one launch per sub-iteration in a
+graph WHILE node) and the resident on-chip loop with each tile height of 64-wide tiles
+(`tile_rows`; 0 = the built-in choice of about 2048 nodes per tile) -- on a short run with
+a fixed number of sub-iterations, and returns the fastest as parameter overrides.  All
+candidates compute the same bits at a fixed sub-iteration count (the tests check this), so
+tuning changes speed only.  Results are cached per device and lattice shape in a JSON
+file ($EHD_AUTOTUNE_CACHE, else ~/.cache/paper_2407_01654_gb300/autotune.json).
+
+    from paper_2407_01654_gb300 import autotune
+    params.update(autotune.tune(params))
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import numpy as np
+
+TILE_ROWS = (0, 16, 24, 32, 40, 48, 56, 64)
+LOOP_STREAM, LOOP_RESIDENT = 1, 2
+
+
+def candidates(params):
+    """Parameter overrides to try: the streaming loop, then the resident loop at each
+    tile height (the library refuses heights whose tiles do not fit on chip)."""
+    ny = params["ny"]
+    rows = [r for r in TILE_ROWS[1:] if r <= ny]
+    taller = [r for r in TILE_ROWS[1:] if r > ny]
+    if taller:
+        rows.append(taller[0])  # one row of tiles; taller heights only add idle threads
+    out = [{"poisson_loop": LOOP_STREAM, "tile_rows": 0},
+           {"poisson_loop": LOOP_RESIDENT, "tile_rows": 0}]
+    out += [{"poisson_loop": LOOP_RESIDENT, "tile_rows": r} for r in rows]
+    return out
+
+
+def shape_key(params, device_name):
+    return (f"{device_name}|{params['nx']}x{params['ny']}|walls{params['walls_y']}"
+            f"|prec{params['precision']}")
+
+
+def cache_path():
+    p = os.environ.get("EHD_AUTOTUNE_CACHE")
+    if p:
+        return p
+    return os.path.join(os.path.expanduser("~"), ".cache", "paper_2407_01654_gb300",
+                        "autotune.json")
+
+
+def load_cache(path):
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def store_cache(path, key, entry):
+    d = load_cache(path)
+    d[key] = entry
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".tmp"
+        with open(tmp, "w") as fh:
+            json.dump(d, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass  # a read-only home only costs a re-tune
+
+
+def pick(timings):
+    """The fastest candidate; ties go to the earlier one.  timings: [(overrides, seconds
+    or None when the candidate could not run)]."""
+    best = None
+    for ov, t in timings:
+        if t is None or not np.isfinite(t):
+            continue
+        if best is None or t < best[1]:
+            best = (ov, t)
+    if best is None:
+        raise RuntimeError("no candidate schedule could run")
+    return best
+
+
+def time_candidate(params, fields, overrides, steps, fixed_iter):
+    """Seconds per step of `steps` coupled steps with `fixed_iter` sub-iterations each,
+    after two warm-up steps; None if the library rejects the schedule."""
+    from . import ehd
+    p = dict(params)
+    p.update(overrides)
+    p["poisson_fixed_iter"] = fixed_iter
+    try:
+        sim = ehd.Sim(p)
+    except ehd.EhdError:
+        return None
+    try:
+        if overrides["poisson_loop"] == LOOP_RESIDENT and not sim.uses_resident_loop():
+            return None
+        sim.set_fields(fields["phi"], fields["q"], fields["ux"], fields["uy"])
+        sim.step(2, stats=False)
+        sim.read_stats()  # synchronises
+        t0 = time.perf_counter()
+        sim.step(steps, stats=False)
+        sim.read_stats()
+        return (time.perf_counter() - t0) / steps
+    finally:
+        sim.close()
+
+
+def tune(params, fields=None, steps=20, fixed_iter=32, use_cache=True, timer=None,
+         device_name=None):
+    """Parameter overrides ({"poisson_loop", "tile_rows"}) of the fastest schedule for this
+    lattice shape.  `fields`: initial fields to time with (default: a flat interface at
+    mid-height); `timer(params, fields, overrides, steps, fixed_iter)` replaces the GPU
+    timing (tests)."""
+    if device_name is None:
+        device_name = _device_name()
+    key = shape_key(params, device_name)
+    path = cache_path()
+    if use_cache:
+        hit = load_cache(path).get(key)
+        if hit:
+            return dict(hit["overrides"])
+    if fields is None:
+        fields = _default_fields(params)
+    timer = timer or time_candidate
+    timings = [(ov, timer(params, fields, ov, steps, fixed_iter)) for ov in candidates(params)]
+    ov, t = pick(timings)
+    if use_cache:
+        store_cache(path, key, {"overrides": ov, "seconds_per_step": t,
+                                "timings": [[o, s] for o, s in timings]})
+    return dict(ov)
+
+
+def _device_name():
+    try:
+        import torch
+        return torch.cuda.get_device_name(0).replace(" ", "_")
+    except Exception:
+        return "unknown"
+
+
+def _default_fields(params):
+    ny, nx = params["ny"], params["nx"]
+    y = np.arange(ny, dtype=float)[:, None] + np.zeros((1, nx))
+    phi = 0.5 + 0.5 * np.tanh(2.0 * (ny / 2.0 - y) / params["width"])
+    z = np.zeros((ny, nx))
+    return {"phi": phi, "q": z, "ux": z, "uy": z}

@@ -94,6 +94,7 @@ int validate(const ehd_params* p) {
   if (p->ramp_steps < 0) return EHD_ERR_INVALID_ARG;
   if (p->poisson_loop < EHD_LOOP_AUTO || p->poisson_loop > EHD_LOOP_RESIDENT)
     return EHD_ERR_INVALID_ARG;
+  if (p->tile_rows < 0 || p->tile_rows > 64 || p->reserved != 0) return EHD_ERR_INVALID_ARG;
   const double lim = 0.5 + 1e-3;
   const double tau_g = 0.5 + p->mobility / CS2D;
   const double tau_h = 0.5 + p->eps_v / CS2D;
@@ -367,7 +368,8 @@ const char* ehd_error_string(int code) {
 
 int ehd_workspace_bytes(const ehd_params* params, size_t* bytes) {
   if (!params || !bytes || !sizes_ok(params)) return EHD_ERR_INVALID_ARG;
-  *bytes = layout_for(*params).total;
+  if (params->tile_rows < 0 || params->tile_rows > 64) return EHD_ERR_INVALID_ARG;
+  *bytes = layout_for(*params, params->tile_rows).total;
   return EHD_OK;
 }
 
@@ -477,7 +479,8 @@ extern "C" {
 
 int ehd_create(const ehd_params* params, void* workspace, size_t workspace_bytes, void* stream,
                ehd_sim** out) {
-  return sim_create(params, workspace, workspace_bytes, stream, 0, out);
+  return sim_create(params, workspace, workspace_bytes, stream, params ? params->tile_rows : 0,
+                    out);
 }
 
 int ehd_profile(ehd_sim* s, int enable) {

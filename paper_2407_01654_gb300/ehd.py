@@ -46,6 +46,7 @@ class Params(ctypes.Structure):
         ("poisson_tol", ctypes.c_double), ("poisson_max_iter", ctypes.c_int32),
         ("poisson_min_iter", ctypes.c_int32), ("poisson_fixed_iter", ctypes.c_int32),
         ("poisson_loop", ctypes.c_int32), ("start_step", ctypes.c_int64),
+        ("tile_rows", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
     @classmethod
