@@ -20,7 +20,7 @@ import time
 
 import numpy as np
 
-TILE_ROWS = (0, 16, 24, 32, 40, 48, 56, 64)
+TILE_ROWS = (0, 8, 16, 24, 32, 40, 48, 56, 64)
 LOOP_STREAM, LOOP_RESIDENT = 1, 2
 
 

@@ -94,7 +94,8 @@ int validate(const ehd_params* p) {
   if (p->ramp_steps < 0) return EHD_ERR_INVALID_ARG;
   if (p->poisson_loop < EHD_LOOP_AUTO || p->poisson_loop > EHD_LOOP_RESIDENT)
     return EHD_ERR_INVALID_ARG;
-  if (p->tile_rows < 0 || p->tile_rows > 64 || p->reserved != 0) return EHD_ERR_INVALID_ARG;
+  if (p->tile_rows < 0 || p->tile_rows > 64 || p->tile_rows % 8 != 0 || p->reserved != 0)
+    return EHD_ERR_INVALID_ARG;
   const double lim = 0.5 + 1e-3;
   const double tau_g = 0.5 + p->mobility / CS2D;
   const double tau_h = 0.5 + p->eps_v / CS2D;
@@ -368,7 +369,8 @@ const char* ehd_error_string(int code) {
 
 int ehd_workspace_bytes(const ehd_params* params, size_t* bytes) {
   if (!params || !bytes || !sizes_ok(params)) return EHD_ERR_INVALID_ARG;
-  if (params->tile_rows < 0 || params->tile_rows > 64) return EHD_ERR_INVALID_ARG;
+  if (params->tile_rows < 0 || params->tile_rows > 64 || params->tile_rows % 8 != 0)
+    return EHD_ERR_INVALID_ARG;
   *bytes = layout_for(*params, params->tile_rows).total;
   return EHD_OK;
 }
@@ -439,10 +441,10 @@ int sim_create(const ehd_params* params, void* workspace, size_t workspace_bytes
       if (resident_geometry(s->kp, use_sms, &g, &th, &sm, fixed_ty) &&
           2 * (size_t)g.ntx * g.nty * 8 * g.pmax <= L.export_floats &&
           (size_t)g.ntx * g.nty <= L.rtiles &&
-          cudaFuncSetAttribute(resident_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+          cudaFuncSetAttribute(resident_kernel(g.TY), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)sm) == cudaSuccess) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_kernel(), th, sm) ==
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_kernel(g.TY), th, sm) ==
                 cudaSuccess &&
             per_sm >= 1 && (long long)g.ntx * g.nty <= (long long)per_sm * sms) {
           s->resident_ok = true;

@@ -26,7 +26,7 @@ using namespace ehd;
 
 namespace {
 
-constexpr int BATCH_TY = 32;
+constexpr int BATCH_TY = BATCH_ROWS;
 constexpr int STEADY_THREADS = 256;
 constexpr int STEPS_PER_GRAPH = 16;  // even: a multi-step graph ends on the copy it began with
 

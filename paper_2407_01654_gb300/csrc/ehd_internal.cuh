@@ -287,6 +287,9 @@ struct ResidentSlot {
   Ctl* ctl;
 };
 
+// Tile height of every simulation in a batch (tiles of 64 x BATCH_ROWS nodes).
+constexpr int BATCH_ROWS = 32;
+
 // One simulation of a batch as the batched moments and coupled kernels see it.
 struct StepSlot {
   KParams k;
@@ -304,10 +307,11 @@ cudaError_t add_coupled_batch_node(cudaGraph_t g, const cudaGraphNode_t* deps, s
                                    cudaGraphNode_t* out, const StepSlot* slots, const int2* work,
                                    int nwork, int cur);
 
-// Resident potential loop (poisson_resident.cu).  fixed_ty > 0: tiles of 64 x fixed_ty.
+// Resident potential loop (poisson_resident.cu).  fixed_ty > 0: tiles of 64 x fixed_ty
+// (a multiple of 8 up to 64).
 bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* threads,
                        size_t* smem, int fixed_ty = 0);
-const void* resident_kernel();
+const void* resident_kernel(int tile_rows);  // nullptr unless a multiple of 8 up to 64
 const void* resident_batch_kernel();
 cudaError_t launch_poisson_resident(const KParams& kp, const ResidentGeom& g, int threads,
                                     size_t smem, const Buffers& b, cudaStream_t st);

@@ -1,9 +1,11 @@
 // The whole potential loop of one solve (Algorithm 1 step 3) in one cooperative launch,
 // with the potential populations held on chip.
 //
-// The lattice is cut into tiles, one CTA per tile and at most one tile per SM.  Each
-// thread keeps the post-stream populations h_1..h_8 of up to NPT nodes in registers for
-// the whole loop.  A sub-iteration (Eq. weq53, the same arithmetic as k_poisson):
+// The lattice is cut into 64 x TY tiles (TY a multiple of 8, a compile-time constant of
+// the kernel), one CTA of 16 TY threads per tile.  Thread t owns the four nodes of column
+// t mod 64 in rows t/64 + s TY/4 (s = 0..3) and keeps their post-stream populations
+// h_1..h_8 in registers for the whole loop, so every shared-memory address is a
+// per-thread base plus a constant.  A sub-iteration (Eq. weq53, the same arithmetic as k_poisson):
 //   1. collide the tile's nodes; post-collision populations go to shared memory, and
 //      those of perimeter nodes also to a per-tile export area in global memory;
 //   2. grid barrier;
@@ -37,7 +39,8 @@ namespace ehd {
 namespace {
 
 constexpr int NPT = 4;              // nodes per thread
-constexpr int MAX_THREADS = 1024;
+constexpr int TXR = 64;             // tile width
+constexpr int RX = TXR + 2;         // shared ring row: the tile row plus one node each side
 constexpr unsigned long long BARRIER_TIMEOUT_NS = 2000000000ull;  // 2 s
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -85,40 +88,48 @@ __device__ __forceinline__ int perim_slot(int lx, int ly, int w, int h) {
   return 2 * w + h + ly;  // lx == w - 1
 }
 
-// Tile width is fixed: node j of a tile sits at (j & 63, j >> 6).  Shared memory holds
-// the post-collision populations of the tile plus a one-node ring: [8][RY][RX].
-constexpr int TXR = 64;
-constexpr int RX = TXR + 2;
-
 // One of the 3 x 3 tiles around (and including) this one.
 struct Nb {
   int id;      // tile index, -1 beyond a wall
   int w, h;    // its size
 };
 
+// Compile-time shape of a 64 x TY tile.
+template <int TY>
+struct Tile {
+  static_assert(TY % 8 == 0 && TY >= 8 && TY <= 64, "tile height: a multiple of 8 up to 64");
+  static constexpr int RY = TY + 2;
+  static constexpr int PLANE = RY * RX;            // one direction's shared populations
+  static constexpr int THREADS = TXR * TY / NPT;   // 16 TY
+  static constexpr int ROWS = TY / NPT;            // rows between a thread's nodes
+  static constexpr int PMAX = 2 * TXR + 2 * TY;    // perimeter slots
+  static constexpr int SMEM = (int)sizeof(float) * (8 * PLANE + 2 * TY * TXR);
+  static constexpr int MIN_BLOCKS = THREADS >= 1024 ? 1 : (1024 / THREADS);
+};
+
 }  // namespace
 
 // The loop for one tile of one simulation; `tile` of `ntiles` tiles of that simulation.
+template <int TY>
 __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGeom& rg,
                                               float* __restrict__ hbuf,
                                               const float2* __restrict__ aq,
                                               float* __restrict__ exports,
                                               float2* __restrict__ rpartials, Ctl* ctl,
                                               const int tile, const int ntiles) {
+  using T = Tile<TY>;
   extern __shared__ float sm[];  // [8][RY][RX] populations, then [TY*64] a, [TY*64] q
-  __shared__ float2 s_w[MAX_THREADS / 32];
+  __shared__ float2 s_w[T::THREADS / 32];
   __shared__ int s_done;
   __shared__ Nb s_nb[3][3];
 
   const int nx = k.nx, ny = k.ny;
   const size_t N = (size_t)k.N;
   const int tcol = tile % rg.ntx, trow = tile / rg.ntx;
-  const int tx0 = tcol * TXR, ty0 = trow * rg.TY;
-  const int tw = min(TXR, nx - tx0), th = min(rg.TY, ny - ty0);
-  const int RY = rg.TY + 2;
-  const int plane = RY * RX;
-  float* ca = sm + 8 * plane;
-  float* cq = ca + rg.TY * TXR;
+  const int tx0 = tcol * TXR, ty0 = trow * TY;
+  const int tw = min(TXR, nx - tx0), th = min(TY, ny - ty0);
+  float* ca = sm + 8 * T::PLANE;
+  float* cq = ca + TY * TXR;
   const int parity = ld_cg(&ctl->parity);
   float* __restrict__ hsrc = hbuf + (size_t)parity * NH * N;
   const float qshift = k.neutralize ? ld_cg(&ctl->mean_q) : 0.0f;
@@ -126,8 +137,13 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
   const double tol = ctl->tol;
   const int min_iter = ctl->min_iter, max_iter = ctl->max_iter, fixed = ctl->fixed_iter;
   const float om = k.omega_h;
-  const int pstride = 8 * rg.pmax;
-  const int tnodes = TXR * th;  // node slots j < tnodes (lx < tw valid)
+  constexpr int pstride = 8 * T::PMAX;
+  // this thread's nodes: column lx, rows ly0 + s ROWS
+  const int lx = threadIdx.x & (TXR - 1);
+  const int ly0 = threadIdx.x >> 6;
+  const int at0 = (ly0 + 1) * RX + lx + 1;   // shared index of node 0 (direction 1's plane)
+  const int j0 = ly0 * TXR + lx;             // coefficient index of node 0
+  const int nrows = lx < tw ? th : 0;        // my nodes are the rows ly0 + s ROWS < nrows
 
   if (threadIdx.x < 9) {
     const int dx = (int)threadIdx.x % 3 - 1, dy = (int)threadIdx.x / 3 - 1;
@@ -147,7 +163,7 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
     if (r >= 0) {
       nb.id = r * rg.ntx + c;
       nb.w = min(TXR, nx - c * TXR);
-      nb.h = min(rg.TY, ny - r * rg.TY);
+      nb.h = min(TY, ny - r * TY);
       s_nb[dy + 1][dx + 1] = nb;
     }
   }
@@ -156,15 +172,13 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
   float h[NPT][8];
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
-    const int j = threadIdx.x + s * blockDim.x;
-    const int lx = j & (TXR - 1), ly = j >> 6;
-    if (j < tnodes && lx < tw) {
-      const int g = (ty0 + ly) * nx + tx0 + lx;
+    if (ly0 + s * T::ROWS < nrows) {
+      const int g = (ty0 + ly0 + s * T::ROWS) * nx + tx0 + lx;
 #pragma unroll
       for (int i = 0; i < 8; ++i) h[s][i] = hsrc[i * N + g];
       const float2 c = aq[g];
-      ca[j] = c.x;
-      cq[j] = c.y - qshift;
+      ca[j0 + s * T::ROWS * TXR] = c.x;
+      cq[j0 + s * T::ROWS * TXR] = c.y - qshift;
     } else {
 #pragma unroll
       for (int i = 0; i < 8; ++i) h[s][i] = 0.0f;
@@ -176,42 +190,39 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
   int it = 0;
   float rel = 0.0f;
   int conv = 0;
-  const int nwarps = (int)(blockDim.x >> 5);
-  const int dwarp = nwarps - 1;  // the warp that reduces the tiles' sums and decides
+  constexpr int dwarp = T::THREADS / 32 - 1;  // the warp that reduces the tiles' sums
   for (;;) {
     // 1. collide into the tile's shared populations; keep varphi^k per node
     float vold[NPT];
 #pragma unroll
     for (int s = 0; s < NPT; ++s) {
-      const int j = threadIdx.x + s * blockDim.x;
-      const int lx = j & (TXR - 1), ly = j >> 6;
       vold[s] = 0.0f;
-      if (j >= tnodes || lx >= tw) continue;
+      if (ly0 + s * T::ROWS >= nrows) continue;
       const float varphi = h_varphi(h_sum8(h[s]));
       vold[s] = varphi;
       float m1x, m1y;
       h_moment1(h[s], m1x, m1y);
-      const float qs = 0.125f * cq[j];
-      const float a = ca[j];
-      const int at = (ly + 1) * RX + lx + 1;
+      const float qs = 0.125f * cq[j0 + s * T::ROWS * TXR];
+      const float a = ca[j0 + s * T::ROWS * TXR];
+      const int at = at0 + s * T::ROWS * RX;
 #pragma unroll
       for (int i = 1; i < 9; ++i)
-        sm[(i - 1) * plane + at] = h_star(i, h[s][i - 1], om, varphi, a, m1x, m1y, qs);
+        sm[(i - 1) * T::PLANE + at] = h_star(i, h[s][i - 1], om, varphi, a, m1x, m1y, qs);
     }
     __syncthreads();
     // perimeter nodes export their post-collision populations for the neighbour tiles
     {
       float* exp_cur = exports + (size_t)(it & 1) * ntiles * pstride + (size_t)tile * pstride;
       const int np = 2 * tw + 2 * th;
-      for (int sl = threadIdx.x; sl < np; sl += blockDim.x) {
-        int lx, ly;
-        if (sl < tw) { lx = sl; ly = 0; }
-        else if (sl < 2 * tw) { lx = sl - tw; ly = th - 1; }
-        else if (sl < 2 * tw + th) { lx = 0; ly = sl - 2 * tw; }
-        else { lx = tw - 1; ly = sl - 2 * tw - th; }
-        const int at = (ly + 1) * RX + lx + 1;
+      for (int sl = threadIdx.x; sl < np; sl += T::THREADS) {
+        int ex, ey;
+        if (sl < tw) { ex = sl; ey = 0; }
+        else if (sl < 2 * tw) { ex = sl - tw; ey = th - 1; }
+        else if (sl < 2 * tw + th) { ex = 0; ey = sl - 2 * tw; }
+        else { ex = tw - 1; ey = sl - 2 * tw - th; }
+        const int at = (ey + 1) * RX + ex + 1;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) exp_cur[i * rg.pmax + sl] = sm[i * plane + at];
+        for (int i = 0; i < 8; ++i) exp_cur[i * T::PMAX + sl] = sm[i * T::PLANE + at];
       }
     }
     // 2. all tiles' exports (and the previous sub-iteration's partial sums) are visible
@@ -255,29 +266,29 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
     {
       const float* exp_all = exports + (size_t)(it & 1) * ntiles * pstride;
       const int nring = 6 * (tw + th);
-      for (int e = threadIdx.x; e < nring; e += blockDim.x) {
-        int lx, ly, i;
+      for (int e = threadIdx.x; e < nring; e += T::THREADS) {
+        int bx, by, i;
         if (e < 3 * th) {                 // west boundary, directions with cx = +1
-          ly = e / 3; lx = 0;
-          const int kk = e - 3 * ly;
+          by = e / 3; bx = 0;
+          const int kk = e - 3 * by;
           i = kk == 0 ? 1 : (kk == 1 ? 5 : 8);
         } else if (e < 6 * th) {          // east boundary, cx = -1
           const int f = e - 3 * th;
-          ly = f / 3; lx = tw - 1;
-          const int kk = f - 3 * ly;
+          by = f / 3; bx = tw - 1;
+          const int kk = f - 3 * by;
           i = kk == 0 ? 3 : (kk == 1 ? 6 : 7);
         } else if (e < 6 * th + 3 * tw) { // south boundary, cy = +1
           const int f = e - 6 * th;
-          lx = f / 3; ly = 0;
-          const int kk = f - 3 * lx;
+          bx = f / 3; by = 0;
+          const int kk = f - 3 * bx;
           i = kk == 0 ? 2 : (kk == 1 ? 5 : 6);
         } else {                          // north boundary, cy = -1
           const int f = e - 6 * th - 3 * tw;
-          lx = f / 3; ly = th - 1;
-          const int kk = f - 3 * lx;
+          bx = f / 3; by = th - 1;
+          const int kk = f - 3 * bx;
           i = kk == 0 ? 4 : (kk == 1 ? 7 : 8);
         }
-        const int sxl = lx - cx(i), syl = ly - cy(i);
+        const int sxl = bx - cx(i), syl = by - cy(i);
         if (sxl >= 0 && sxl < tw && syl >= 0 && syl < th) continue;  // inside the tile
         const int nbx = sxl < 0 ? 0 : (sxl >= tw ? 2 : 1);
         const int nby = syl < 0 ? 0 : (syl >= th ? 2 : 1);
@@ -286,14 +297,14 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
         if (nb.id < 0) {
           // beyond a wall: anti-bounce-back on the consuming node's own population
           const float vw = nby == 0 ? vw_b : vw_t;
-          v = h_wall(i, sm[(opp(i) - 1) * plane + (ly + 1) * RX + lx + 1], vw);
+          v = h_wall(i, sm[(opp(i) - 1) * T::PLANE + (by + 1) * RX + bx + 1], vw);
         } else {
           const int olx = nbx == 0 ? nb.w - 1 : (nbx == 2 ? 0 : sxl);
           const int oly = nby == 0 ? nb.h - 1 : (nby == 2 ? 0 : syl);
-          v = __ldcg(exp_all + (size_t)nb.id * pstride + (i - 1) * rg.pmax +
+          v = __ldcg(exp_all + (size_t)nb.id * pstride + (i - 1) * T::PMAX +
                      perim_slot(olx, oly, nb.w, nb.h));
         }
-        sm[(i - 1) * plane + (syl + 1) * RX + sxl + 1] = v;
+        sm[(i - 1) * T::PLANE + (syl + 1) * RX + sxl + 1] = v;
       }
     }
     __syncthreads();
@@ -303,12 +314,10 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
     float num = 0.0f, den = 0.0f;
 #pragma unroll
     for (int s = 0; s < NPT; ++s) {
-      const int j = threadIdx.x + s * blockDim.x;
-      const int lx = j & (TXR - 1), ly = j >> 6;
-      if (j >= tnodes || lx >= tw) continue;
-      const int at = (ly + 1) * RX + lx + 1;
+      if (ly0 + s * T::ROWS >= nrows) continue;
+      const int at = at0 + s * T::ROWS * RX;
 #pragma unroll
-      for (int i = 1; i < 9; ++i) h[s][i - 1] = sm[(i - 1) * plane + at - cy(i) * RX - cx(i)];
+      for (int i = 1; i < 9; ++i) h[s][i - 1] = sm[(i - 1) * T::PLANE + at - cy(i) * RX - cx(i)];
       h_change(h_varphi(h_sum8(h[s])), vold[s], num, den);
     }
 #pragma unroll
@@ -319,6 +328,7 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = make_float2(num, den);
     __syncthreads();  // shared populations consumed; warp sums visible
     if (threadIdx.x < 32) {
+      constexpr int nwarps = T::THREADS / 32;
       float2 v = (int)threadIdx.x < nwarps ? s_w[threadIdx.x] : make_float2(0.0f, 0.0f);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -333,10 +343,8 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
   // the registers hold the final state: write it back in place
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
-    const int j = threadIdx.x + s * blockDim.x;
-    const int lx = j & (TXR - 1), ly = j >> 6;
-    if (j >= tnodes || lx >= tw) continue;
-    const int g = (ty0 + ly) * nx + tx0 + lx;
+    if (ly0 + s * T::ROWS >= nrows) continue;
+    const int g = (ty0 + ly0 + s * T::ROWS) * nx + tx0 + lx;
 #pragma unroll
     for (int i = 0; i < 8; ++i) hsrc[i * N + g] = h[s][i];
   }
@@ -348,34 +356,54 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
   }
 }
 
-__global__ void __launch_bounds__(MAX_THREADS, 1)
+template <int TY>
+__global__ void __launch_bounds__(Tile<TY>::THREADS, Tile<TY>::MIN_BLOCKS)
     k_poisson_resident(KParams k, ResidentGeom rg, float* __restrict__ hbuf,
                        const float2* __restrict__ aq, float* __restrict__ exports,
                        float2* __restrict__ rpartials, Ctl* ctl) {
-  resident_loop(k, rg, hbuf, aq, exports, rpartials, ctl, blockIdx.x, gridDim.x);
+  resident_loop<TY>(k, rg, hbuf, aq, exports, rpartials, ctl, blockIdx.x, gridDim.x);
 }
 
-// Several simulations in one cooperative launch: CTA b runs tile work[b].y of simulation
-// work[b].x.  Simulations exchange nothing, so each synchronises only its own tiles (its
-// own barrier counter and partial sums) and stops at its own sub-iteration count.
-__global__ void __launch_bounds__(MAX_THREADS, 1)
+// Several simulations in one cooperative launch, all tiled 64 x BATCH_ROWS: CTA b runs
+// tile work[b].y of simulation work[b].x.  Simulations exchange nothing, so each
+// synchronises only its own tiles (its own barrier counter and partial sums) and stops at
+// its own sub-iteration count.
+__global__ void __launch_bounds__(Tile<BATCH_ROWS>::THREADS, Tile<BATCH_ROWS>::MIN_BLOCKS)
     k_poisson_resident_batch(const ResidentSlot* __restrict__ slots,
                              const int2* __restrict__ work) {
   const int2 w = work[blockIdx.x];
   const ResidentSlot& S = slots[w.x];
-  resident_loop(S.k, S.rg, S.h, S.aq, S.exports, S.rpartials, S.ctl, w.y,
-                S.rg.ntx * S.rg.nty);
+  resident_loop<BATCH_ROWS>(S.k, S.rg, S.h, S.aq, S.exports, S.rpartials, S.ctl, w.y,
+                            S.rg.ntx * S.rg.nty);
 }
 
+// The kernel of a tile height (nullptr: not a supported height).
+const void* resident_kernel(int ty) {
+  switch (ty) {
+    case 8: return (const void*)k_poisson_resident<8>;
+    case 16: return (const void*)k_poisson_resident<16>;
+    case 24: return (const void*)k_poisson_resident<24>;
+    case 32: return (const void*)k_poisson_resident<32>;
+    case 40: return (const void*)k_poisson_resident<40>;
+    case 48: return (const void*)k_poisson_resident<48>;
+    case 56: return (const void*)k_poisson_resident<56>;
+    case 64: return (const void*)k_poisson_resident<64>;
+    default: return nullptr;
+  }
+}
+const void* resident_batch_kernel() { return (const void*)k_poisson_resident_batch; }
+
 // Tile geometry for the resident loop, or false if the lattice does not fit on chip with
-// one tile per SM.
+// one tile per SM.  Heights are rounded up to a multiple of 8.
 bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* threads,
                        size_t* smem, int fixed_ty) {
   const long long N = (long long)kp.nx * kp.ny;
   const int ntx = (kp.nx + TXR - 1) / TXR;
   int TY, nty;
   if (fixed_ty > 0) {
-    // fixed 64 x fixed_ty tiles (batches: a simulation tiles the same way in any mix)
+    // fixed 64 x fixed_ty tiles (autotuned schedules; batches: a simulation tiles the
+    // same way in any mix)
+    if (fixed_ty % 8 != 0 || fixed_ty > 64) return false;
     TY = fixed_ty;
     nty = (kp.ny + TY - 1) / TY;
   } else {
@@ -387,7 +415,8 @@ bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* thr
     if (nty < 1) nty = 1;
     if (nty > num_sms / ntx) nty = num_sms / ntx;
     TY = (kp.ny + nty - 1) / nty;
-    if (TY > TXR) return false;
+    TY = (TY + 7) / 8 * 8;
+    if (TY > 64) return false;
     nty = (kp.ny + TY - 1) / TY;
   }
   g->TX = TXR;
@@ -395,20 +424,15 @@ bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* thr
   g->ntx = ntx;
   g->nty = nty;
   g->pmax = 2 * TXR + 2 * TY;
-  int t = (TXR * TY + NPT - 1) / NPT;
-  t = (t + 31) / 32 * 32;
-  *threads = t < 32 ? 32 : t;
+  *threads = TXR * TY / NPT;
   *smem = sizeof(float) * (8 * (size_t)(TY + 2) * RX + 2 * (size_t)TY * TXR);
   return true;
 }
 
-int resident_nodes_per_thread() { return NPT; }
-
-const void* resident_kernel() { return (const void*)k_poisson_resident; }
-const void* resident_batch_kernel() { return (const void*)k_poisson_resident_batch; }
-
 cudaError_t launch_poisson_resident(const KParams& kp, const ResidentGeom& g, int threads,
                                     size_t smem, const Buffers& b, cudaStream_t st) {
+  const void* f = resident_kernel(g.TY);
+  if (!f) return cudaErrorInvalidValue;
   KParams k = kp;
   ResidentGeom gg = g;
   float* h = b.h;
@@ -417,14 +441,15 @@ cudaError_t launch_poisson_resident(const KParams& kp, const ResidentGeom& g, in
   float2* rp = b.rpartials;
   Ctl* ctl = b.ctl;
   void* args[] = {&k, &gg, &h, &aq, &ex, &rp, &ctl};
-  return cudaLaunchCooperativeKernel((const void*)k_poisson_resident, dim3(g.ntx * g.nty),
-                                     dim3(threads), args, smem, st);
+  return cudaLaunchCooperativeKernel(f, dim3(g.ntx * g.nty), dim3(threads), args, smem, st);
 }
 
 cudaError_t add_poisson_resident_node(cudaGraph_t graph, const cudaGraphNode_t* deps, size_t nd,
                                       cudaGraphNode_t* out, const KParams& kp,
                                       const ResidentGeom& g, int threads, size_t smem,
                                       const Buffers& b) {
+  const void* f = resident_kernel(g.TY);
+  if (!f) return cudaErrorInvalidValue;
   KParams k = kp;
   ResidentGeom gg = g;
   float* h = b.h;
@@ -434,7 +459,7 @@ cudaError_t add_poisson_resident_node(cudaGraph_t graph, const cudaGraphNode_t* 
   Ctl* ctl = b.ctl;
   void* args[] = {&k, &gg, &h, &aq, &ex, &rp, &ctl};
   cudaKernelNodeParams p = {};
-  p.func = (void*)k_poisson_resident;
+  p.func = const_cast<void*>(f);
   p.gridDim = dim3(g.ntx * g.nty);
   p.blockDim = dim3(threads);
   p.sharedMemBytes = (unsigned)smem;
