@@ -208,9 +208,9 @@ __device__ __forceinline__ T ld_cg(const T* p) { return __ldcg(p); }
 //
 // varphi = (sum_{i>0} h_i) / (1 - w_0) = 9/5 sum h_i (Eq. weq55); m1 = sum c_i h_i.
 __device__ __forceinline__ float h_sum8(const float (&h)[8]) {
-  float s = 0.0f;
+  float s = h[0];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) s = __fadd_rn(s, h[i]);
+  for (int i = 1; i < 8; ++i) s = __fadd_rn(s, h[i]);
   return s;
 }
 __device__ __forceinline__ float h_varphi(float hsum) { return __fmul_rn(hsum, 9.0f / 5.0f); }
@@ -236,6 +236,47 @@ __device__ __forceinline__ float h_star(int i, float hi, float om, float varphi,
 __device__ __forceinline__ float h_wall(int i, float h_opp_star, float vw) {
   return __fmaf_rn(2.0f * wgt(i), vw, -h_opp_star);
 }
+// The same arithmetic on two nodes at once (packed FP32 pairs; each component rounds as
+// the scalar form above, so the results are bit-identical to it).
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ float2 h_sum8x2(const float2 (&h)[8]) {
+  float2 s = h[0];
+#pragma unroll
+  for (int i = 1; i < 8; ++i) s = __fadd2_rn(s, h[i]);
+  return s;
+}
+__device__ __forceinline__ float2 h_varphi2(float2 hsum) { return __fmul2_rn(hsum, f2(9.0f / 5.0f)); }
+__device__ __forceinline__ void h_moment1x2(const float2 (&h)[8], float2& m1x, float2& m1y) {
+  m1x = __fadd2_rn(__fadd2_rn(__fadd2_rn(__fadd2_rn(__fadd2_rn(h[0], neg2(h[2])), h[4]),
+                                         neg2(h[5])), neg2(h[6])), h[7]);
+  m1y = __fadd2_rn(__fadd2_rn(__fadd2_rn(__fadd2_rn(__fadd2_rn(h[1], neg2(h[3])), h[4]), h[5]),
+                              neg2(h[6])), neg2(h[7]));
+}
+// Post-collision h_1*..h_8* of two nodes.  c_i.m1 is +-m1x, +-m1y, +-(m1x + m1y) or
+// +-(m1x - m1y); its sign is moved onto a w_i (exact), which the scalar form rounds alike.
+__device__ __forceinline__ void h_star8x2(const float2 (&h)[8], float om, float2 varphi, float2 a,
+                                          float2 m1x, float2 m1y, float2 qs, float2 (&out)[8]) {
+  const float2 aw1 = __fmul2_rn(a, f2(wgt(1))), aw2 = __fmul2_rn(a, f2(wgt(5)));
+  const float2 dp = __fadd2_rn(m1x, m1y), dm = __fadd2_rn(m1x, neg2(m1y));
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    const float w = wgt(i);
+    float2 coef, m;
+    if (i <= 4) {
+      coef = (cx(i) + cy(i)) > 0 ? aw1 : neg2(aw1);
+      m = cx(i) != 0 ? m1x : m1y;
+    } else {
+      coef = cx(i) > 0 ? aw2 : neg2(aw2);
+      m = cx(i) == cy(i) ? dp : dm;
+    }
+    float2 v = __ffma2_rn(f2(-w), varphi, h[i - 1]);
+    v = __ffma2_rn(f2(-om), v, h[i - 1]);
+    v = __ffma2_rn(coef, m, v);
+    out[i - 1] = __fadd2_rn(v, qs);
+  }
+}
+
 // Stopping sums: (varphi^{k+1} - varphi^k)^2 and (varphi^k)^2 added to num, den.
 __device__ __forceinline__ void h_change(float vnew, float vold, float& num, float& den) {
   const float d = __fsub_rn(vnew, vold);

@@ -168,20 +168,37 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
     }
   }
 
-  // state of my nodes: registers; coefficients: shared memory
-  float h[NPT][8];
+  // state of my nodes: registers, as two pairs (nodes 0, 1 and 2, 3) for packed FP32
+  // arithmetic; coefficients: shared memory.  Nodes outside the lattice (partial tiles)
+  // compute along with their pair but never enter a sum, an export or the result, and
+  // every shared-memory cell they write lies inside the tile's array and is either never
+  // read by a lattice node or rewritten by the ring fill before it is.
+  float2 h[2][8];
+  bool valid[NPT];
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
-    if (ly0 + s * T::ROWS < nrows) {
+    valid[s] = ly0 + s * T::ROWS < nrows;
+    float v[8];
+    float a = 0.0f, q = 0.0f;
+    if (valid[s]) {
       const int g = (ty0 + ly0 + s * T::ROWS) * nx + tx0 + lx;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) h[s][i] = hsrc[i * N + g];
+      for (int i = 0; i < 8; ++i) v[i] = hsrc[i * N + g];
       const float2 c = aq[g];
-      ca[j0 + s * T::ROWS * TXR] = c.x;
-      cq[j0 + s * T::ROWS * TXR] = c.y - qshift;
+      a = c.x;
+      q = c.y - qshift;
     } else {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) h[s][i] = 0.0f;
+      for (int i = 0; i < 8; ++i) v[i] = 0.0f;
+    }
+    ca[j0 + s * T::ROWS * TXR] = a;
+    cq[j0 + s * T::ROWS * TXR] = q;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (s & 1)
+        h[s >> 1][i].y = v[i];
+      else
+        h[s >> 1][i].x = v[i];
     }
   }
   __syncthreads();
@@ -193,21 +210,23 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
   constexpr int dwarp = T::THREADS / 32 - 1;  // the warp that reduces the tiles' sums
   for (;;) {
     // 1. collide into the tile's shared populations; keep varphi^k per node
-    float vold[NPT];
+    float2 vold[2];
 #pragma unroll
-    for (int s = 0; s < NPT; ++s) {
-      vold[s] = 0.0f;
-      if (ly0 + s * T::ROWS >= nrows) continue;
-      const float varphi = h_varphi(h_sum8(h[s]));
-      vold[s] = varphi;
-      float m1x, m1y;
-      h_moment1(h[s], m1x, m1y);
-      const float qs = 0.125f * cq[j0 + s * T::ROWS * TXR];
-      const float a = ca[j0 + s * T::ROWS * TXR];
-      const int at = at0 + s * T::ROWS * RX;
+    for (int p = 0; p < 2; ++p) {
+      const int o0 = 2 * p * T::ROWS, o1 = (2 * p + 1) * T::ROWS;  // row offsets of the pair
+      const float2 varphi = h_varphi2(h_sum8x2(h[p]));
+      vold[p] = varphi;
+      float2 m1x, m1y;
+      h_moment1x2(h[p], m1x, m1y);
+      const float2 a = make_float2(ca[j0 + o0 * TXR], ca[j0 + o1 * TXR]);
+      const float2 qs = __fmul2_rn(f2(0.125f), make_float2(cq[j0 + o0 * TXR], cq[j0 + o1 * TXR]));
+      float2 hs[8];
+      h_star8x2(h[p], om, varphi, a, m1x, m1y, qs, hs);
 #pragma unroll
-      for (int i = 1; i < 9; ++i)
-        sm[(i - 1) * T::PLANE + at] = h_star(i, h[s][i - 1], om, varphi, a, m1x, m1y, qs);
+      for (int i = 0; i < 8; ++i) {
+        sm[i * T::PLANE + at0 + o0 * RX] = hs[i].x;
+        sm[i * T::PLANE + at0 + o1 * RX] = hs[i].y;
+      }
     }
     __syncthreads();
     // perimeter nodes export their post-collision populations for the neighbour tiles
@@ -313,12 +332,22 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
     // 4b. stream: every source is now in shared memory
     float num = 0.0f, den = 0.0f;
 #pragma unroll
-    for (int s = 0; s < NPT; ++s) {
-      if (ly0 + s * T::ROWS >= nrows) continue;
-      const int at = at0 + s * T::ROWS * RX;
+    for (int p = 0; p < 2; ++p) {
+      const int o0 = 2 * p * T::ROWS, o1 = (2 * p + 1) * T::ROWS;
 #pragma unroll
-      for (int i = 1; i < 9; ++i) h[s][i - 1] = sm[(i - 1) * T::PLANE + at - cy(i) * RX - cx(i)];
-      h_change(h_varphi(h_sum8(h[s])), vold[s], num, den);
+      for (int i = 1; i < 9; ++i) {
+        const int off = (i - 1) * T::PLANE + at0 - cy(i) * RX - cx(i);
+        h[p][i - 1] = make_float2(sm[off + o0 * RX], sm[off + o1 * RX]);
+      }
+      const float2 d = __fadd2_rn(h_varphi2(h_sum8x2(h[p])), neg2(vold[p]));
+      if (valid[2 * p]) {
+        num = __fmaf_rn(d.x, d.x, num);
+        den = __fmaf_rn(vold[p].x, vold[p].x, den);
+      }
+      if (valid[2 * p + 1]) {
+        num = __fmaf_rn(d.y, d.y, num);
+        den = __fmaf_rn(vold[p].y, vold[p].y, den);
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -343,10 +372,10 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
   // the registers hold the final state: write it back in place
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
-    if (ly0 + s * T::ROWS >= nrows) continue;
+    if (!valid[s]) continue;
     const int g = (ty0 + ly0 + s * T::ROWS) * nx + tx0 + lx;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) hsrc[i * N + g] = h[s][i];
+    for (int i = 0; i < 8; ++i) hsrc[i * N + g] = (s & 1) ? h[s >> 1][i].y : h[s >> 1][i].x;
   }
   if (tile == 0 && (int)threadIdx.x == dwarp * 32) {
     ctl->iter = it;
