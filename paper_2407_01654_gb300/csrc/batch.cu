@@ -246,7 +246,7 @@ int rebuild(ehd_batch* b) {
     q.min_iter = s->P.poisson_min_iter;
     q.max_iter = s->P.poisson_max_iter;
     q.fixed_iter = s->P.poisson_fixed_iter;
-    q.mblocks = (s->kp.N + 255) / 256;
+    q.mblocks = moments_blocks(s->kp.N);
     for (int t = 0; t < q.mblocks; ++t) mwork.push_back(make_int2((int)j, t));
     const int cb = (s->kp.N + 127) / 128;
     for (int t = 0; t < cb; ++t) cwork.push_back(make_int2((int)j, t));
@@ -345,7 +345,7 @@ int ehd_batch_create(size_t hbm_budget, int max_slots, double steady_tol, int64_
   // device tables at the start of the arena; a slot's nodes never exceed its tiles x 2048,
   // which bounds the work lists of the moments (256 nodes a block) and coupled (128) passes
   const size_t max_nodes = (size_t)b->tile_capacity * 64 * BATCH_TY;
-  b->mwork_cap = (int)(max_nodes / 256) + max_slots;
+  b->mwork_cap = (int)(max_nodes / 256) + max_slots;  // moments_blocks(N) <= N / 256 + 1
   b->cwork_cap = (int)(max_nodes / 128) + max_slots;
   const size_t t1 = al256(sizeof(ResidentSlot) * (size_t)max_slots);
   const size_t t2 = al256(sizeof(int2) * (size_t)b->tile_capacity);

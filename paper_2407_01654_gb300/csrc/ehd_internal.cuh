@@ -33,6 +33,12 @@ constexpr int NH = 8;      // h_1..h_8
 constexpr int NHIST = 6;
 constexpr int NIO = 8;
 constexpr int MAX_PARTIALS = 1 << 16;
+// The moments pass runs at most this many CTAs of 256 threads (one wave on the GPU), each
+// thread striding over the lattice, so the per-CTA reduction tails overlap.
+constexpr int MOMENTS_MAX_BLOCKS = 1216;
+__host__ __device__ constexpr int moments_blocks(int n) {
+  return (n + 255) / 256 < MOMENTS_MAX_BLOCKS ? (n + 255) / 256 : MOMENTS_MAX_BLOCKS;
+}
 
 __host__ __device__ constexpr int cx(int i) {
   return i == 1 || i == 5 || i == 8 ? 1 : (i == 3 || i == 6 || i == 7 ? -1 : 0);
@@ -337,7 +343,7 @@ struct StepSlot {
   Buffers b;
   double tol;
   int min_iter, max_iter, fixed_iter;
-  int mblocks;       // moments blocks of this simulation (256 nodes each)
+  int mblocks;       // moments blocks of this simulation (moments_blocks(N))
 };
 
 // Batched moments / coupled passes: one launch over work[] = (slot, block of that slot).

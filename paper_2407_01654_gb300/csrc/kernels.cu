@@ -152,10 +152,10 @@ __device__ __forceinline__ void moments_body(const KParams& k, const StepState* 
                                              double tol, int min_iter, int max_iter,
                                              int fixed_iter, int bid, int nblk) {
   const int N = k.N;
-  const int idx = bid * blockDim.x + threadIdx.x;
-  float phi = 0.0f, q = 0.0f;
+  float phi_acc = 0.0f, q_acc = 0.0f;
   int bad = 0;
-  if (idx < N) {
+  for (int idx = bid * blockDim.x + threadIdx.x; idx < N; idx += nblk * blockDim.x) {
+    float phi = 0.0f, q = 0.0f;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       phi += ld_pop<HALF>(k, pops, 0, i, idx);
@@ -167,55 +167,63 @@ __device__ __forceinline__ void moments_body(const KParams& k, const StepState* 
     const float a = eh / (k.cs2tauh * den);
     phi_out[idx] = phi;
     aq[idx] = make_float2(a, q);
-    bad = !(isfinite(phi) && isfinite(q));
+    bad |= !(isfinite(phi) && isfinite(q));
+    phi_acc += phi;
+    q_acc += q;
   }
-  // FP32 within a warp, FP64 across warps and CTAs
-  __shared__ double s_sum[8][2];
-  __shared__ int s_last;
-  const float wp = warp_sum(phi), wq = warp_sum(q);
+  // FP32 within a warp, FP64 across warps and CTAs.  Only warp 0 stays for the CTA's
+  // FP64 tail (the FP64 units are slow: the other warps leave at once).
+  __shared__ float2 s_sum[8];
+  const float wp = warp_sum(phi_acc), wq = warp_sum(q_acc);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) {
-    s_sum[warp][0] = (double)wp;
-    s_sum[warp][1] = (double)wq;
-  }
+  if (lane == 0) s_sum[warp] = make_float2(wp, wq);
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&ctl->nonfinite, 1);
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      a += s_sum[w][0];
-      b += s_sum[w][1];
-    }
+  if (warp != 0) return;
+  const int nw = (int)(blockDim.x >> 5);
+  double a = 0.0, b = 0.0;
+  if (lane < nw) {
+    a = (double)s_sum[lane].x;
+    b = (double)s_sum[lane].y;
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {  // fixed tree over the (at most 8) warps
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  unsigned t = 0;
+  if (lane == 0) {
     partials[bid] = make_double2(a, b);
     __threadfence();
-    const unsigned t = atomicAdd(&ctl->ticket_m, 1u);
-    s_last = (t == (unsigned)nblk - 1u);
+    t = atomicAdd(&ctl->ticket_m, 1u);
   }
-  __syncthreads();
-  if (!s_last) return;
+  t = __shfl_sync(0xffffffffu, t, 0);
+  if (t != (unsigned)nblk - 1u) return;
   __threadfence();
-  // last CTA: fixed-order FP64 reduction of the per-CTA partials
-  __shared__ double s_red[256][2];
-  double a = 0.0, b = 0.0;
-  for (int j = threadIdx.x; j < nblk; j += blockDim.x) {
-    const double2 v = __ldcg(partials + j);
-    a += v.x;
-    b += v.y;
-  }
-  s_red[threadIdx.x][0] = a;
-  s_red[threadIdx.x][1] = b;
-  __syncthreads();
-  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) {
-      s_red[threadIdx.x][0] += s_red[threadIdx.x + o][0];
-      s_red[threadIdx.x][1] += s_red[threadIdx.x + o][1];
+  // last CTA, warp 0: fixed-order FP64 reduction of the per-CTA partials (four
+  // interleaved accumulators per lane, then a fixed shuffle tree)
+  double ra[4] = {0.0, 0.0, 0.0, 0.0}, rb[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int j = lane; j < nblk; j += 128) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (j + 32 * u < nblk) {
+        const double2 v = __ldcg(partials + j + 32 * u);
+        ra[u] += v.x;
+        rb[u] += v.y;
+      }
     }
-    __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    ctl->sum_phi = s_red[0][0];
-    ctl->sum_q = s_red[0][1];
-    ctl->mean_q = (float)(s_red[0][1] / (double)N);
+  double sa = (ra[0] + ra[1]) + (ra[2] + ra[3]);
+  double sb = (rb[0] + rb[1]) + (rb[2] + rb[3]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+  }
+  if (lane == 0) {
+    ctl->sum_phi = sa;
+    ctl->sum_q = sb;
+    ctl->mean_q = (float)(sb / (double)N);
     ctl->iter = 0;
     ctl->done = 0;
     ctl->converged = 0;
@@ -542,8 +550,7 @@ cudaError_t launch_init(const KParams& kp, const Buffers& b, int cur, bool have_
 
 cudaError_t launch_moments(const KParams& kp, const Buffers& b, int cur, double tol,
                            int min_iter, int max_iter, int fixed_iter, cudaStream_t st) {
-  const int nb = blocks_for(kp.N, 256);
-  if (nb > MAX_PARTIALS) return cudaErrorInvalidValue;
+  const int nb = moments_blocks(kp.N);
   const Pops P = pops_copy(kp, b, cur);
   if (kp.half)
     k_moments<true><<<nb, 256, 0, st>>>(kp, b.ss + cur, P, b.hist, b.phi, b.aq, b.partials,
@@ -601,7 +608,7 @@ cudaError_t add_moments_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t 
                   &fixed_iter};
   cudaKernelNodeParams p = {};
   p.func = kp.half ? (void*)k_moments<true> : (void*)k_moments<false>;
-  p.gridDim = dim3(blocks_for(kp.N, 256));
+  p.gridDim = dim3(moments_blocks(kp.N));
   p.blockDim = dim3(256);
   p.kernelParams = args;
   return cudaGraphAddKernelNode(out, g, deps, nd, &p);
