@@ -66,6 +66,9 @@ enum {
 };
 #define EHD_NUM_FIELDS 8
 
+/* Potential LBE schemes (ehd_params.potential_scheme). */
+enum { EHD_SCHEME_IMPROVED = 0, EHD_SCHEME_CONVENTIONAL = 1 };
+
 /* Parameters, lattice units.  Phase l is phi = 1, phase v is phi = 0 (Sec. 2.2). */
 typedef struct ehd_params {
   int32_t nx, ny;               /* lattice size; x is periodic                           */
@@ -106,7 +109,13 @@ typedef struct ehd_params {
                                    other values: EHD_ERR_INVALID_ARG.  Results
                                    do not depend on the tiling at a fixed sub-iteration
                                    count.  Batches always tile 64 x 32                    */
-  int32_t reserved;             /* must be 0                                              */
+  int32_t potential_scheme;     /* EHD_SCHEME_IMPROVED: the paper's potential LBE with the
+                                   large-ratio forcing (Eq. weq53); EHD_SCHEME_CONVENTIONAL:
+                                   the conventional scheme of Sec. 3.3 (no forcing,
+                                   eps(phi) = chi c_s^2 (tau_varphi - 1/2)), kept as the
+                                   paper's comparison baseline; it always runs the
+                                   streaming loop                                         */
+  double chi;                   /* conventional scheme: the artificial factor chi > 0     */
 } ehd_params;
 
 /* Statistics of one ehd_step call. */

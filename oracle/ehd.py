@@ -112,6 +112,8 @@ class Params:
     poisson_fixed_iter: int = 0   # > 0: exactly this many sub-iterations, no stopping test
     neutralize_charge: bool = False
     start_step: int = 0
+    potential_scheme: int = 0     # 0: the paper's scheme (Eq. weq53); 1: conventional
+    chi: float = 1.0              # conventional scheme: eps = chi c_s^2 (tau_varphi - 1/2)
 
     @classmethod
     def from_dict(cls, d):
@@ -441,6 +443,46 @@ def poisson_collide(P, h, eps_hat, qsrc):
     return out
 
 
+# The conventional potential LBE (Sec. 3.3, the scheme of Chai et al. the paper compares
+# against): no discrete forcing; instead the relaxation time follows the permittivity,
+# eps(phi) = chi c_s^2 (tau_varphi - 1/2) dt with an artificial factor chi.
+
+
+def tau_phi_conventional(P, phi):
+    """tau_varphi(x) = 1/2 + eps(phi(x)) / (chi c_s^2 dt), from the relation of Sec. 3.3."""
+    return 0.5 + eps_of(P, phi) / (P.chi * CS2)
+
+
+def grad_varphi_conventional(P, h, tau_phi):
+    """Local potential gradient of the conventional scheme: its first moment relaxes with
+    tau_varphi, sum_i c_i h_i = -c_s^2 tau_varphi dt grad varphi (Eq. eqA.16 with
+    eps_hat = 0 and tau_h replaced by the local tau_varphi)."""
+    mx = sum(CX[i] * h[i] for i in range(9))
+    my = sum(CY[i] * h[i] for i in range(9))
+    den = CS2 * tau_phi
+    return -mx / den, -my / den
+
+
+def poisson_collide_conventional(P, h, tau_phi, qsrc):
+    """One collision of the conventional potential LBE:
+    h* = h - (h - h_eq)/tau_varphi + dt varpi_i q / chi.
+    Its steady state solves div(c_s^2 (tau_varphi - 1/2) grad varphi) + q / chi = 0, which
+    is div(eps grad varphi) + q = 0 (the equation before Eq. weq52) divided by chi."""
+    heq = h_eq(varphi_of(h))
+    out = np.empty_like(h)
+    for i in range(9):
+        out[i] = h[i] - (h[i] - heq[i]) / tau_phi + VARPI[i] * qsrc / P.chi
+    return out
+
+
+def potential_gradient(P, h, phi):
+    """grad varphi from the local first moment of the scheme in use (phi: the phase field
+    the potential was solved with)."""
+    if P.potential_scheme == 1:
+        return grad_varphi_conventional(P, h, tau_phi_conventional(P, phi))
+    return grad_varphi_local(P, h, eps_hat_of(P, phi))
+
+
 def poisson_solve(P, h, phi, q, varphi_w, tol=None, max_iter=None, fixed_iter=None,
                   min_iter=None):
     """Poisson inner loop of Algorithm 1 (step 3) with phi and q held fixed.
@@ -457,12 +499,17 @@ def poisson_solve(P, h, phi, q, varphi_w, tol=None, max_iter=None, fixed_iter=No
     fixed_iter = P.poisson_fixed_iter if fixed_iter is None else fixed_iter
     min_iter = P.poisson_min_iter if min_iter is None else min_iter
     eps_hat = eps_hat_of(P, phi)
+    tau_phi = tau_phi_conventional(P, phi) if P.potential_scheme == 1 else None
     qsrc = q - q.mean() if P.neutralize_charge else q
     varphi_old = varphi_of(h)
     it = 0
     rel = math.inf
     while True:
-        h = stream(P, poisson_collide(P, h, eps_hat, qsrc), "abb", varphi_w)
+        if P.potential_scheme == 1:
+            post = poisson_collide_conventional(P, h, tau_phi, qsrc)
+        else:
+            post = poisson_collide(P, h, eps_hat, qsrc)
+        h = stream(P, post, "abb", varphi_w)
         it += 1
         varphi_new = varphi_of(h)
         num = float(np.sum((varphi_new - varphi_old) ** 2))
@@ -636,9 +683,8 @@ class Sim:
         vw = wall_potentials(P, n)
         self.h, it, rel, ok = poisson_solve(P, self.h, phi, q, vw)
         self.phi_poisson = phi
-        eps_hat = eps_hat_of(P, phi)
         # a4: E = -grad varphi from the converged h (Eq. eqA.16)
-        gvx, gvy = grad_varphi_local(P, self.h, eps_hat)
+        gvx, gvy = potential_gradient(P, self.h, phi)
         Ex, Ey = -gvx, -gvy
         # a5: chemical potential (Eq. weq31), force (Eq. weq30), charge source (Eq. weq57)
         mu_c = chemical_potential(P, phi, lap_phi, Ex, Ey)
@@ -703,6 +749,6 @@ class Sim:
         gx, gy = gradient(ext)
         p = self._pressure(phi, rho, ux, uy, gx, gy)
         varphi = varphi_of(self.h)
-        gvx, gvy = grad_varphi_local(P, self.h, eps_hat_of(P, self.phi_poisson))
+        gvx, gvy = potential_gradient(P, self.h, self.phi_poisson)
         return {"phi": phi, "q": q, "varphi": varphi, "Ex": -gvx, "Ey": -gvy,
                 "ux": ux, "uy": uy, "p": p}

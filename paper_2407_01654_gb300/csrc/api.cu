@@ -94,8 +94,9 @@ int validate(const ehd_params* p) {
   if (p->ramp_steps < 0) return EHD_ERR_INVALID_ARG;
   if (p->poisson_loop < EHD_LOOP_AUTO || p->poisson_loop > EHD_LOOP_RESIDENT)
     return EHD_ERR_INVALID_ARG;
-  if (p->tile_rows < 0 || p->tile_rows > 64 || p->tile_rows % 8 != 0 || p->reserved != 0)
+  if (p->tile_rows < 0 || p->tile_rows > 64 || p->tile_rows % 8 != 0)
     return EHD_ERR_INVALID_ARG;
+  if (p->potential_scheme != EHD_SCHEME_IMPROVED || !(p->chi > 0)) return EHD_ERR_INVALID_ARG;
   const double lim = 0.5 + 1e-3;
   const double tau_g = 0.5 + p->mobility / CS2D;
   const double tau_h = 0.5 + p->eps_v / CS2D;

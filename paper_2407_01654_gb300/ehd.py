@@ -46,7 +46,8 @@ class Params(ctypes.Structure):
         ("poisson_tol", ctypes.c_double), ("poisson_max_iter", ctypes.c_int32),
         ("poisson_min_iter", ctypes.c_int32), ("poisson_fixed_iter", ctypes.c_int32),
         ("poisson_loop", ctypes.c_int32), ("start_step", ctypes.c_int64),
-        ("tile_rows", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("tile_rows", ctypes.c_int32), ("potential_scheme", ctypes.c_int32),
+        ("chi", ctypes.c_double),
     ]
 
     @classmethod
