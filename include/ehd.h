@@ -225,7 +225,9 @@ int ehd_profile_read(ehd_sim* sim, ehd_kernel_times* out);
  * The paper has no counterpart: it is a deployment variant of the solve, not a step of
  * the method.
  *   params   lattice, permittivities, walls, wall potentials (ramp fraction at
- *            start_step), neutralize_charge and the potential-loop rule;
+ *            start_step), neutralize_charge and the potential-loop rule; the paper's
+ *            scheme only (potential_scheme other than EHD_SCHEME_IMPROVED:
+ *            EHD_ERR_INVALID_ARG);
  *   phi, q   device float32 [ny][nx], read only;
  *   h        device float32 [8][ny][nx]: h_1..h_8 in, the solved populations out;
  *   h_work   device float32 [8][ny][nx], overwritten (the loop alternates between the two);
@@ -288,7 +290,8 @@ typedef struct ehd_batch_info_t {
 int ehd_batch_create(size_t hbm_budget, int max_slots, double steady_tol, int64_t step_cap,
                      void* arena, void* stream, ehd_batch** out);
 /* Admits a request (host double fields [ny][nx], as ehd_set_fields).  EHD_ERR_BUSY when no
- * slot, arena space or on-chip tile capacity is free; the batch is then unchanged. */
+ * slot, arena space or on-chip tile capacity is free; the batch is then unchanged.
+ * EHD_ERR_INVALID_ARG for the conventional potential scheme (batches run the paper's). */
 int ehd_batch_admit(ehd_batch* b, const ehd_params* params, const double* phi, const double* q,
                     const double* ux, const double* uy, int64_t request_id, int* slot);
 /* Advances every live slot by nsteps steps, then measures steadiness and statistics

@@ -96,7 +96,10 @@ int validate(const ehd_params* p) {
     return EHD_ERR_INVALID_ARG;
   if (p->tile_rows < 0 || p->tile_rows > 64 || p->tile_rows % 8 != 0)
     return EHD_ERR_INVALID_ARG;
-  if (p->potential_scheme != EHD_SCHEME_IMPROVED || !(p->chi > 0)) return EHD_ERR_INVALID_ARG;
+  if ((p->potential_scheme != EHD_SCHEME_IMPROVED &&
+       p->potential_scheme != EHD_SCHEME_CONVENTIONAL) ||
+      !(p->chi > 0))
+    return EHD_ERR_INVALID_ARG;
   const double lim = 0.5 + 1e-3;
   const double tau_g = 0.5 + p->mobility / CS2D;
   const double tau_h = 0.5 + p->eps_v / CS2D;
@@ -111,6 +114,8 @@ int validate(const ehd_params* p) {
     const double sig = p->sigma_v + (p->sigma_l - p->sigma_v) * phi;
     if (tau_f <= lim) return EHD_ERR_UNSTABLE_PARAMS;
     if (sig / eps > 0.5) return EHD_ERR_UNSTABLE_PARAMS;
+    if (p->potential_scheme == EHD_SCHEME_CONVENTIONAL && 0.5 + eps / (p->chi * CS2D) <= lim)
+      return EHD_ERR_UNSTABLE_PARAMS;
   }
   return EHD_OK;
 }
@@ -143,6 +148,9 @@ KParams make_kparams(const ehd_params& P) {
   k.pref_l = (float)(1.0 - 0.5 / tau_l);
   k.omega_h = (float)(1.0 / tau_h);
   k.cs2tauh = (float)(CS2D * tau_h);
+  k.scheme = P.potential_scheme;
+  k.inv_chi = (float)(1.0 / P.chi);
+  k.inv_chi_cs2 = (float)(1.0 / (P.chi * CS2D));
   k.gbx = (float)P.body_gx;
   k.gby = (float)P.body_gy;
   const double pi = 3.14159265358979323846;
@@ -434,7 +442,8 @@ int sim_create(const ehd_params* params, void* workspace, size_t workspace_bytes
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess &&
-        coop && L.export_floats && params->poisson_loop != EHD_LOOP_STREAM) {
+        coop && L.export_floats && params->poisson_loop != EHD_LOOP_STREAM &&
+        params->potential_scheme == EHD_SCHEME_IMPROVED) {
       const int use_sms = sms < DESIGN_SMS ? sms : DESIGN_SMS;
       ResidentGeom g;
       int th;

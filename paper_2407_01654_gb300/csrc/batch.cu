@@ -370,6 +370,8 @@ int ehd_batch_admit(ehd_batch* b, const ehd_params* params, const double* phi, c
                     const double* ux, const double* uy, int64_t request_id, int* slot) {
   if (!b || !params || !phi || !q || !ux || !uy || !slot) return EHD_ERR_INVALID_ARG;
   if (params->nx < 1 || params->ny < 1) return EHD_ERR_INVALID_ARG;
+  // batches run the on-chip loop, which implements the paper's scheme only
+  if (params->potential_scheme != EHD_SCHEME_IMPROVED) return EHD_ERR_INVALID_ARG;
   int idx = -1;
   for (int i = 0; i < (int)b->slots.size(); ++i)
     if (!b->slots[i].live) {

@@ -75,6 +75,9 @@ struct KParams {
   float pref_l;             // 1 - 1 / (2 tau_l)
   float omega_h;            // 1 / tau_h
   float cs2tauh;            // c_s^2 tau_h
+  int scheme;               // potential LBE: 0 the paper's (Eq. weq53), 1 conventional
+  float inv_chi;            // conventional: 1 / chi
+  float inv_chi_cs2;        // conventional: 1 / (chi c_s^2)
   float gbx, gby;           // body acceleration
   // ramped wall values (double: evaluated once per step by one thread)
   double cos_yb, cos_yt;    // cosines of the Young angles
@@ -195,6 +198,23 @@ struct DevStats {
 __device__ __forceinline__ float eps_hat_of(const KParams& k, float phi) {
   return phi * phi * (2.0f * phi - 3.0f) * k.deps;
 }
+
+// Per-node coefficient of the potential collision, kept in aq[].x: the paper's scheme
+// a = eps_hat / (c_s^2 tau_h (eps_hat + c_s^2 tau_h)) (forcing through the local first
+// moment, Eq. eqA.16); the conventional scheme its relaxation rate 1 / tau_varphi with
+// tau_varphi = 1/2 + eps(phi) / (chi c_s^2) (Sec. 3.3).
+__device__ __forceinline__ float potential_coef(const KParams& k, float phi) {
+  const float eh = eps_hat_of(k, phi);
+  if (k.scheme == 1) return 1.0f / (0.5f + (k.eps_v + eh) * k.inv_chi_cs2);
+  return eh / (k.cs2tauh * (eh + k.cs2tauh));
+}
+// The denominator d of grad varphi = -sum_i c_i h_i / d: eps_hat + c_s^2 tau_h
+// (Eq. eqA.16), or c_s^2 tau_varphi for the conventional scheme.
+__device__ __forceinline__ float potential_den(const KParams& k, float phi) {
+  const float eh = eps_hat_of(k, phi);
+  if (k.scheme == 1) return (1.0f / 3.0f) * (0.5f + (k.eps_v + eh) * k.inv_chi_cs2);
+  return eh + k.cs2tauh;
+}
 __device__ __forceinline__ float deps_of(const KParams& k, float phi) {
   return 6.0f * phi * (phi - 1.0f) * k.deps;
 }
@@ -236,6 +256,14 @@ __device__ __forceinline__ float h_star(int i, float hi, float om, float varphi,
   float v = __fmaf_rn(-w, varphi, hi);
   v = __fmaf_rn(-om, v, hi);
   v = __fmaf_rn(__fmul_rn(a, w), cm, v);
+  return __fadd_rn(v, qs);
+}
+// Conventional scheme (Sec. 3.3): h_i - (h_i - w_i varphi) / tau_varphi + q / (8 chi),
+// om_x = 1 / tau_varphi of the node, qs = q / (8 chi).
+__device__ __forceinline__ float h_star_conv(int i, float hi, float om_x, float varphi,
+                                             float qs) {
+  float v = __fmaf_rn(-wgt(i), varphi, hi);
+  v = __fmaf_rn(-om_x, v, hi);
   return __fadd_rn(v, qs);
 }
 // Anti-bounce-back at a Dirichlet wall of potential vw: -h_opp* + 2 w_i vw.

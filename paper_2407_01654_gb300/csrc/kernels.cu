@@ -162,11 +162,8 @@ __device__ __forceinline__ void moments_body(const KParams& k, const StepState* 
       q += ld_pop<HALF>(k, pops, 1, i, idx);
     }
     q += 0.5f * __ldg(hist + 3 * (size_t)N + idx);
-    const float eh = eps_hat_of(k, phi);
-    const float den = eh + k.cs2tauh;
-    const float a = eh / (k.cs2tauh * den);
     phi_out[idx] = phi;
-    aq[idx] = make_float2(a, q);
+    aq[idx] = make_float2(potential_coef(k, phi), q);
     bad |= !(isfinite(phi) && isfinite(q));
     phi_acc += phi;
     q_acc += q;
@@ -334,7 +331,7 @@ __device__ __forceinline__ void coupled_body(const KParams& k, StepState* ss, in
   const float m1x = hv[0] - hv[2] + hv[4] - hv[5] - hv[6] + hv[7];
   const float m1y = hv[1] - hv[3] + hv[4] + hv[5] - hv[6] - hv[7];
   const float eh = eps_hat_of(k, phi);
-  const float inv_den = 1.0f / (eh + k.cs2tauh);
+  const float inv_den = 1.0f / potential_den(k, phi);
   const float Ex = m1x * inv_den, Ey = m1y * inv_den;
 
   // a5: chemical potential (Eq. weq31), force (Eq. weq30), charge source (Eq. weq57)
@@ -513,7 +510,7 @@ __global__ void k_fields(KParams k, const StepState* __restrict__ ss, Pops pops,
   const float varphi = hsum * (9.0f / 5.0f);
   const float m1x = hv[0] - hv[2] + hv[4] - hv[5] - hv[6] + hv[7];
   const float m1y = hv[1] - hv[3] + hv[4] + hv[5] - hv[6] - hv[7];
-  const float inv_den = 1.0f / (eps_hat_of(k, __ldg(phi_solve + idx)) + k.cs2tauh);
+  const float inv_den = 1.0f / potential_den(k, __ldg(phi_solve + idx));
   const float vals[8] = {phi, q, varphi, m1x * inv_den, m1y * inv_den, ux, uy, p};
   int slot = 0;
 #pragma unroll

@@ -265,7 +265,8 @@ extern "C" int ehd_potential_solve_noalloc(const ehd_params* params, const float
   const ehd_params& P = *params;
   if (P.nx < 1 || P.ny < 1 || (P.walls_y != 0 && P.walls_y != 1) || !(P.eps_v > 0) ||
       !(P.eps_l > 0) || P.poisson_max_iter < 1 || P.poisson_min_iter < 1 ||
-      P.poisson_fixed_iter < 0 || (P.poisson_fixed_iter == 0 && !(P.poisson_tol > 0)))
+      P.poisson_fixed_iter < 0 || (P.poisson_fixed_iter == 0 && !(P.poisson_tol > 0)) ||
+      P.potential_scheme != EHD_SCHEME_IMPROVED)
     return EHD_ERR_INVALID_ARG;
   const int gx = (P.nx + NA_TX - 1) / NA_TX, gy = (P.ny + NA_TY - 1) / NA_TY;
   if ((long long)gx * gy > NA_MAX_CTAS) return EHD_ERR_TOO_LARGE;

@@ -68,9 +68,16 @@ __global__ void __launch_bounds__(THREADS) k_poisson(KParams k, float* __restric
     const float varphi = h_varphi(h_sum8(h));
     float m1x, m1y;
     h_moment1(h, m1x, m1y);
-    const float qs = 0.125f * (c.y - qshift);
+    if (k.scheme == 1) {
+      const float qs = 0.125f * ((c.y - qshift) * k.inv_chi);
 #pragma unroll
-    for (int i = 1; i < 9; ++i) sm[i - 1][ly][lx] = h_star(i, h[i - 1], om, varphi, c.x, m1x, m1y, qs);
+      for (int i = 1; i < 9; ++i) sm[i - 1][ly][lx] = h_star_conv(i, h[i - 1], c.x, varphi, qs);
+    } else {
+      const float qs = 0.125f * (c.y - qshift);
+#pragma unroll
+      for (int i = 1; i < 9; ++i)
+        sm[i - 1][ly][lx] = h_star(i, h[i - 1], om, varphi, c.x, m1x, m1y, qs);
+    }
     if (lx >= 1 && lx <= TX && ly >= 1 && ly <= TY) sphi[ly - 1][lx - 1] = varphi;
   }
   __syncthreads();
