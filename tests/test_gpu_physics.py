@@ -99,3 +99,24 @@ def test_droplet_deformation_table1(gpu, R, S, Ca, present):
     assert np.sign(D) == np.sign(feng) == np.sign(an.taylor_D(R, S, Ca)) == np.sign(present)
     assert abs(D - feng) <= 0.25 * abs(feng) + 0.005
     assert abs(D / present - 1) < 0.20
+
+
+def test_electrowetting_young_lippmann(gpu):
+    """Electrowetting equilibrium (Sec. 6.3, Fig. 4b) at the paper's set-up (200 x 100,
+    r = 25, density and viscosity ratio 100, permittivity ratio 81): after the two-stage
+    relaxation cos(theta_B) is linear in eta/d with slope 1 +- 0.1, every point within
+    0.02 of Young-Lippmann, and the gas permittivity (eps_v = 1 or 0.5) changes the angles
+    by less than 0.5 degrees."""
+    import electrowetting as ew
+    cy = math.cos(math.radians(110.0))
+    fits = []
+    for eps_v in (1.0, 0.5):
+        theta1, pts = ew.sweep(gpu, eps_v=eps_v)
+        assert abs(theta1 - 110.0) < 2.0
+        e = np.array([p[0] for p in pts])
+        c = np.array([math.cos(math.radians(p[1])) for p in pts])
+        slope, icpt = np.polyfit(e, c, 1)
+        assert abs(slope - 1.0) < 0.1 and abs(icpt - cy) < 0.03, (slope, icpt)
+        assert np.abs(c - (cy + e)).max() < 0.02
+        fits.append(np.array([p[1] for p in pts]))
+    assert np.abs(fits[0] - fits[1]).max() < 0.5
