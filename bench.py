@@ -153,9 +153,20 @@ class ClockSampler:
 
 
 # Mean potential sub-iterations per step of this workload with the paper's stopping rule
-# over the benchmark's window (steps 10005-10055), measured on the GPU; the CPU arms scale
-# their per-sub-iteration cost to it.
-WORKLOAD_K = 364.18
+# over the default benchmark window (20 warm-up steps, then 200 timed steps from step
+# 10000), measured on the GPU; the reference arm scales the oracle's per-sub-iteration cost
+# to it (the GPU arm's own cpu_baseline uses the K of its run).
+WORKLOAD_K = 117.52
+
+
+def reduce_max(value, device):
+    """The largest `value` over the ranks of the default process group (the slowest rank's
+    time); `device` is where the reduction tensor lives ("cuda" with NCCL, "cpu" with
+    gloo)."""
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
 
 
 def oracle_step_costs(k1=4, k2=12):
@@ -287,12 +298,7 @@ def run_gpu(args, rank, world):
         raise RuntimeError(f"profiled replay made {prof_iters} sub-iterations, timed steps "
                            f"{kt_total}")
     t_local = step_ms / 1e3
-    if world > 1:
-        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
+    t_max = reduce_max(t_local, "cuda") if world > 1 else t_local
     value = world * nodes * args.steps / t_max / 1e6
     kbar = kt_total / args.steps
     # e2e through the C ABI with host buffers: set_fields (host -> device), the same
