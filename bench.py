@@ -39,8 +39,10 @@ WORKLOAD = ("reversed-electrowetting sessile drop, 512x1024 lattice (r=80, rho/m
             "eps ratio 20, ramped potential), full coupled step, potential rule tol 1e-5")
 # algorithmic bytes per node (FP32 populations read once and written once per pass):
 # coupled pass: 27 populations read + written (216 B) + 6 lagged quantities read + written
-# (48 B); potential sub-iteration: 8 populations read + written (64 B) + (a, q) read (8 B).
-BYTES_COUPLED = 216 + 48
+# (48 B) + the 8 converged potential populations its local field needs (32 B) + phi for
+# the stencils (4 B, each value read once); potential sub-iteration: 8 populations read +
+# written (64 B) + (a, q) read (8 B).
+BYTES_COUPLED = 216 + 48 + 32 + 4
 BYTES_POTENTIAL = 64 + 8
 # FP32 operations per node and potential sub-iteration (collision: moments 18, eight
 # relaxations with forcing and source 8 x 8; stream and stopping sums 14), counted from
