@@ -116,6 +116,12 @@ typedef struct ehd_params {
                                    paper's comparison baseline; it always runs the
                                    streaming loop                                         */
   double chi;                   /* conventional scheme: the artificial factor chi > 0     */
+  int32_t field_mode;           /* E used in hbar, F and R (and returned): 0 the local
+                                   first moment of the converged h (Eq. eqA.16); 1 the
+                                   isotropic stencil (Sec. 3.2) on varphi (Eq. weq55)
+                                   with ghost rows 2 varphi_w - varphi at the electrodes  */
+  int32_t lagged_field;         /* 1: hbar of step n uses E of step n-1 (the order in
+                                   which Algorithm 1 lists the LBEs); 0: E of step n     */
 } ehd_params;
 
 /* Statistics of one ehd_step call. */

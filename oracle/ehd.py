@@ -114,6 +114,8 @@ class Params:
     start_step: int = 0
     potential_scheme: int = 0     # 0: the paper's scheme (Eq. weq53); 1: conventional
     chi: float = 1.0              # conventional scheme: eps = chi c_s^2 (tau_varphi - 1/2)
+    field_mode: int = 0           # E outside the h forcing: 0 local (Eq. eqA.16), 1 stencil
+    lagged_field: int = 0         # 1: hbar of step n uses E of step n-1 (Alg. 1's order)
 
     @classmethod
     def from_dict(cls, d):
@@ -483,6 +485,37 @@ def potential_gradient(P, h, phi):
     return grad_varphi_local(P, h, eps_hat_of(P, phi))
 
 
+def extend_potential_with_ghosts(P, varphi, varphi_w):
+    """varphi on an (ny+2, nx+2) frame for the stencil: x periodic; at a wall half-way
+    between row 0 and the ghost row the potential is the Dirichlet value varphi_w, so the
+    ghost row is its linear extension 2 varphi_w - varphi(row 0) (top wall alike).
+    reading: the paper gives no stencil rule for varphi at an electrode."""
+    ny, nx = varphi.shape
+    ext = np.empty((ny + 2, nx + 2))
+    ext[1:-1, 1:-1] = varphi
+    if P.walls_y:
+        ext[0, 1:-1] = 2.0 * varphi_w[0] - varphi[0]
+        ext[-1, 1:-1] = 2.0 * varphi_w[1] - varphi[-1]
+    else:
+        ext[0, 1:-1] = varphi[-1]
+        ext[-1, 1:-1] = varphi[0]
+    ext[:, 0] = ext[:, -2]
+    ext[:, -1] = ext[:, 1]
+    return ext
+
+
+def electric_field(P, h, phi, varphi_w):
+    """E = -grad varphi for the chemical potential, force and charge source (a4).
+    field_mode 0: the local first moment of the scheme in use (Eq. eqA.16); field_mode 1:
+    the isotropic stencil of Sec. 3.2 on varphi of Eq. weq55 (the variant of the reading
+    that E outside the h forcing is local)."""
+    if P.field_mode == 1:
+        gx, gy = gradient(extend_potential_with_ghosts(P, varphi_of(h), varphi_w))
+    else:
+        gx, gy = potential_gradient(P, h, phi)
+    return -gx, -gy
+
+
 def poisson_solve(P, h, phi, q, varphi_w, tol=None, max_iter=None, fixed_iter=None,
                   min_iter=None):
     """Poisson inner loop of Algorithm 1 (step 3) with phi and q held fixed.
@@ -572,6 +605,9 @@ class Sim:
         self.Jy_prev = np.zeros(shape)
         self.history_valid = False
         self.phi_poisson = np.zeros(shape)   # phi the last Poisson solve used
+        self.vw_poisson = (0.0, 0.0)         # wall potentials of the last Poisson solve
+        self.Ex_prev = np.zeros(shape)       # E of the previous step (lagged_field)
+        self.Ey_prev = np.zeros(shape)
 
     # -- initialisation (Algorithm 1, step 1) ---------------------------------------
     def set_fields(self, phi0, q0, ux0, uy0, p0=None):
@@ -644,6 +680,7 @@ class Sim:
         self.h, it, rel, ok = poisson_solve(self.P, self.h, phi, q, vw, tol=tol,
                                             max_iter=max_iter)
         self.phi_poisson = phi
+        self.vw_poisson = vw
         return it, rel, ok
 
     # -- one coupled step (Algorithm 1, steps 2-6) -------------------------------------
@@ -683,11 +720,16 @@ class Sim:
         vw = wall_potentials(P, n)
         self.h, it, rel, ok = poisson_solve(P, self.h, phi, q, vw)
         self.phi_poisson = phi
-        # a4: E = -grad varphi from the converged h (Eq. eqA.16)
-        gvx, gvy = potential_gradient(P, self.h, phi)
-        Ex, Ey = -gvx, -gvy
-        # a5: chemical potential (Eq. weq31), force (Eq. weq30), charge source (Eq. weq57)
-        mu_c = chemical_potential(P, phi, lap_phi, Ex, Ey)
+        self.vw_poisson = vw
+        # a4: E = -grad varphi from the converged h (Eq. eqA.16, or the stencil variant)
+        Ex, Ey = electric_field(P, self.h, phi, vw)
+        # a5: chemical potential (Eq. weq31), force (Eq. weq30), charge source (Eq. weq57).
+        # lagged_field: Algorithm 1 lists the Cahn-Hilliard LBE before the potential solve,
+        # so hbar there can only see the previous step's field (the same at the first step)
+        if P.lagged_field and self.history_valid:
+            mu_c = chemical_potential(P, phi, lap_phi, self.Ex_prev, self.Ey_prev)
+        else:
+            mu_c = chemical_potential(P, phi, lap_phi, Ex, Ey)
         Fx, Fy = body_force(P, mu_c, gphi_x, gphi_y, q, Ex, Ey, rho)
         R = charge_source(P, phi, q, gphi_x, gphi_y, Ex, Ey)
         p = self._pressure(phi, rho, ux, uy, gphi_x, gphi_y)
@@ -730,6 +772,8 @@ class Sim:
         self.s_prev = s_adv
         self.Jx_prev = Jx
         self.Jy_prev = Jy
+        self.Ex_prev = Ex
+        self.Ey_prev = Ey
         self.history_valid = True
         self.n += 1
         return it, rel, ok
@@ -749,6 +793,6 @@ class Sim:
         gx, gy = gradient(ext)
         p = self._pressure(phi, rho, ux, uy, gx, gy)
         varphi = varphi_of(self.h)
-        gvx, gvy = potential_gradient(P, self.h, self.phi_poisson)
-        return {"phi": phi, "q": q, "varphi": varphi, "Ex": -gvx, "Ey": -gvy,
+        Ex, Ey = electric_field(P, self.h, self.phi_poisson, self.vw_poisson)
+        return {"phi": phi, "q": q, "varphi": varphi, "Ex": Ex, "Ey": Ey,
                 "ux": ux, "uy": uy, "p": p}

@@ -100,6 +100,7 @@ int validate(const ehd_params* p) {
        p->potential_scheme != EHD_SCHEME_CONVENTIONAL) ||
       !(p->chi > 0))
     return EHD_ERR_INVALID_ARG;
+  if (p->field_mode != 0 || p->lagged_field != 0) return EHD_ERR_INVALID_ARG;
   const double lim = 0.5 + 1e-3;
   const double tau_g = 0.5 + p->mobility / CS2D;
   const double tau_h = 0.5 + p->eps_v / CS2D;

@@ -47,7 +47,8 @@ class Params(ctypes.Structure):
         ("poisson_min_iter", ctypes.c_int32), ("poisson_fixed_iter", ctypes.c_int32),
         ("poisson_loop", ctypes.c_int32), ("start_step", ctypes.c_int64),
         ("tile_rows", ctypes.c_int32), ("potential_scheme", ctypes.c_int32),
-        ("chi", ctypes.c_double),
+        ("chi", ctypes.c_double), ("field_mode", ctypes.c_int32),
+        ("lagged_field", ctypes.c_int32),
     ]
 
     @classmethod

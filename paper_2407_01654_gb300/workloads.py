@@ -32,7 +32,8 @@ PARAM_DEFAULTS = dict(
     varphi_bottom=0.0, varphi_top=0.0, ramp_steps=0, neutralize_charge=0,
     body_gx=0.0, body_gy=0.0,
     poisson_tol=1e-5, poisson_max_iter=100000, poisson_min_iter=1, poisson_fixed_iter=0,
-    poisson_loop=0, start_step=0, tile_rows=0, potential_scheme=0, chi=1.0,
+    poisson_loop=0, start_step=0, tile_rows=0, potential_scheme=0, chi=1.0, field_mode=0,
+    lagged_field=0,
 )
 
 
