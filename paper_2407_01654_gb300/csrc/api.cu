@@ -100,7 +100,8 @@ int validate(const ehd_params* p) {
        p->potential_scheme != EHD_SCHEME_CONVENTIONAL) ||
       !(p->chi > 0))
     return EHD_ERR_INVALID_ARG;
-  if (p->field_mode != 0 || p->lagged_field != 0) return EHD_ERR_INVALID_ARG;
+  if ((p->field_mode != 0 && p->field_mode != 1) || (p->lagged_field != 0 && p->lagged_field != 1))
+    return EHD_ERR_INVALID_ARG;
   const double lim = 0.5 + 1e-3;
   const double tau_g = 0.5 + p->mobility / CS2D;
   const double tau_h = 0.5 + p->eps_v / CS2D;
@@ -150,6 +151,8 @@ KParams make_kparams(const ehd_params& P) {
   k.omega_h = (float)(1.0 / tau_h);
   k.cs2tauh = (float)(CS2D * tau_h);
   k.scheme = P.potential_scheme;
+  k.field_fd = P.field_mode;
+  k.lagged = P.lagged_field;
   k.inv_chi = (float)(1.0 / P.chi);
   k.inv_chi_cs2 = (float)(1.0 / (P.chi * CS2D));
   k.gbx = (float)P.body_gx;

@@ -10,7 +10,8 @@
 //   h[2][8][N]      post-stream potential populations h_1..h_8, two copies.  h_0 is not
 //                   stored: it never enters varphi (Eq. weq55), grad varphi (Eq. eqA.16)
 //                   or any other population, so it cannot influence any result;
-//   hist[6][N]      lagged quantities s = u.grad phi, J = q u (x, y), R, F (x, y);
+//   hist[8][N]      lagged quantities s = u.grad phi, J = q u (x, y), R, F (x, y), and
+//                   E (x, y) of the previous step (used by the lagged-field variant);
 //   phi[N]          phi of the current step (input of the stencils and of the
 //                   potential coefficient);
 //   aq[N]           float2 per node: (a, q) with a = eps_hat / (c_s^2 tau_h (eps_hat +
@@ -30,7 +31,7 @@ namespace ehd {
 constexpr int Q9 = 9;
 constexpr int NPOP = 27;   // g, l, f
 constexpr int NH = 8;      // h_1..h_8
-constexpr int NHIST = 6;
+constexpr int NHIST = 8;
 constexpr int NIO = 8;
 constexpr int MAX_PARTIALS = 1 << 16;
 // The moments pass runs at most this many CTAs of 256 threads (one wave on the GPU), each
@@ -76,6 +77,8 @@ struct KParams {
   float omega_h;            // 1 / tau_h
   float cs2tauh;            // c_s^2 tau_h
   int scheme;               // potential LBE: 0 the paper's (Eq. weq53), 1 conventional
+  int field_fd;             // E outside the forcing: 0 local first moment, 1 stencil on varphi
+  int lagged;               // 1: hbar of step n uses E of step n-1
   float inv_chi;            // conventional: 1 / chi
   float inv_chi_cs2;        // conventional: 1 / (chi c_s^2)
   float gbx, gby;           // body acceleration

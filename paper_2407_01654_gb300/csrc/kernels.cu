@@ -63,6 +63,51 @@ __device__ __forceinline__ void grad_lap(const Stencil& s, float& gx, float& gy,
         s.c * (10.0f / 3.0f);
 }
 
+// varphi = 9/5 sum_{i>0} h_i (Eq. weq55) of node idx from the converged populations.
+__device__ __forceinline__ float varphi_node(const float* __restrict__ hs, size_t N, int idx) {
+  float h[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) h[i] = __ldg(hs + i * N + idx);
+  return h_varphi(h_sum8(h));
+}
+
+// varphi at the 3x3 neighbourhood of (x, y); beyond an electrode the ghost value is the
+// linear extension through the wall potential, 2 varphi_w - varphi of the first row.
+__device__ __forceinline__ Stencil load_varphi_stencil(const KParams& k,
+                                                       const float* __restrict__ hs, int x,
+                                                       int y, float vw_b, float vw_t) {
+  const int nx = k.nx, ny = k.ny;
+  const size_t N = (size_t)k.N;
+  const int xm = x == 0 ? nx - 1 : x - 1;
+  const int xp = x + 1 == nx ? 0 : x + 1;
+  Stencil s;
+  const int row = y * nx;
+  s.c = varphi_node(hs, N, row + x);
+  s.e = varphi_node(hs, N, row + xp);
+  s.w = varphi_node(hs, N, row + xm);
+  if (k.walls && y + 1 == ny) {
+    s.n = 2.0f * vw_t - s.c;
+    s.ne = 2.0f * vw_t - s.e;
+    s.nw = 2.0f * vw_t - s.w;
+  } else {
+    const int r = (y + 1 == ny ? 0 : y + 1) * nx;
+    s.n = varphi_node(hs, N, r + x);
+    s.ne = varphi_node(hs, N, r + xp);
+    s.nw = varphi_node(hs, N, r + xm);
+  }
+  if (k.walls && y == 0) {
+    s.s = 2.0f * vw_b - s.c;
+    s.se = 2.0f * vw_b - s.e;
+    s.sw = 2.0f * vw_b - s.w;
+  } else {
+    const int r = (y == 0 ? ny - 1 : y - 1) * nx;
+    s.s = varphi_node(hs, N, r + x);
+    s.se = varphi_node(hs, N, r + xp);
+    s.sw = varphi_node(hs, N, r + xm);
+  }
+  return s;
+}
+
 // Index of the node a population leaving (x, y) in direction i lands on, and the
 // direction it lands in: periodic in x; at a wall, half-way bounce-back returns it to
 // (x, y) in the opposite direction.
@@ -327,17 +372,39 @@ __device__ __forceinline__ void coupled_body(const KParams& k, StepState* ss, in
   const float ux = (mx + 0.5f * Fx_prev) * inv_rho;
   const float uy = (my + 0.5f * Fy_prev) * inv_rho;
 
-  // a4: E = -grad(varphi) from the converged potential populations (Eq. eqA.16)
-  const float m1x = hv[0] - hv[2] + hv[4] - hv[5] - hv[6] + hv[7];
-  const float m1y = hv[1] - hv[3] + hv[4] + hv[5] - hv[6] - hv[7];
+  // a4: E = -grad(varphi) from the converged potential populations: the local first
+  // moment (Eq. eqA.16), or the stencil on varphi (variant)
   const float eh = eps_hat_of(k, phi);
-  const float inv_den = 1.0f / potential_den(k, phi);
-  const float Ex = m1x * inv_den, Ey = m1y * inv_den;
+  float Ex, Ey;
+  if (k.field_fd) {
+    const Stencil sv = load_varphi_stencil(k, hs, x, y, ld_cg(&ctl->vw_b), ld_cg(&ctl->vw_t));
+    float gvx, gvy, lv;
+    grad_lap(sv, gvx, gvy, lv);
+    Ex = -gvx;
+    Ey = -gvy;
+  } else {
+    const float m1x = hv[0] - hv[2] + hv[4] - hv[5] - hv[6] + hv[7];
+    const float m1y = hv[1] - hv[3] + hv[4] + hv[5] - hv[6] - hv[7];
+    const float inv_den = 1.0f / potential_den(k, phi);
+    Ex = m1x * inv_den;
+    Ey = m1y * inv_den;
+  }
+  // the field in hbar: this step's, or (variant) the previous step's, as Algorithm 1
+  // lists the Cahn-Hilliard LBE before the potential solve (the same at the first step)
+  float Emx = Ex, Emy = Ey;
+  if (k.lagged) {
+    if (!sa.first) {
+      Emx = hist[6 * (size_t)N + idx];
+      Emy = hist[7 * (size_t)N + idx];
+    }
+    hist[6 * (size_t)N + idx] = Ex;
+    hist[7 * (size_t)N + idx] = Ey;
+  }
 
   // a5: chemical potential (Eq. weq31), force (Eq. weq30), charge source (Eq. weq57)
   const float de = deps_of(k, phi);
   const float mu = k.beta4 * phi * (phi - 0.5f) * (phi - 1.0f) - k.kappa * lap -
-                   0.5f * de * (Ex * Ex + Ey * Ey);
+                   0.5f * de * (Emx * Emx + Emy * Emy);
   const float Fx = mu * gphx + q * Ex + rho * k.gbx;
   const float Fy = mu * gphy + q * Ey + rho * k.gby;
   const float eps = k.eps_v + eh;
@@ -508,10 +575,21 @@ __global__ void k_fields(KParams k, const StepState* __restrict__ ss, Pops pops,
     hsum += hv[i];
   }
   const float varphi = hsum * (9.0f / 5.0f);
-  const float m1x = hv[0] - hv[2] + hv[4] - hv[5] - hv[6] + hv[7];
-  const float m1y = hv[1] - hv[3] + hv[4] + hv[5] - hv[6] - hv[7];
-  const float inv_den = 1.0f / potential_den(k, __ldg(phi_solve + idx));
-  const float vals[8] = {phi, q, varphi, m1x * inv_den, m1y * inv_den, ux, uy, p};
+  float Ex, Ey;
+  if (k.field_fd) {
+    const Stencil sv = load_varphi_stencil(k, hs, x, y, ld_cg(&ctl->vw_b), ld_cg(&ctl->vw_t));
+    float gvx, gvy, lv;
+    grad_lap(sv, gvx, gvy, lv);
+    Ex = -gvx;
+    Ey = -gvy;
+  } else {
+    const float m1x = hv[0] - hv[2] + hv[4] - hv[5] - hv[6] + hv[7];
+    const float m1y = hv[1] - hv[3] + hv[4] + hv[5] - hv[6] - hv[7];
+    const float inv_den = 1.0f / potential_den(k, __ldg(phi_solve + idx));
+    Ex = m1x * inv_den;
+    Ey = m1y * inv_den;
+  }
+  const float vals[8] = {phi, q, varphi, Ex, Ey, ux, uy, p};
   int slot = 0;
 #pragma unroll
   for (int b = 0; b < 8; ++b) {
