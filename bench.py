@@ -414,7 +414,13 @@ def run_serving():
     for arm in ("batched", "one_at_a_time_plain"):
         reqs = serve.make_requests(32, seed=0, sizes=(64, 128, 256, 512), rate=50.0)
         if arm == "batched":
+            from paper_2407_01654_gb300 import autotune
+            sample = [(r.params, r.fields) for r in
+                      serve.make_requests(8, seed=99, sizes=(64, 128, 256, 512), rate=0.0)]
+            schedule = autotune.tune_batch(sample)
+            out["batch_schedule"] = dict(schedule, autotuned=True)
             backend = ehd.Batch(2 << 30, max_slots=64, steady_tol=1e-6, step_cap=3000)
+            backend.set_schedule(**schedule)
         else:
             backend = serve.OneAtATime(1e-6, 3000)
         serve.warm_up(backend)

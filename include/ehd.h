@@ -289,6 +289,8 @@ typedef struct ehd_batch_info_t {
   int32_t tiles_used, tile_capacity;  /* on-chip tiles of the shared potential launch   */
   int64_t steps_run;
   int64_t kernel_launches;            /* kernels launched by run calls                  */
+  int32_t tile_rows;                  /* the schedule: tile height of every slot and    */
+  int32_t steps_per_graph;            /* steps per captured graph                       */
 } ehd_batch_info_t;
 
 /* Creates a batch.  max_slots >= 1; hbm_budget >= 1 MiB; steady_tol > 0; step_cap >= 1.
@@ -300,6 +302,12 @@ int ehd_batch_create(size_t hbm_budget, int max_slots, double steady_tol, int64_
  * EHD_ERR_INVALID_ARG for the conventional potential scheme (batches run the paper's). */
 int ehd_batch_admit(ehd_batch* b, const ehd_params* params, const double* phi, const double* q,
                     const double* ux, const double* uy, int64_t request_id, int* slot);
+/* The batch's schedule (no counterpart in the paper; a launch choice): every slot's
+ * potential loop tiles 64 x tile_rows (16, 32 or 64; default 32) and run calls launch
+ * captured graphs of steps_per_graph steps (even, 2..64; default 16).  Changes nothing in
+ * the results of a request.  Only while no slot is live (EHD_ERR_BUSY otherwise);
+ * EHD_ERR_INVALID_ARG for other values. */
+int ehd_batch_set_schedule(ehd_batch* b, int tile_rows, int steps_per_graph);
 /* Advances every live slot by nsteps steps, then measures steadiness and statistics
  * (synchronises the stream). */
 int ehd_batch_run(ehd_batch* b, int nsteps);

@@ -150,3 +150,61 @@ def _default_fields(params):
     phi = 0.5 + 0.5 * np.tanh(2.0 * (ny / 2.0 - y) / params["width"])
     z = np.zeros((ny, nx))
     return {"phi": phi, "q": z, "ux": z, "uy": z}
+
+
+# ---------------------------------------------------------------------------------------
+# Batches: one schedule for all slots (tile height and steps per captured graph)
+# ---------------------------------------------------------------------------------------
+
+BATCH_ROWS = (16, 32, 64)
+BATCH_STEPS_PER_GRAPH = (8, 16, 32)
+
+
+def batch_candidates():
+    return [{"tile_rows": r, "steps_per_graph": g} for r in BATCH_ROWS
+            for g in BATCH_STEPS_PER_GRAPH]
+
+
+def time_batch_candidate(requests, schedule, steps, budget):
+    """Node updates per second of a batch holding as many of `requests` (params, fields)
+    as it admits under `schedule`, over `steps` steps after a warm-up; None if none fit."""
+    from . import ehd
+    b = ehd.Batch(budget, max_slots=len(requests), steady_tol=1e-30, step_cap=1 << 40)
+    try:
+        b.set_schedule(**schedule)
+        nodes = 0
+        for i, (p, f) in enumerate(requests):
+            if b.admit(p, f, i) is not None:
+                nodes += p["nx"] * p["ny"]
+        if nodes == 0:
+            return None
+        b.run(2)
+        t0 = time.perf_counter()
+        b.run(steps)
+        return nodes * steps / (time.perf_counter() - t0)
+    finally:
+        b.close()
+
+
+def tune_batch(requests, steps=64, budget=2 << 30, use_cache=True, timer=None,
+               device_name=None):
+    """Batch schedule ({"tile_rows", "steps_per_graph"}) with the most node updates per
+    second on a sample of requests [(params, fields)]; cached per device and mix of
+    lattice shapes.  `timer(requests, schedule, steps, budget)` replaces the GPU timing."""
+    if device_name is None:
+        device_name = _device_name()
+    shapes = sorted(f"{p['nx']}x{p['ny']}" for p, _ in requests)
+    key = f"{device_name}|batch|{','.join(shapes)}"
+    path = cache_path()
+    if use_cache:
+        hit = load_cache(path).get(key)
+        if hit:
+            return dict(hit["overrides"])
+    timer = timer or time_batch_candidate
+    rates = [(s, timer(requests, s, steps, budget)) for s in batch_candidates()]
+    # the fastest is the one with the smallest inverse rate
+    best, inv = pick([(s, None if r is None else 1.0 / r) for s, r in rates])
+    if use_cache:
+        store_cache(path, key, {"overrides": best, "node_updates_per_s": 1.0 / inv,
+                                "rates": [[s, r] for s, r in rates]})
+    return dict(best)

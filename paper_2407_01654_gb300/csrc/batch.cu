@@ -6,9 +6,11 @@
 // slots: the moments of every slot; ONE cooperative launch that runs the potential loops
 // of all slots on chip (each slot synchronises only its own tiles and stops at its own
 // sub-iteration count); the coupled pass of every slot.  The steps are captured in CUDA
-// graphs of STEPS_PER_GRAPH steps.  Slots tile their potential loop with fixed 64 x 32
-// tiles and get the blocks of their own launches, so a request computes exactly the same
-// numbers alone and in any mix.
+// graphs of several steps.  All slots of a batch tile their potential loop alike (64 x
+// rows tiles, rows fixed while any slot is live) and get the blocks of their own
+// launches, so a request computes exactly the same numbers alone and in any mix.  The
+// tile height and the steps per graph are the batch's schedule (ehd_batch_set_schedule,
+// e.g. chosen by an autotuner).
 //
 // Admission needs a free slot, room in the arena and room in the co-resident tile
 // capacity of the shared launch; otherwise EHD_ERR_BUSY and nothing changes.  Requests that
@@ -26,9 +28,9 @@ using namespace ehd;
 
 namespace {
 
-constexpr int BATCH_TY = BATCH_ROWS;
 constexpr int STEADY_THREADS = 256;
-constexpr int STEPS_PER_GRAPH = 16;  // even: a multi-step graph ends on the copy it began with
+constexpr int STEPS_PER_GRAPH = 16;  // default; even: a multi-step graph ends on the copy it
+                                     // began with
 
 size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 
@@ -118,15 +120,20 @@ struct ehd_batch {
   int cur = 0;                           // population copy shared by every slot
   double steady_tol = 1e-6;
   int64_t step_cap = 300000;
+  int rows = BATCH_ROWS;                 // tile height of every slot
+  int steps_per_graph = STEPS_PER_GRAPH;
   int tile_capacity = 0;                 // co-resident CTAs of the shared potential launch
   int rthreads = 0;
   size_t rsmem = 0;
+  int cap[3] = {0, 0, 0};                // tile capacity, threads and shared memory per
+  int thr[3] = {0, 0, 0};                // choice of BATCH_ROW_CHOICES
+  size_t smm[3] = {0, 0, 0};
   int tiles_used = 0;
   bool dirty = true;
   cudaGraphExec_t exec[2] = {nullptr, nullptr};    // one step from copy c
-  cudaGraphExec_t execm[2] = {nullptr, nullptr};   // STEPS_PER_GRAPH steps from copy c
+  cudaGraphExec_t execm[2] = {nullptr, nullptr};   // steps_per_graph steps from copy c
   ResidentSlot* d_slots = nullptr;       // [max_slots]
-  int2* d_work = nullptr;                // [tile_capacity]
+  int2* d_work = nullptr;                // [largest tile capacity]
   StepSlot* d_step = nullptr;            // [max_slots]
   int2* d_mwork = nullptr;               // [mwork_cap]: moments blocks of all slots
   int2* d_cwork = nullptr;               // [cwork_cap]: coupled blocks of all slots
@@ -267,7 +274,7 @@ int rebuild(ehd_batch* b) {
       cudaStreamSynchronize(b->stream) != cudaSuccess)
     return EHD_ERR_CUDA;
   BatchLaunch L;
-  L.rfunc = (void*)resident_batch_kernel();
+  L.rfunc = (void*)resident_batch_kernel(b->rows);
   L.ntiles = (int)work.size();
   L.rthreads = b->rthreads;
   L.rsmem = b->rsmem;
@@ -280,7 +287,7 @@ int rebuild(ehd_batch* b) {
   L.nc = (int)cwork.size();
   for (int c = 0; c < 2; ++c) {
     int st = build_batch_graph(L, c, 1, &b->exec[c]);
-    if (st == EHD_OK) st = build_batch_graph(L, c, STEPS_PER_GRAPH, &b->execm[c]);
+    if (st == EHD_OK) st = build_batch_graph(L, c, b->steps_per_graph, &b->execm[c]);
     if (st != EHD_OK) {
       destroy_batch_graphs(b);
       b->dirty = true;
@@ -305,30 +312,41 @@ int ehd_batch_create(size_t hbm_budget, int max_slots, double steady_tol, int64_
   b->steady_tol = steady_tol;
   b->step_cap = step_cap;
   b->slots.resize(max_slots);
-  // co-resident capacity of the shared potential launch (64 x 32 tiles, 512 threads)
+  // co-resident capacity of the shared potential launch for every tile height
   {
-    KParams kp{};
-    kp.nx = 64;
-    kp.ny = BATCH_TY;
-    ResidentGeom g;
-    int th;
-    size_t sm;
-    int dev = 0, sms = 0, coop = 0, per_sm = 0;
-    if (!resident_geometry(kp, 1, &g, &th, &sm, BATCH_TY) || cudaGetDevice(&dev) != cudaSuccess ||
+    int dev = 0, sms = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop ||
-        cudaFuncSetAttribute(resident_batch_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sm) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_batch_kernel(), th, sm) !=
-            cudaSuccess ||
-        per_sm < 1) {
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
       cudaGetLastError();
       delete b;
       return EHD_ERR_CUDA;
     }
-    b->tile_capacity = per_sm * sms;
-    b->rthreads = th;
-    b->rsmem = sm;
+    for (int c = 0; c < 3; ++c) {
+      const int rows = BATCH_ROW_CHOICES[c];
+      KParams kp{};
+      kp.nx = 64;
+      kp.ny = rows;
+      ResidentGeom g;
+      int th, per_sm = 0;
+      size_t sm;
+      if (!resident_geometry(kp, 1, &g, &th, &sm, rows) ||
+          cudaFuncSetAttribute(resident_batch_kernel(rows),
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_batch_kernel(rows), th,
+                                                        sm) != cudaSuccess ||
+          per_sm < 1) {
+        cudaGetLastError();
+        delete b;
+        return EHD_ERR_CUDA;
+      }
+      b->cap[c] = per_sm * sms;
+      b->thr[c] = th;
+      b->smm[c] = sm;
+    }
+    b->tile_capacity = b->cap[1];
+    b->rthreads = b->thr[1];
+    b->rsmem = b->smm[1];
   }
   if (arena) {
     b->arena = static_cast<char*>(arena);
@@ -344,11 +362,17 @@ int ehd_batch_create(size_t hbm_budget, int max_slots, double steady_tol, int64_
   b->arena_bytes = hbm_budget;
   // device tables at the start of the arena; a slot's nodes never exceed its tiles x 2048,
   // which bounds the work lists of the moments (256 nodes a block) and coupled (128) passes
-  const size_t max_nodes = (size_t)b->tile_capacity * 64 * BATCH_TY;
+  size_t max_nodes = 0;
+  int max_tiles = 0;
+  for (int c = 0; c < 3; ++c) {
+    const size_t n = (size_t)b->cap[c] * 64 * BATCH_ROW_CHOICES[c];
+    if (n > max_nodes) max_nodes = n;
+    if (b->cap[c] > max_tiles) max_tiles = b->cap[c];
+  }
   b->mwork_cap = (int)(max_nodes / 256) + max_slots;  // moments_blocks(N) <= N / 256 + 1
   b->cwork_cap = (int)(max_nodes / 128) + max_slots;
   const size_t t1 = al256(sizeof(ResidentSlot) * (size_t)max_slots);
-  const size_t t2 = al256(sizeof(int2) * (size_t)b->tile_capacity);
+  const size_t t2 = al256(sizeof(int2) * (size_t)max_tiles);
   const size_t t3 = al256(sizeof(StepSlot) * (size_t)max_slots);
   const size_t t4 = al256(sizeof(int2) * (size_t)b->mwork_cap);
   const size_t t5 = al256(sizeof(int2) * (size_t)b->cwork_cap);
@@ -379,17 +403,17 @@ int ehd_batch_admit(ehd_batch* b, const ehd_params* params, const double* phi, c
       break;
     }
   if (idx < 0) return EHD_ERR_BUSY;
-  const int ntiles = ((params->nx + 63) / 64) * ((params->ny + BATCH_TY - 1) / BATCH_TY);
+  const int ntiles = ((params->nx + 63) / 64) * ((params->ny + b->rows - 1) / b->rows);
   if (b->tiles_used + ntiles > b->tile_capacity) return EHD_ERR_BUSY;
   const size_t N = (size_t)params->nx * params->ny;
   const int nblocks = (int)((N + STEADY_THREADS - 1) / STEADY_THREADS);
-  const size_t ws = al256(sim_workspace_bytes(params, BATCH_TY));
+  const size_t ws = al256(sim_workspace_bytes(params, b->rows));
   const size_t snap = al256(sizeof(float) * 3 * N);
   const size_t part = al256(sizeof(double) * 4 * (size_t)nblocks);
   size_t off;
   if (!arena_alloc(b, ws + snap + part, &off)) return EHD_ERR_BUSY;
   ehd_sim* s = nullptr;
-  int st = sim_create(params, b->arena + off, ws, b->stream, BATCH_TY, &s);
+  int st = sim_create(params, b->arena + off, ws, b->stream, b->rows, &s);
   if (st != EHD_OK) {
     arena_free(b, off);
     return st;
@@ -444,7 +468,7 @@ int ehd_batch_run(ehd_batch* b, int nsteps) {
     }
   if (!any) return EHD_OK;
   int k = 0;
-  for (; k + STEPS_PER_GRAPH <= nsteps; k += STEPS_PER_GRAPH)
+  for (; k + b->steps_per_graph <= nsteps; k += b->steps_per_graph)
     if (cudaGraphLaunch(b->execm[b->cur], b->stream) != cudaSuccess) return EHD_ERR_CUDA;
   for (; k < nsteps; ++k) {
     if (cudaGraphLaunch(b->exec[b->cur], b->stream) != cudaSuccess) return EHD_ERR_CUDA;
@@ -546,6 +570,24 @@ int ehd_batch_retire(ehd_batch* b, int slot) {
   return EHD_OK;
 }
 
+int ehd_batch_set_schedule(ehd_batch* b, int tile_rows, int steps_per_graph) {
+  if (!b || steps_per_graph < 2 || steps_per_graph > 64 || (steps_per_graph & 1))
+    return EHD_ERR_INVALID_ARG;
+  int c = -1;
+  for (int j = 0; j < 3; ++j)
+    if (BATCH_ROW_CHOICES[j] == tile_rows) c = j;
+  if (c < 0) return EHD_ERR_INVALID_ARG;
+  for (const Slot& sl : b->slots)
+    if (sl.live) return EHD_ERR_BUSY;
+  b->rows = tile_rows;
+  b->steps_per_graph = steps_per_graph;
+  b->tile_capacity = b->cap[c];
+  b->rthreads = b->thr[c];
+  b->rsmem = b->smm[c];
+  b->dirty = true;
+  return EHD_OK;
+}
+
 int ehd_batch_info(ehd_batch* b, ehd_batch_info_t* info) {
   if (!b || !info) return EHD_ERR_INVALID_ARG;
   int live = 0;
@@ -558,6 +600,8 @@ int ehd_batch_info(ehd_batch* b, ehd_batch_info_t* info) {
   info->arena_used = used + b->heap_start;
   info->tiles_used = b->tiles_used;
   info->tile_capacity = b->tile_capacity;
+  info->tile_rows = b->rows;
+  info->steps_per_graph = b->steps_per_graph;
   info->steps_run = b->steps_run;
   info->kernel_launches = b->launches;
   return EHD_OK;

@@ -365,8 +365,10 @@ struct ResidentSlot {
   Ctl* ctl;
 };
 
-// Tile height of every simulation in a batch (tiles of 64 x BATCH_ROWS nodes).
+// Tile height of every simulation in a batch (tiles of 64 x rows nodes): the default, and
+// the heights a batch may be set to (all slots of a batch share one).
 constexpr int BATCH_ROWS = 32;
+constexpr int BATCH_ROW_CHOICES[3] = {16, 32, 64};
 
 // One simulation of a batch as the batched moments and coupled kernels see it.
 struct StepSlot {
@@ -390,7 +392,7 @@ cudaError_t add_coupled_batch_node(cudaGraph_t g, const cudaGraphNode_t* deps, s
 bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* threads,
                        size_t* smem, int fixed_ty = 0);
 const void* resident_kernel(int tile_rows);  // nullptr unless a multiple of 8 up to 64
-const void* resident_batch_kernel();
+const void* resident_batch_kernel(int tile_rows);  // 16, 32 or 64; else nullptr
 cudaError_t launch_poisson_resident(const KParams& kp, const ResidentGeom& g, int threads,
                                     size_t smem, const Buffers& b, cudaStream_t st);
 cudaError_t add_poisson_resident_node(cudaGraph_t graph, const cudaGraphNode_t* deps, size_t nd,

@@ -393,17 +393,18 @@ __global__ void __launch_bounds__(Tile<TY>::THREADS, Tile<TY>::MIN_BLOCKS)
   resident_loop<TY>(k, rg, hbuf, aq, exports, rpartials, ctl, blockIdx.x, gridDim.x);
 }
 
-// Several simulations in one cooperative launch, all tiled 64 x BATCH_ROWS: CTA b runs
-// tile work[b].y of simulation work[b].x.  Simulations exchange nothing, so each
-// synchronises only its own tiles (its own barrier counter and partial sums) and stops at
-// its own sub-iteration count.
-__global__ void __launch_bounds__(Tile<BATCH_ROWS>::THREADS, Tile<BATCH_ROWS>::MIN_BLOCKS)
+// Several simulations in one cooperative launch, all tiled 64 x TY: CTA b runs tile
+// work[b].y of simulation work[b].x.  Simulations exchange nothing, so each synchronises
+// only its own tiles (its own barrier counter and partial sums) and stops at its own
+// sub-iteration count.
+template <int TY>
+__global__ void __launch_bounds__(Tile<TY>::THREADS, Tile<TY>::MIN_BLOCKS)
     k_poisson_resident_batch(const ResidentSlot* __restrict__ slots,
                              const int2* __restrict__ work) {
   const int2 w = work[blockIdx.x];
   const ResidentSlot& S = slots[w.x];
-  resident_loop<BATCH_ROWS>(S.k, S.rg, S.h, S.aq, S.exports, S.rpartials, S.ctl, w.y,
-                            S.rg.ntx * S.rg.nty);
+  resident_loop<TY>(S.k, S.rg, S.h, S.aq, S.exports, S.rpartials, S.ctl, w.y,
+                    S.rg.ntx * S.rg.nty);
 }
 
 // The kernel of a tile height (nullptr: not a supported height).
@@ -420,7 +421,14 @@ const void* resident_kernel(int ty) {
     default: return nullptr;
   }
 }
-const void* resident_batch_kernel() { return (const void*)k_poisson_resident_batch; }
+const void* resident_batch_kernel(int ty) {
+  switch (ty) {
+    case 16: return (const void*)k_poisson_resident_batch<16>;
+    case 32: return (const void*)k_poisson_resident_batch<32>;
+    case 64: return (const void*)k_poisson_resident_batch<64>;
+    default: return nullptr;
+  }
+}
 
 // Tile geometry for the resident loop, or false if the lattice does not fit on chip with
 // one tile per SM.  Heights are rounded up to a multiple of 8.

@@ -103,6 +103,7 @@ class BatchInfo(ctypes.Structure):
         ("arena_bytes", ctypes.c_size_t), ("arena_used", ctypes.c_size_t),
         ("tiles_used", ctypes.c_int32), ("tile_capacity", ctypes.c_int32),
         ("steps_run", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+        ("tile_rows", ctypes.c_int32), ("steps_per_graph", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -139,6 +140,7 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_void_p)]),
     "ehd_batch_admit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Params)]
                         + [ctypes.c_void_p] * 4 + [ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]),
+    "ehd_batch_set_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "ehd_batch_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "ehd_batch_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SlotStatus), ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_int)]),
@@ -396,6 +398,15 @@ class Batch:
             _check(code, "ehd_batch_admit")
         self.shapes[slot.value] = (params["ny"], params["nx"])
         return slot.value
+
+    def set_schedule(self, tile_rows=32, steps_per_graph=16):
+        """Tile height of every slot's potential loop and steps per captured graph; only
+        while no slot is live.  Returns False when slots are live (EHD_ERR_BUSY)."""
+        code = lib().ehd_batch_set_schedule(self._h, int(tile_rows), int(steps_per_graph))
+        if code == 6:
+            return False
+        _check(code, "ehd_batch_set_schedule")
+        return True
 
     def run(self, nsteps):
         code = lib().ehd_batch_run(self._h, int(nsteps))

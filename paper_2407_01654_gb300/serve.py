@@ -236,12 +236,17 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--cap", type=int, default=20000)
     ap.add_argument("--baseline", action="store_true")
+    ap.add_argument("--tune", action="store_true", help="autotune the batch schedule first")
     args = ap.parse_args()
     from . import ehd
     sizes = tuple(int(x) for x in args.sizes.split(","))
     reqs = make_requests(args.requests, sizes=sizes, rate=args.rate)
     b = ehd.Batch(int(args.budget_gb * (1 << 30)), max_slots=args.slots, steady_tol=args.tol,
                   step_cap=args.cap)
+    if args.tune:
+        from . import autotune
+        sample = [(r.params, r.fields) for r in make_requests(8, seed=99, sizes=sizes, rate=0.0)]
+        b.set_schedule(**autotune.tune_batch(sample, budget=int(args.budget_gb * (1 << 30))))
     warm_up(b)
     clock = WallClock()
     done = serve(b, reqs, clock, window=args.window)

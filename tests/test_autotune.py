@@ -45,3 +45,22 @@ def test_tune_times_every_candidate_once_then_uses_the_cache(tmp_path, monkeypat
     assert calls == []                       # served from the cache
     assert autotune.tune(p, timer=fake, device_name="other") == best
     assert len(calls) == len(autotune.candidates(p))  # another device tunes again
+
+
+def test_tune_batch_picks_the_highest_rate_and_caches(tmp_path, monkeypatch):
+    monkeypatch.setenv("EHD_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    reqs = [(wl.make_params(nx=64, ny=64), {}), (wl.make_params(nx=128, ny=128), {})]
+    calls = []
+
+    def fake(requests, schedule, steps, budget):
+        calls.append(schedule)
+        if schedule["tile_rows"] == 64:
+            return None                       # nothing admitted
+        return 1e9 * (2 if schedule == {"tile_rows": 16, "steps_per_graph": 32} else 1)
+
+    best = autotune.tune_batch(reqs, timer=fake, device_name="dev")
+    assert best == {"tile_rows": 16, "steps_per_graph": 32}
+    assert len(calls) == len(autotune.batch_candidates()) == 9
+    calls.clear()
+    assert autotune.tune_batch(list(reversed(reqs)), timer=fake, device_name="dev") == best
+    assert calls == []                        # same mix of shapes: from the cache

@@ -127,3 +127,56 @@ def test_serving_loop_runs_requests(gpu):
     s = serve.summarize(done, clock.now())
     assert s["sims_per_hour"] > 0 and s["p99_latency_s"] >= s["p50_latency_s"]
     assert all(r.arrival <= r.admitted <= r.finished for r in done)
+
+
+@pytest.mark.parametrize("rows,spg", [(16, 8), (64, 32)])
+def test_alone_equals_in_mix_other_schedules(gpu, rows, spg):
+    """The alone-versus-mix guarantee holds for every batch schedule."""
+    pa, fa = request(96, 1)
+    alone = gpu.Batch(256 << 20, max_slots=4)
+    assert alone.set_schedule(rows, spg)
+    s = alone.admit(pa, fa, 1)
+    for _ in range(3):
+        alone.run(50)
+    ref = alone.read_fields(s)
+    mix = gpu.Batch(512 << 20, max_slots=8)
+    assert mix.set_schedule(rows, spg)
+    pb, fb = request(64, 2)
+    pc, fc = request(128, 3, precision=1)
+    sb = mix.admit(pb, fb, 2)
+    mix.run(50)
+    sa = mix.admit(pa, fa, 1)
+    sc = mix.admit(pc, fc, 3)
+    mix.run(50)
+    mix.retire(sb)
+    mix.run(100)
+    got = mix.read_fields(sa)
+    for k in FIELDS:
+        assert np.array_equal(got[k], ref[k]), k
+    assert mix.info()["tile_rows"] == rows and mix.info()["steps_per_graph"] == spg
+    assert sc is not None
+
+
+def test_schedules_compute_the_same_fields(gpu):
+    """At a fixed sub-iteration count every tile height gives identical fields, and the
+    schedule cannot change while a slot is live."""
+    p, f = request(100, 4, poisson_fixed_iter=4)
+    out = []
+    for rows, spg in ((16, 8), (32, 16), (64, 32)):
+        b = gpu.Batch(128 << 20, max_slots=2)
+        assert b.set_schedule(rows, spg)
+        s = b.admit(p, f, 0)
+        assert not b.set_schedule(32, 16)
+        b.run(37)
+        out.append(b.read_fields(s))
+        b.close()
+    for k in FIELDS:
+        assert np.array_equal(out[0][k], out[1][k]) and np.array_equal(out[1][k], out[2][k]), k
+
+
+def test_tuned_batch_schedule(gpu, tmp_path, monkeypatch):
+    from paper_2407_01654_gb300 import autotune
+    monkeypatch.setenv("EHD_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    reqs = [request(n, i) for i, n in enumerate((64, 64, 128, 256))]
+    best = autotune.tune_batch(reqs, steps=32, budget=512 << 20)
+    assert best in autotune.batch_candidates()
