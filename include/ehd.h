@@ -41,8 +41,12 @@ typedef enum ehd_status {
   EHD_ERR_NONFINITE = 5,       /* NaN or Inf in phi or q (state advanced)               */
   EHD_ERR_BUSY = 6,            /* batch: no free slot or memory for a request           */
   EHD_ERR_CUDA = 7,            /* a CUDA runtime call failed                            */
-  EHD_ERR_TOO_LARGE = 8        /* lattice exceeds the fixed scratch of the no-allocation
+  EHD_ERR_TOO_LARGE = 8,       /* lattice exceeds the fixed scratch of the no-allocation
                                   potential solve                                         */
+  EHD_ERR_TIMEOUT = 9          /* a bounded device-side wait ran out (the grid barrier of
+                                  the on-chip potential loop, 2 s): the kernel returned
+                                  early, the results of the call are invalid, the CUDA
+                                  context stays usable; destroy the simulation            */
 } ehd_status;
 
 enum { EHD_HOST = 0, EHD_DEVICE = 1 };
@@ -248,6 +252,14 @@ int ehd_profile_read(ehd_sim* sim, ehd_kernel_times* out);
 int ehd_potential_solve_noalloc(const ehd_params* params, const float* phi, const float* q,
                                 float* h, float* h_work, void* stream, int* iters,
                                 double* rel_change);
+
+/* Diagnostics (no counterpart in the paper): arms the next potential solve of a
+ * simulation on the on-chip loop so that its grid barrier never completes.  Every CTA's
+ * bounded wait then runs out after 2 s, the kernel returns early and the call reports
+ * EHD_ERR_TIMEOUT; nothing faults or hangs.  It exists to exercise that failure path in
+ * tests.  The simulation's state is invalid afterwards.  EHD_ERR_INVALID_ARG when the
+ * simulation does not use the on-chip loop. */
+int ehd_diag_expire_barrier(ehd_sim* sim);
 
 /* Releases the simulation (and its workspace if the library allocated it). */
 void ehd_destroy(ehd_sim* sim);

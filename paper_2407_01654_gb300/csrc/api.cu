@@ -229,13 +229,18 @@ void prof_end(ehd_sim* s, long j) {
 // host when to stop queueing.
 int run_potential_loop(ehd_sim* s, int fixed, int max_iter) {
   if (s->resident_ok) {
+    if (s->expire_barrier) {
+      s->expire_barrier = false;
+      EHD_CUDA(launch_expire_barrier(s->b, s->stream));
+    }
     // the whole loop in one cooperative launch
     EHD_LAUNCH(s, 1, launch_poisson_resident(s->kp, s->rg, s->rthreads, s->rsmem, s->b,
                                              s->stream));
     EHD_CUDA(cudaMemcpyAsync(s->h_ctl, s->b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost,
                              s->stream));
     EHD_CUDA(cudaStreamSynchronize(s->stream));
-    if (s->h_ctl->bar_error || !s->h_ctl->done) return EHD_ERR_CUDA;
+    if (s->h_ctl->bar_error) return EHD_ERR_TIMEOUT;
+    if (!s->h_ctl->done) return EHD_ERR_CUDA;
     s->last_k = s->h_ctl->iter;
     return s->h_ctl->converged ? EHD_OK : EHD_ERR_NOT_CONVERGED;
   }
@@ -376,6 +381,7 @@ const char* ehd_error_string(int code) {
     case EHD_ERR_BUSY: return "no free slot or memory";
     case EHD_ERR_CUDA: return "CUDA runtime error";
     case EHD_ERR_TOO_LARGE: return "lattice exceeds the fixed scratch of the no-allocation solve";
+    case EHD_ERR_TIMEOUT: return "a bounded device-side wait ran out (grid barrier)";
     default: return "unknown status";
   }
 }
@@ -604,7 +610,7 @@ static int fill_stats(ehd_sim* s, ehd_stats* out) {
   int status = EHD_OK;
   if (d.not_converged) status = EHD_ERR_NOT_CONVERGED;
   if (d.nonfinite) status = EHD_ERR_NONFINITE;
-  if (d.barrier_error) status = EHD_ERR_CUDA;
+  if (d.barrier_error) status = EHD_ERR_TIMEOUT;
   return status;
 }
 
@@ -625,8 +631,9 @@ int ehd_step(ehd_sim* s, int nsteps, ehd_stats* out) {
     s->stats_live = true;
   }
   if (!s->profiling) ensure_graphs(s);
-  const bool use_graphs = s->graphs_ok && !s->profiling;
   for (int k = 0; k < nsteps; ++k) {
+    // an armed diagnostic runs its step from the host (the graph has no slot for it)
+    const bool use_graphs = s->graphs_ok && !s->profiling && !s->expire_barrier;
     if (use_graphs) {
       // the whole step, potential loop included, without returning to the host
       EHD_CUDA(cudaGraphLaunch(s->exec[s->cur], s->stream));
@@ -635,7 +642,7 @@ int ehd_step(ehd_sim* s, int nsteps, ehd_stats* out) {
       EHD_LAUNCH(s, 0, launch_moments(s->kp, s->b, s->cur, P.poisson_tol, P.poisson_min_iter,
                                        P.poisson_max_iter, P.poisson_fixed_iter, s->stream));
       const int st = run_potential_loop(s, P.poisson_fixed_iter, P.poisson_max_iter);
-      if (st == EHD_ERR_CUDA) return st;
+      if (st == EHD_ERR_CUDA || st == EHD_ERR_TIMEOUT) return st;
       if (st != EHD_OK) status = st;
       if (!s->resident_ok) s->host_iters += s->h_ctl->iter;
       EHD_LAUNCH(s, 3, launch_coupled(s->kp, s->b, s->cur, s->stream));
@@ -648,9 +655,15 @@ int ehd_step(ehd_sim* s, int nsteps, ehd_stats* out) {
     const int st = fill_stats(s, out);
     s->stats_live = false;
     if (st != EHD_OK && status == EHD_OK) status = st;
-    if (st == EHD_ERR_NONFINITE || st == EHD_ERR_CUDA) status = st;
+    if (st == EHD_ERR_NONFINITE || st == EHD_ERR_CUDA || st == EHD_ERR_TIMEOUT) status = st;
   }
   return status;
+}
+
+int ehd_diag_expire_barrier(ehd_sim* s) {
+  if (!s || !s->resident_ok) return EHD_ERR_INVALID_ARG;
+  s->expire_barrier = true;
+  return EHD_OK;
 }
 
 int ehd_loop_kind(const ehd_sim* s) {

@@ -522,7 +522,7 @@ int ehd_batch_run(ehd_batch* b, int nsteps) {
     const int st = ehd_read_stats(s, &es);
     sl.iters += es.poisson_iters_total;
     sl.status = st;
-    if (st == EHD_ERR_NONFINITE || st == EHD_ERR_CUDA) status = st;
+    if (st == EHD_ERR_NONFINITE || st == EHD_ERR_CUDA || st == EHD_ERR_TIMEOUT) status = st;
   }
   return status;
 }

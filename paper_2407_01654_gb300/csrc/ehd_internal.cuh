@@ -409,6 +409,7 @@ cudaError_t launch_moments(const KParams& kp, const Buffers& b, int cur, double 
 cudaError_t launch_poisson(const KParams& kp, const Buffers& b, cudaStream_t st);
 cudaError_t launch_coupled(const KParams& kp, const Buffers& b, int cur, cudaStream_t st);
 cudaError_t launch_stats_reset(const Buffers& b, cudaStream_t st);
+cudaError_t launch_expire_barrier(const Buffers& b, cudaStream_t st);
 cudaError_t launch_fields(const KParams& kp, const Buffers& b, int cur, unsigned mask,
                           cudaStream_t st);
 

@@ -508,6 +508,12 @@ __global__ void __launch_bounds__(128) k_coupled_batch(const StepSlot* __restric
                         w.y);
 }
 
+// Diagnostics: puts the grid barrier's arrival count half the counter range behind every
+// target, so the next on-chip solve's waits run out (bounded) instead of completing.
+__global__ void k_expire_barrier(Ctl* ctl) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) ctl->bar_count = 0x80000000u;
+}
+
 __global__ void k_stats_reset(DevStats* s) {
   s->iters_total = 0;
   s->iters_min = 0x7fffffff;
@@ -644,6 +650,11 @@ cudaError_t launch_coupled(const KParams& kp, const Buffers& b, int cur, cudaStr
   else
     k_coupled<false><<<blocks_for(kp.N, 128), 128, 0, st>>>(kp, b.ss, cur, Pi, Po, b.phi, b.h,
                                                             b.hist, b.ctl, b.stats);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expire_barrier(const Buffers& b, cudaStream_t st) {
+  k_expire_barrier<<<1, 32, 0, st>>>(b.ctl);
   return cudaGetLastError();
 }
 

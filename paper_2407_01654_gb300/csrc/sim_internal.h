@@ -32,6 +32,7 @@ struct ehd_sim {
   bool stats_live = false;  // device statistics are accumulating
   // per-launch event timing
   bool profiling = false;
+  bool expire_barrier = false;  // diagnostics: the next on-chip solve's barrier never completes
   std::vector<cudaEvent_t> ev;     // start/stop pairs
   std::vector<int> ev_kind;        // kind per pair
   size_t ev_used = 0;              // pairs recorded and not yet accumulated

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libehd.so")
 EHD_OK = 0
 STATUS = {0: "EHD_OK", 1: "EHD_ERR_INVALID_ARG", 2: "EHD_ERR_UNSTABLE_PARAMS",
           3: "EHD_ERR_NOMEM", 4: "EHD_ERR_NOT_CONVERGED", 5: "EHD_ERR_NONFINITE",
-          6: "EHD_ERR_BUSY", 7: "EHD_ERR_CUDA", 8: "EHD_ERR_TOO_LARGE"}
+          6: "EHD_ERR_BUSY", 7: "EHD_ERR_CUDA", 8: "EHD_ERR_TOO_LARGE", 9: "EHD_ERR_TIMEOUT"}
 EHD_HOST, EHD_DEVICE = 0, 1
 FIELDS = ("phi", "q", "varphi", "Ex", "Ey", "ux", "uy", "p")
 
@@ -129,6 +129,7 @@ SIGNATURES = {
     "ehd_state_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "ehd_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "ehd_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
+    "ehd_diag_expire_barrier": (ctypes.c_int, [ctypes.c_void_p]),
     "ehd_destroy": (None, [ctypes.c_void_p]),
     "ehd_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ehd_version": (ctypes.c_char_p, []),
@@ -278,6 +279,11 @@ class Sim:
         out = st.as_dict() if stats else {}
         out["status"] = code
         return out
+
+    def diag_expire_barrier(self):
+        """Diagnostics: the next on-chip potential solve's grid barrier never completes, so
+        its bounded waits run out and the call reports EHD_ERR_TIMEOUT (9)."""
+        _check(lib().ehd_diag_expire_barrier(self._h), "ehd_diag_expire_barrier")
 
     def uses_resident_loop(self):
         """True when the potential loop runs on chip (one cooperative launch per solve)."""
