@@ -70,6 +70,7 @@ def peaks():
 # the hash of these files is the one it was measured on.
 KERNEL_FILES = {
     "k_poisson_resident": ("poisson_resident.cu", "ehd_internal.cuh"),
+    "k_poisson_resident2": ("poisson_resident.cu", "ehd_internal.cuh"),
     "k_coupled": ("kernels.cu", "ehd_internal.cuh"),
     "k_poisson": ("poisson.cu", "ehd_internal.cuh"),
 }
@@ -261,7 +262,9 @@ def run_gpu(args, rank, world):
     stream = torch.cuda.current_stream()
     sim = ehd.Sim(p, stream=stream)
     sim.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
-    resident = sim.uses_resident_loop()
+    loop_kind = sim.loop_kind()
+    resident = loop_kind in (2, 3)
+    rkernel = "k_poisson_resident2" if loop_kind == 3 else "k_poisson_resident"
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     sim.step(args.warmup)
     # the state the timed steps start from: the per-kernel profile below replays exactly
@@ -353,10 +356,10 @@ def run_gpu(args, rank, world):
     if resident:
         # on-chip loop: FP32 arithmetic per node and sub-iteration against the FP32 rate
         fl = FLOPS_POTENTIAL * nodes_f / t_it / 1e12
-        roof_pot = {"bound": "alu", "kernel": "k_poisson_resident", "achieved": fl,
+        roof_pot = {"bound": "alu", "kernel": rkernel, "achieved": fl,
                     "peak": FP32_PEAK_TFLOPS, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x "
                     "2 flop x 2.07 GHz", "unit": "TFLOP/s", "frac": fl / FP32_PEAK_TFLOPS,
-                    "traffic": recorded_traffic("k_poisson_resident"),
+                    "traffic": recorded_traffic(rkernel),
                     "flops_per_node_iteration": FLOPS_POTENTIAL,
                     "sub_iteration_us": t_it * 1e6,
                     "streamed_equivalent_GBps": BYTES_POTENTIAL * nodes_f / t_it / 1e9}
@@ -378,8 +381,10 @@ def run_gpu(args, rank, world):
         "config": {"workload": WORKLOAD, "nodes": nodes, "parallelism": f"replicas x{world}",
                    "poisson_iters_mean": kbar, "contact_angle_deg": round(info["theta"], 2),
                    "storage": "fp32 SoA populations",
-                   "potential_loop": "resident (on chip, one cooperative launch per step)"
-                   if resident else "streaming (one launch per sub-iteration, graph WHILE node)",
+                   "potential_loop": {1: "streaming (one launch per sub-iteration, graph WHILE node)",
+                                      2: "resident (on chip, one cooperative launch per step)",
+                                      3: "resident, two sub-iterations per halo exchange (on chip, "
+                                         "one cooperative launch per step)"}[loop_kind],
                    "schedule": dict(schedule, autotuned=True) if schedule else "built-in",
                    "l2": "flushed between timed steps (512 MiB device write outside the events)",
                    "step_algorithmic_bytes_per_node": step_bytes,

@@ -62,12 +62,14 @@ Layout layout_for(const ehd_params& P, int fixed_ty = 0) {
   kp.ny = P.ny;
   L.export_floats = 0;
   L.rtiles = 0;
-  if (resident_geometry(kp, DESIGN_SMS, &g, &th, &sm, fixed_ty)) {
+  if (resident_geometry(kp, DESIGN_SMS, &g, &th, &sm, fixed_ty,
+                        P.poisson_loop == EHD_LOOP_RESIDENT2)) {
     L.rtiles = (size_t)g.ntx * g.nty;
     L.export_floats = 2 * L.rtiles * 8 * (size_t)g.pmax;
   }
   L.exports = take(sizeof(float) * (L.export_floats ? L.export_floats : 1));
-  L.rpartials = take(sizeof(float2) * 2 * (L.rtiles > 0 ? L.rtiles : 1));
+  // [2][tiles] partial sums (two-step loop: [2][2][tiles])
+  L.rpartials = take(sizeof(float2) * 4 * (L.rtiles > 0 ? L.rtiles : 1));
   L.total = o;
   return L;
 }
@@ -92,7 +94,7 @@ int validate(const ehd_params* p) {
     return EHD_ERR_INVALID_ARG;
   if (p->poisson_fixed_iter == 0 && !(p->poisson_tol > 0)) return EHD_ERR_INVALID_ARG;
   if (p->ramp_steps < 0) return EHD_ERR_INVALID_ARG;
-  if (p->poisson_loop < EHD_LOOP_AUTO || p->poisson_loop > EHD_LOOP_RESIDENT)
+  if (p->poisson_loop < EHD_LOOP_AUTO || p->poisson_loop > EHD_LOOP_RESIDENT2)
     return EHD_ERR_INVALID_ARG;
   if (p->tile_rows < 0 || p->tile_rows > 64 || p->tile_rows % 8 != 0)
     return EHD_ERR_INVALID_ARG;
@@ -458,13 +460,14 @@ int sim_create(const ehd_params* params, void* workspace, size_t workspace_bytes
       ResidentGeom g;
       int th;
       size_t sm;
-      if (resident_geometry(s->kp, use_sms, &g, &th, &sm, fixed_ty) &&
+      const bool two = params->poisson_loop == EHD_LOOP_RESIDENT2;
+      if (resident_geometry(s->kp, use_sms, &g, &th, &sm, fixed_ty, two) &&
           2 * (size_t)g.ntx * g.nty * 8 * g.pmax <= L.export_floats &&
           (size_t)g.ntx * g.nty <= L.rtiles &&
-          cudaFuncSetAttribute(resident_kernel(g.TY), cudaFuncAttributeMaxDynamicSharedMemorySize,
+          cudaFuncSetAttribute(resident_kernel(g.TY, two), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)sm) == cudaSuccess) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_kernel(g.TY), th, sm) ==
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_kernel(g.TY, two), th, sm) ==
                 cudaSuccess &&
             per_sm >= 1 && (long long)g.ntx * g.nty <= (long long)per_sm * sms) {
           s->resident_ok = true;
@@ -475,7 +478,8 @@ int sim_create(const ehd_params* params, void* workspace, size_t workspace_bytes
       }
     }
     cudaGetLastError();
-    if (params->poisson_loop == EHD_LOOP_RESIDENT && !s->resident_ok) {
+    if ((params->poisson_loop == EHD_LOOP_RESIDENT || params->poisson_loop == EHD_LOOP_RESIDENT2) &&
+        !s->resident_ok) {
       ehd_destroy(s);
       return EHD_ERR_INVALID_ARG;  // the lattice does not fit on chip on this device
     }
@@ -668,7 +672,8 @@ int ehd_diag_expire_barrier(ehd_sim* s) {
 
 int ehd_loop_kind(const ehd_sim* s) {
   if (!s) return -1;
-  return s->resident_ok ? EHD_LOOP_RESIDENT : EHD_LOOP_STREAM;
+  if (!s->resident_ok) return EHD_LOOP_STREAM;
+  return s->rg.two ? EHD_LOOP_RESIDENT2 : EHD_LOOP_RESIDENT;
 }
 
 int ehd_read_stats(ehd_sim* s, ehd_stats* out) {

@@ -103,7 +103,6 @@ struct Tile {
   static constexpr int THREADS = TXR * TY / NPT;   // 16 TY
   static constexpr int ROWS = TY / NPT;            // rows between a thread's nodes
   static constexpr int PMAX = 2 * TXR + 2 * TY;    // perimeter slots
-  static constexpr int SMEM = (int)sizeof(float) * (8 * PLANE + 2 * TY * TXR);
   static constexpr int MIN_BLOCKS = THREADS >= 1024 ? 1 : (1024 / THREADS);
 };
 
@@ -407,8 +406,574 @@ __global__ void __launch_bounds__(Tile<TY>::THREADS, Tile<TY>::MIN_BLOCKS)
                     S.rg.ntx * S.rg.nty);
 }
 
-// The kernel of a tile height (nullptr: not a supported height).
-const void* resident_kernel(int ty) {
+// ---------------------------------------------------------------------------------------
+// Two sub-iterations per exchange.  The same arithmetic per node as resident_loop, but a
+// CTA advances its tile by two sub-iterations between grid barriers: it imports a
+// two-node-wide ring of its neighbours' post-stream state, collides tile and ring in the
+// first sub-iteration (streaming into the tile and the ring's inner layer), collides tile
+// and inner layer in the second, then exports its own two-node-wide band.  The stopping
+// rule is applied to both sub-iterations after the barrier, in order; when the first one
+// already ends the loop, the state it produced is restored from tensor memory (TMEM),
+// where every thread parks its four nodes' populations after the first sub-iteration.
+// Every CTA reaches the same decisions and each state is the one resident_loop produces,
+// bit for bit.  Half the grid barriers and halo round trips of resident_loop.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+constexpr int PXF = TXR + 4;  // frame row: the tile row plus two ring nodes each side
+
+__host__ __device__ constexpr int pow2_at_least(int v) {
+  return v <= 32 ? 32 : (v <= 64 ? 64 : (v <= 128 ? 128 : (v <= 256 ? 256 : 512)));
+}
+
+template <int TY>
+struct Tile2 {
+  static_assert(TY % 8 == 0 && TY >= 24 && TY <= 64, "two-step tiles: 24 to 64 rows");
+  static constexpr int PY = TY + 4;
+  static constexpr int PLANE = PY * PXF;           // one direction over tile and ring
+  static constexpr int THREADS = TXR * TY / NPT;
+  static constexpr int ROWS = TY / NPT;
+  static constexpr int NR = 4 * PXF + 4 * TY;      // ring nodes of a full tile
+  static constexpr int PMAX = 4 * TXR + 4 * TY;    // band slots (a full tile uses 16 fewer)
+  static constexpr int TCOLS = pow2_at_least((THREADS / 128) * 32);  // TMEM columns
+  static_assert(THREADS >= NR, "one ring node per thread at most");
+  static_assert(THREADS % 128 == 0, "whole warp quarters for TMEM");
+};
+
+// Slot of node (x, y) in the two-node-wide export band of a w x h tile (w, h >= 4): the
+// two bottom rows, the two top rows, then the two left and two right columns between.
+__device__ __forceinline__ int band_slot(int x, int y, int w, int h) {
+  if (y < 2) return y * w + x;
+  if (y >= h - 2) return 2 * w + (y - (h - 2)) * w + x;
+  if (x < 2) return 4 * w + (y - 2) * 2 + x;
+  return 4 * w + 2 * (h - 4) + (y - 2) * 2 + (x - (w - 2));
+}
+
+// Tile-relative coordinates of ring node r of a tw x th tile: two rows below, two rows
+// above (each tw + 4 wide), then two columns left and two right (th high).
+__device__ __forceinline__ void ring_coords(int r, int tw, int th, int& x, int& y) {
+  const int w4 = tw + 4;
+  if (r < 2 * w4) {
+    y = r < w4 ? -2 : -1;
+    x = r - (r < w4 ? 0 : w4) - 2;
+    return;
+  }
+  r -= 2 * w4;
+  if (r < 2 * w4) {
+    y = r < w4 ? th : th + 1;
+    x = r - (r < w4 ? 0 : w4) - 2;
+    return;
+  }
+  r -= 2 * w4;
+  if (r < 2 * th) {
+    y = r >> 1;
+    x = -2 + (r & 1);
+    return;
+  }
+  r -= 2 * th;
+  y = r >> 1;
+  x = tw + (r & 1);
+}
+
+__device__ __forceinline__ void tmem_store32(uint32_t taddr, const float2 (&h)[2][8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, "
+      "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, "
+      "%27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+      "f"(h[0][0].x), "f"(h[0][0].y), "f"(h[0][1].x), "f"(h[0][1].y), "f"(h[0][2].x),
+      "f"(h[0][2].y), "f"(h[0][3].x), "f"(h[0][3].y), "f"(h[0][4].x), "f"(h[0][4].y),
+      "f"(h[0][5].x), "f"(h[0][5].y), "f"(h[0][6].x), "f"(h[0][6].y), "f"(h[0][7].x),
+      "f"(h[0][7].y), "f"(h[1][0].x), "f"(h[1][0].y), "f"(h[1][1].x), "f"(h[1][1].y),
+      "f"(h[1][2].x), "f"(h[1][2].y), "f"(h[1][3].x), "f"(h[1][3].y), "f"(h[1][4].x),
+      "f"(h[1][4].y), "f"(h[1][5].x), "f"(h[1][5].y), "f"(h[1][6].x), "f"(h[1][6].y),
+      "f"(h[1][7].x), "f"(h[1][7].y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_load32(uint32_t taddr, float2 (&h)[2][8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=f"(h[0][0].x), "=f"(h[0][0].y), "=f"(h[0][1].x), "=f"(h[0][1].y), "=f"(h[0][2].x),
+        "=f"(h[0][2].y), "=f"(h[0][3].x), "=f"(h[0][3].y), "=f"(h[0][4].x), "=f"(h[0][4].y),
+        "=f"(h[0][5].x), "=f"(h[0][5].y), "=f"(h[0][6].x), "=f"(h[0][6].y), "=f"(h[0][7].x),
+        "=f"(h[0][7].y), "=f"(h[1][0].x), "=f"(h[1][0].y), "=f"(h[1][1].x), "=f"(h[1][1].y),
+        "=f"(h[1][2].x), "=f"(h[1][2].y), "=f"(h[1][3].x), "=f"(h[1][3].y), "=f"(h[1][4].x),
+        "=f"(h[1][4].y), "=f"(h[1][5].x), "=f"(h[1][5].y), "=f"(h[1][6].x), "=f"(h[1][6].y),
+        "=f"(h[1][7].x), "=f"(h[1][7].y)
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Post-stream population i of the node at frame index f: the post-collision population
+// of the node behind it, or the anti-bounce-back rule when that node lies beyond a wall
+// (bw / tw_: the consuming node is on the bottom / top lattice row of a walled lattice).
+template <int PLANE>
+__device__ __forceinline__ float gather(const float* sm, int i, int f, bool bw, bool tw_,
+                                        float vw_b, float vw_t) {
+  if (cy(i) > 0 && bw) return h_wall(i, sm[(opp(i) - 1) * PLANE + f], vw_b);
+  if (cy(i) < 0 && tw_) return h_wall(i, sm[(opp(i) - 1) * PLANE + f], vw_t);
+  return sm[(i - 1) * PLANE + f - cy(i) * PXF - cx(i)];
+}
+
+}  // namespace
+
+template <int TY>
+__device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentGeom& rg,
+                                               float* __restrict__ hbuf,
+                                               const float2* __restrict__ aq,
+                                               float* __restrict__ exports,
+                                               float2* __restrict__ rpartials, Ctl* ctl,
+                                               const int tile, const int ntiles) {
+  using T = Tile2<TY>;
+  // shared memory: [8][PY][PXF] post-collision populations over tile and ring, [PY][PXF]
+  // a, [PY][PXF] q, then [8][NR] ring state (also the export staging area)
+  extern __shared__ float sm[];
+  __shared__ float2 s_w[T::THREADS / 32];
+  __shared__ int s_done;
+  __shared__ uint32_t s_taddr;
+  __shared__ Nb s_nb[3][3];
+
+  const int nx = k.nx, ny = k.ny;
+  const size_t N = (size_t)k.N;
+  const int tcol = tile % rg.ntx, trow = tile / rg.ntx;
+  const int tx0 = tcol * TXR, ty0 = trow * TY;
+  const int tw = min(TXR, nx - tx0), th = min(TY, ny - ty0);
+  float* ca = sm + 8 * T::PLANE;
+  float* cq = ca + T::PLANE;
+  float* ring = cq + T::PLANE;
+  const int parity = ld_cg(&ctl->parity);
+  float* __restrict__ hsrc = hbuf + (size_t)parity * NH * N;
+  const float qshift = k.neutralize ? ld_cg(&ctl->mean_q) : 0.0f;
+  const float vw_b = ld_cg(&ctl->vw_b), vw_t = ld_cg(&ctl->vw_t);
+  const double tol = ctl->tol;
+  const int min_iter = ctl->min_iter, max_iter = ctl->max_iter, fixed = ctl->fixed_iter;
+  const float om = k.omega_h;
+  constexpr int pstride = 8 * T::PMAX;
+  const int warp = threadIdx.x >> 5;
+  constexpr int dwarp = T::THREADS / 32 - 1;
+
+  // TMEM for the parked state: warp w uses lanes 32 (w mod 4) .. + 31, columns 32 (w / 4)
+  if (warp == 0) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_taddr);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst),
+                 "n"(T::TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+
+  // my tile nodes: column lx, rows ly0 + s ROWS
+  const int lx = threadIdx.x & (TXR - 1);
+  const int ly0 = threadIdx.x >> 6;
+  const int at0 = (ly0 + 2) * PXF + lx + 2;   // frame index of node 0
+  const int nrows = lx < tw ? th : 0;
+
+  if (threadIdx.x < 9) {
+    const int dx = (int)threadIdx.x % 3 - 1, dy = (int)threadIdx.x / 3 - 1;
+    const int c = (tcol + dx + rg.ntx) % rg.ntx;
+    int r = trow + dy;
+    Nb nb;
+    if (r < 0 || r >= rg.nty) {
+      if (k.walls) {
+        nb.id = -1;
+        nb.w = nb.h = 0;
+        s_nb[dy + 1][dx + 1] = nb;
+        r = -1;
+      } else {
+        r = (r + rg.nty) % rg.nty;
+      }
+    }
+    if (r >= 0) {
+      nb.id = r * rg.ntx + c;
+      nb.w = min(TXR, nx - c * TXR);
+      nb.h = min(TY, ny - r * TY);
+      s_nb[dy + 1][dx + 1] = nb;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = s_taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2));
+
+  // my ring node (thread r < number of ring nodes): frame index, flags, import source
+  const int nring = 4 * (tw + 4) + 4 * th;
+  int rf = 0, rnb = -1, rslot = 0;
+  bool rexist = false, rlayer1 = false, rbw = false, rtw = false;
+  if ((int)threadIdx.x < nring) {
+    int x, y;
+    ring_coords(threadIdx.x, tw, th, x, y);
+    rf = (y + 2) * PXF + x + 2;
+    const int nbx = x < 0 ? 0 : (x >= tw ? 2 : 1);
+    const int nby = y < 0 ? 0 : (y >= th ? 2 : 1);
+    const Nb nb = s_nb[nby][nbx];
+    rexist = nb.id >= 0;
+    if (rexist) {
+      rnb = nb.id;
+      const int olx = x < 0 ? nb.w + x : (x >= tw ? x - tw : x);
+      const int oly = y < 0 ? nb.h + y : (y >= th ? y - th : y);
+      rslot = band_slot(olx, oly, nb.w, nb.h);
+      rlayer1 = ((y == -1 || y == th) && x >= -1 && x <= tw) ||
+                ((x == -1 || x == tw) && y >= 0 && y < th);
+      const int gy = ty0 + y;
+      rbw = k.walls && gy == 0;
+      rtw = k.walls && gy == ny - 1;
+      // first import: the lattice's own post-stream state; coefficients once per solve
+      const int gx = (tx0 + x + nx) % nx;
+      const int g = ((gy + ny) % ny) * nx + gx;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) ring[i * T::NR + threadIdx.x] = hsrc[i * N + g];
+      const float2 c = aq[g];
+      ca[rf] = c.x;
+      cq[rf] = c.y - qshift;
+    }
+  }
+
+  // my tile nodes: state in registers (two packed pairs), coefficients in the frame.
+  // Nodes outside the lattice (partial tiles) compute with their pair but write nothing
+  // to shared memory: their cells may be ring nodes of this tile.
+  float2 h[2][8];
+  bool valid[NPT], bw[NPT], tw_[NPT];
+#pragma unroll
+  for (int s = 0; s < NPT; ++s) {
+    const int ly = ly0 + s * T::ROWS;
+    valid[s] = ly < nrows;
+    bw[s] = k.walls && ty0 + ly == 0;
+    tw_[s] = k.walls && ty0 + ly == ny - 1;
+    float v[8];
+    float a = 0.0f, q = 0.0f;
+    if (valid[s]) {
+      const int g = (ty0 + ly) * nx + tx0 + lx;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = hsrc[i * N + g];
+      const float2 c = aq[g];
+      a = c.x;
+      q = c.y - qshift;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = 0.0f;
+    }
+    if (valid[s]) {  // a node outside the lattice may sit on a ring node's cell
+      ca[at0 + s * T::ROWS * PXF] = a;
+      cq[at0 + s * T::ROWS * PXF] = q;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (s & 1)
+        h[s >> 1][i].y = v[i];
+      else
+        h[s >> 1][i].x = v[i];
+    }
+  }
+  __syncthreads();
+
+  unsigned target = 0;
+  int cyc = 0, it = 0, conv = 0;
+  float rel = 0.0f;
+  int done = 0;
+  for (;;) {
+    float2* pp = rpartials + (size_t)(cyc & 1) * 2 * ntiles;
+    // ---- sub-iteration 1: collide tile and ring, stream into tile and inner ring ----
+    float2 vold[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int o0 = 2 * p * T::ROWS * PXF, o1 = (2 * p + 1) * T::ROWS * PXF;
+      const float2 varphi = h_varphi2(h_sum8x2(h[p]));
+      vold[p] = varphi;
+      float2 m1x, m1y;
+      h_moment1x2(h[p], m1x, m1y);
+      const float2 a = make_float2(ca[at0 + o0], ca[at0 + o1]);
+      const float2 qs = __fmul2_rn(f2(0.125f), make_float2(cq[at0 + o0], cq[at0 + o1]));
+      float2 hs[8];
+      h_star8x2(h[p], om, varphi, a, m1x, m1y, qs, hs);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (valid[2 * p]) sm[i * T::PLANE + at0 + o0] = hs[i].x;
+        if (valid[2 * p + 1]) sm[i * T::PLANE + at0 + o1] = hs[i].y;
+      }
+    }
+    if (rexist) {
+      float hr[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) hr[i] = ring[i * T::NR + threadIdx.x];
+      const float varphi = h_varphi(h_sum8(hr));
+      float m1x, m1y;
+      h_moment1(hr, m1x, m1y);
+      const float qs = 0.125f * cq[rf];
+      const float a = ca[rf];
+#pragma unroll
+      for (int i = 1; i < 9; ++i)
+        sm[(i - 1) * T::PLANE + rf] = h_star(i, hr[i - 1], om, varphi, a, m1x, m1y, qs);
+    }
+    __syncthreads();
+    float num = 0.0f, den = 0.0f;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int f0 = at0 + 2 * p * T::ROWS * PXF, f1 = at0 + (2 * p + 1) * T::ROWS * PXF;
+      if (bw[2 * p] || tw_[2 * p] || bw[2 * p + 1] || tw_[2 * p + 1]) {
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+          h[p][i - 1] = make_float2(
+              gather<T::PLANE>(sm, i, f0, bw[2 * p], tw_[2 * p], vw_b, vw_t),
+              gather<T::PLANE>(sm, i, f1, bw[2 * p + 1], tw_[2 * p + 1], vw_b, vw_t));
+      } else {
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+          const int off = (i - 1) * T::PLANE - cy(i) * PXF - cx(i);
+          h[p][i - 1] = make_float2(sm[off + f0], sm[off + f1]);
+        }
+      }
+      const float2 d = __fadd2_rn(h_varphi2(h_sum8x2(h[p])), neg2(vold[p]));
+      if (valid[2 * p]) {
+        num = __fmaf_rn(d.x, d.x, num);
+        den = __fmaf_rn(vold[p].x, vold[p].x, den);
+      }
+      if (valid[2 * p + 1]) {
+        num = __fmaf_rn(d.y, d.y, num);
+        den = __fmaf_rn(vold[p].y, vold[p].y, den);
+      }
+    }
+    if (rlayer1) {
+#pragma unroll
+      for (int i = 1; i < 9; ++i)
+        ring[(i - 1) * T::NR + threadIdx.x] = gather<T::PLANE>(sm, i, rf, rbw, rtw, vw_b, vw_t);
+    }
+    // park the state after the first sub-iteration in TMEM (restored if the rule stops
+    // the loop there)
+    tmem_store32(taddr, h);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      num += __shfl_xor_sync(0xffffffffu, num, o);
+      den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    if ((threadIdx.x & 31) == 0) s_w[warp] = make_float2(num, den);
+    __syncthreads();  // populations consumed, inner ring state and warp sums visible
+    if (threadIdx.x < 32) {
+      constexpr int nwarps = T::THREADS / 32;
+      float2 v = (int)threadIdx.x < nwarps ? s_w[threadIdx.x] : make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+      }
+      if (threadIdx.x == 0) pp[tile] = v;
+    }
+    // ---- sub-iteration 2: collide tile and inner ring, stream into the tile ----
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int o0 = 2 * p * T::ROWS * PXF, o1 = (2 * p + 1) * T::ROWS * PXF;
+      const float2 varphi = h_varphi2(h_sum8x2(h[p]));
+      vold[p] = varphi;
+      float2 m1x, m1y;
+      h_moment1x2(h[p], m1x, m1y);
+      const float2 a = make_float2(ca[at0 + o0], ca[at0 + o1]);
+      const float2 qs = __fmul2_rn(f2(0.125f), make_float2(cq[at0 + o0], cq[at0 + o1]));
+      float2 hs[8];
+      h_star8x2(h[p], om, varphi, a, m1x, m1y, qs, hs);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (valid[2 * p]) sm[i * T::PLANE + at0 + o0] = hs[i].x;
+        if (valid[2 * p + 1]) sm[i * T::PLANE + at0 + o1] = hs[i].y;
+      }
+    }
+    if (rlayer1) {
+      float hr[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) hr[i] = ring[i * T::NR + threadIdx.x];
+      const float varphi = h_varphi(h_sum8(hr));
+      float m1x, m1y;
+      h_moment1(hr, m1x, m1y);
+      const float qs = 0.125f * cq[rf];
+      const float a = ca[rf];
+#pragma unroll
+      for (int i = 1; i < 9; ++i)
+        sm[(i - 1) * T::PLANE + rf] = h_star(i, hr[i - 1], om, varphi, a, m1x, m1y, qs);
+    }
+    __syncthreads();
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    num = 0.0f;
+    den = 0.0f;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int f0 = at0 + 2 * p * T::ROWS * PXF, f1 = at0 + (2 * p + 1) * T::ROWS * PXF;
+      if (bw[2 * p] || tw_[2 * p] || bw[2 * p + 1] || tw_[2 * p + 1]) {
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+          h[p][i - 1] = make_float2(
+              gather<T::PLANE>(sm, i, f0, bw[2 * p], tw_[2 * p], vw_b, vw_t),
+              gather<T::PLANE>(sm, i, f1, bw[2 * p + 1], tw_[2 * p + 1], vw_b, vw_t));
+      } else {
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+          const int off = (i - 1) * T::PLANE - cy(i) * PXF - cx(i);
+          h[p][i - 1] = make_float2(sm[off + f0], sm[off + f1]);
+        }
+      }
+      const float2 d = __fadd2_rn(h_varphi2(h_sum8x2(h[p])), neg2(vold[p]));
+      if (valid[2 * p]) {
+        num = __fmaf_rn(d.x, d.x, num);
+        den = __fmaf_rn(vold[p].x, vold[p].x, den);
+      }
+      if (valid[2 * p + 1]) {
+        num = __fmaf_rn(d.y, d.y, num);
+        den = __fmaf_rn(vold[p].y, vold[p].y, den);
+      }
+    }
+    // stage my band nodes' new state for export (the ring area is free now)
+#pragma unroll
+    for (int s = 0; s < NPT; ++s) {
+      const int ly = ly0 + s * T::ROWS;
+      if (valid[s] && (ly < 2 || ly >= th - 2 || lx < 2 || lx >= tw - 2)) {
+        const int sl = band_slot(lx, ly, tw, th);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          ring[i * T::PMAX + sl] = (s & 1) ? h[s >> 1][i].y : h[s >> 1][i].x;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      num += __shfl_xor_sync(0xffffffffu, num, o);
+      den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    if ((threadIdx.x & 31) == 0) s_w[warp] = make_float2(num, den);
+    __syncthreads();  // populations consumed, staging and warp sums visible
+    if (threadIdx.x < 32) {
+      constexpr int nwarps = T::THREADS / 32;
+      float2 v = (int)threadIdx.x < nwarps ? s_w[threadIdx.x] : make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+      }
+      if (threadIdx.x == 0) pp[ntiles + tile] = v;
+    }
+    {
+      float* exp_cur = exports + (size_t)(cyc & 1) * ntiles * pstride + (size_t)tile * pstride;
+      const int nslots = 4 * tw + 4 * th - 16;
+      for (int sl = threadIdx.x; sl < nslots; sl += T::THREADS) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) exp_cur[i * T::PMAX + sl] = ring[i * T::PMAX + sl];
+      }
+    }
+    // all tiles' bands and both sub-iterations' partial sums are visible
+    if (!grid_barrier(ctl, ntiles, target)) {
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_taddr),
+                     "n"(T::TCOLS)
+                     : "memory");
+      }
+      return;
+    }
+    // the deciding warp applies the rule to both sub-iterations, in order, while the
+    // other threads import the ring for the next cycle
+    if (warp == dwarp) {
+      const int lane = threadIdx.x & 31;
+      float a1 = 0.0f, b1 = 0.0f, a2 = 0.0f, b2 = 0.0f;
+      for (int t = lane; t < ntiles; t += 32) {
+        const float2 v1 = __ldcg(pp + t), v2 = __ldcg(pp + ntiles + t);
+        a1 += v1.x;
+        b1 += v1.y;
+        a2 += v2.x;
+        b2 += v2.y;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        b1 += __shfl_xor_sync(0xffffffffu, b1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+      }
+      if (lane == 0) {
+        int d = 0;
+        for (int u = 0; u < 2 && !d; ++u) {
+          const int st = 2 * cyc + 1 + u;
+          const float sa = u ? a2 : a1, sb = u ? b2 : b1;
+          float r;
+          if (sa == 0.0f && sb == 0.0f)
+            r = 0.0f;
+          else if (sb == 0.0f)
+            r = __int_as_float(0x7f800000);
+          else
+            r = sqrtf(sa / sb);
+          bool dn;
+          int cv;
+          if (fixed > 0) {
+            dn = st >= fixed;
+            cv = 1;
+          } else {
+            cv = (st >= min_iter) && ((double)r < tol);
+            dn = cv || st >= max_iter;
+          }
+          rel = r;
+          conv = cv;
+          it = st;
+          if (dn) d = u + 1;
+        }
+        s_done = d;
+      }
+    }
+    if (rexist) {
+      const float* src = exports + (size_t)(cyc & 1) * ntiles * pstride + (size_t)rnb * pstride;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) ring[i * T::NR + threadIdx.x] = __ldcg(src + i * T::PMAX + rslot);
+    }
+    __syncthreads();
+    done = s_done;
+    if (done) break;
+    ++cyc;
+  }
+  if (done == 1) tmem_load32(taddr, h);  // the loop stopped after the first sub-iteration
+
+  // the registers hold the final state: write it back in place
+#pragma unroll
+  for (int s = 0; s < NPT; ++s) {
+    if (!valid[s]) continue;
+    const int g = (ty0 + ly0 + s * T::ROWS) * nx + tx0 + lx;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) hsrc[i * N + g] = (s & 1) ? h[s >> 1][i].y : h[s >> 1][i].x;
+  }
+  if (tile == 0 && (int)threadIdx.x == dwarp * 32) {
+    ctl->iter = it;
+    ctl->rel = (double)rel;
+    ctl->converged = conv;
+    ctl->done = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_taddr),
+                 "n"(T::TCOLS)
+                 : "memory");
+  }
+}
+
+template <int TY>
+__global__ void __launch_bounds__(Tile2<TY>::THREADS, 1)
+    k_poisson_resident2(KParams k, ResidentGeom rg, float* __restrict__ hbuf,
+                        const float2* __restrict__ aq, float* __restrict__ exports,
+                        float2* __restrict__ rpartials, Ctl* ctl) {
+  resident_loop2<TY>(k, rg, hbuf, aq, exports, rpartials, ctl, blockIdx.x, gridDim.x);
+}
+
+// The kernel of a tile height (nullptr: not a supported height); two: the loop with two
+// sub-iterations per exchange (heights 24 to 64).
+const void* resident_kernel(int ty, bool two) {
+  if (two) {
+    switch (ty) {
+      case 24: return (const void*)k_poisson_resident2<24>;
+      case 32: return (const void*)k_poisson_resident2<32>;
+      case 40: return (const void*)k_poisson_resident2<40>;
+      case 48: return (const void*)k_poisson_resident2<48>;
+      case 56: return (const void*)k_poisson_resident2<56>;
+      case 64: return (const void*)k_poisson_resident2<64>;
+      default: return nullptr;
+    }
+  }
   switch (ty) {
     case 8: return (const void*)k_poisson_resident<8>;
     case 16: return (const void*)k_poisson_resident<16>;
@@ -431,9 +996,11 @@ const void* resident_batch_kernel(int ty) {
 }
 
 // Tile geometry for the resident loop, or false if the lattice does not fit on chip with
-// one tile per SM.  Heights are rounded up to a multiple of 8.
+// one tile per SM.  Heights are rounded up to a multiple of 8.  two: the loop with two
+// sub-iterations per exchange, which needs heights of at least 24 and every tile at least
+// 4 x 4 (its export band is two nodes wide).
 bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* threads,
-                       size_t* smem, int fixed_ty) {
+                       size_t* smem, int fixed_ty, bool two) {
   const long long N = (long long)kp.nx * kp.ny;
   const int ntx = (kp.nx + TXR - 1) / TXR;
   int TY, nty;
@@ -453,6 +1020,7 @@ bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* thr
     if (nty > num_sms / ntx) nty = num_sms / ntx;
     TY = (kp.ny + nty - 1) / nty;
     TY = (TY + 7) / 8 * 8;
+    if (two && TY < 24) TY = 24;
     if (TY > 64) return false;
     nty = (kp.ny + TY - 1) / TY;
   }
@@ -460,15 +1028,24 @@ bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* thr
   g->TY = TY;
   g->ntx = ntx;
   g->nty = nty;
-  g->pmax = 2 * TXR + 2 * TY;
+  g->two = two ? 1 : 0;
   *threads = TXR * TY / NPT;
-  *smem = sizeof(float) * (8 * (size_t)(TY + 2) * RX + 2 * (size_t)TY * TXR);
+  if (two) {
+    if (TY < 24 || kp.nx < 4 || kp.ny < 4 || kp.nx - (ntx - 1) * TXR < 4 ||
+        kp.ny - (nty - 1) * TY < 4)
+      return false;
+    g->pmax = 4 * TXR + 4 * TY;
+    *smem = sizeof(float) * (10 * (size_t)(TY + 4) * PXF + 8 * (size_t)(4 * PXF + 4 * TY));
+  } else {
+    g->pmax = 2 * TXR + 2 * TY;
+    *smem = sizeof(float) * (8 * (size_t)(TY + 2) * RX + 2 * (size_t)TY * TXR);
+  }
   return true;
 }
 
 cudaError_t launch_poisson_resident(const KParams& kp, const ResidentGeom& g, int threads,
                                     size_t smem, const Buffers& b, cudaStream_t st) {
-  const void* f = resident_kernel(g.TY);
+  const void* f = resident_kernel(g.TY, g.two != 0);
   if (!f) return cudaErrorInvalidValue;
   KParams k = kp;
   ResidentGeom gg = g;
@@ -485,7 +1062,7 @@ cudaError_t add_poisson_resident_node(cudaGraph_t graph, const cudaGraphNode_t* 
                                       cudaGraphNode_t* out, const KParams& kp,
                                       const ResidentGeom& g, int threads, size_t smem,
                                       const Buffers& b) {
-  const void* f = resident_kernel(g.TY);
+  const void* f = resident_kernel(g.TY, g.two != 0);
   if (!f) return cudaErrorInvalidValue;
   KParams k = kp;
   ResidentGeom gg = g;

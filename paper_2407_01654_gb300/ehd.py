@@ -285,9 +285,14 @@ class Sim:
         its bounded waits run out and the call reports EHD_ERR_TIMEOUT (9)."""
         _check(lib().ehd_diag_expire_barrier(self._h), "ehd_diag_expire_barrier")
 
+    def loop_kind(self):
+        """1 streaming loop, 2 on-chip loop, 3 on-chip loop with two sub-iterations per
+        exchange."""
+        return int(lib().ehd_loop_kind(self._h))
+
     def uses_resident_loop(self):
         """True when the potential loop runs on chip (one cooperative launch per solve)."""
-        return bool(lib().ehd_loop_kind(self._h) == 2)
+        return self.loop_kind() in (2, 3)
 
     def read_stats(self):
         st = Stats()
