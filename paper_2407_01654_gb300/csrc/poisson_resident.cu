@@ -449,6 +449,30 @@ __device__ __forceinline__ int band_slot(int x, int y, int w, int h) {
   return 4 * w + 2 * (h - 4) + (y - 2) * 2 + (x - (w - 2));
 }
 
+// Inverse of band_slot: the node of band slot sl of a w x h tile.
+__device__ __forceinline__ void band_coords(int sl, int w, int h, int& x, int& y) {
+  if (sl < 2 * w) {
+    y = sl < w ? 0 : 1;
+    x = sl - y * w;
+    return;
+  }
+  sl -= 2 * w;
+  if (sl < 2 * w) {
+    y = h - 2 + (sl < w ? 0 : 1);
+    x = sl - (sl < w ? 0 : w);
+    return;
+  }
+  sl -= 2 * w;
+  if (sl < 2 * (h - 4)) {
+    y = 2 + (sl >> 1);
+    x = sl & 1;
+    return;
+  }
+  sl -= 2 * (h - 4);
+  y = 2 + (sl >> 1);
+  x = w - 2 + (sl & 1);
+}
+
 // Tile-relative coordinates of ring node r of a tw x th tile: two rows below, two rows
 // above (each tw + 4 wide), then two columns left and two right (th high).
 __device__ __forceinline__ void ring_coords(int r, int tw, int th, int& x, int& y) {
@@ -599,7 +623,7 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
 
   // my ring node (thread r < number of ring nodes): frame index, flags, import source
   const int nring = 4 * (tw + 4) + 4 * th;
-  int rf = 0, rnb = -1, rslot = 0;
+  int rf = 0, rsrc = 0;  // frame index; offset of my ring node in its tile's export band
   bool rexist = false, rlayer1 = false, rbw = false, rtw = false;
   if ((int)threadIdx.x < nring) {
     int x, y;
@@ -610,10 +634,9 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
     const Nb nb = s_nb[nby][nbx];
     rexist = nb.id >= 0;
     if (rexist) {
-      rnb = nb.id;
       const int olx = x < 0 ? nb.w + x : (x >= tw ? x - tw : x);
       const int oly = y < 0 ? nb.h + y : (y >= th ? y - th : y);
-      rslot = band_slot(olx, oly, nb.w, nb.h);
+      rsrc = nb.id * pstride + band_slot(olx, oly, nb.w, nb.h);
       rlayer1 = ((y == -1 || y == th) && x >= -1 && x <= tw) ||
                 ((x == -1 || x == tw) && y >= 0 && y < th);
       const int gy = ty0 + y;
@@ -634,16 +657,16 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
   // Nodes outside the lattice (partial tiles) compute with their pair but write nothing
   // to shared memory: their cells may be ring nodes of this tile.
   float2 h[2][8];
-  bool valid[NPT], bw[NPT], tw_[NPT];
+  // per node: inside the lattice; on the bottom / top lattice row next to a wall
+  auto valid = [&](int s) { return ly0 + s * T::ROWS < nrows; };
+  auto bw = [&](int s) { return k.walls && ty0 + ly0 + s * T::ROWS == 0; };
+  auto tw_ = [&](int s) { return k.walls && ty0 + ly0 + s * T::ROWS == ny - 1; };
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
     const int ly = ly0 + s * T::ROWS;
-    valid[s] = ly < nrows;
-    bw[s] = k.walls && ty0 + ly == 0;
-    tw_[s] = k.walls && ty0 + ly == ny - 1;
     float v[8];
     float a = 0.0f, q = 0.0f;
-    if (valid[s]) {
+    if (valid(s)) {
       const int g = (ty0 + ly) * nx + tx0 + lx;
 #pragma unroll
       for (int i = 0; i < 8; ++i) v[i] = hsrc[i * N + g];
@@ -654,7 +677,7 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
 #pragma unroll
       for (int i = 0; i < 8; ++i) v[i] = 0.0f;
     }
-    if (valid[s]) {  // a node outside the lattice may sit on a ring node's cell
+    if (valid(s)) {  // a node outside the lattice may sit on a ring node's cell
       ca[at0 + s * T::ROWS * PXF] = a;
       cq[at0 + s * T::ROWS * PXF] = q;
     }
@@ -689,8 +712,8 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       h_star8x2(h[p], om, varphi, a, m1x, m1y, qs, hs);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        if (valid[2 * p]) sm[i * T::PLANE + at0 + o0] = hs[i].x;
-        if (valid[2 * p + 1]) sm[i * T::PLANE + at0 + o1] = hs[i].y;
+        if (valid(2 * p)) sm[i * T::PLANE + at0 + o0] = hs[i].x;
+        if (valid(2 * p + 1)) sm[i * T::PLANE + at0 + o1] = hs[i].y;
       }
     }
     if (rexist) {
@@ -711,12 +734,12 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
       const int f0 = at0 + 2 * p * T::ROWS * PXF, f1 = at0 + (2 * p + 1) * T::ROWS * PXF;
-      if (bw[2 * p] || tw_[2 * p] || bw[2 * p + 1] || tw_[2 * p + 1]) {
+      if (bw(2 * p) || tw_(2 * p) || bw(2 * p + 1) || tw_(2 * p + 1)) {
 #pragma unroll
         for (int i = 1; i < 9; ++i)
           h[p][i - 1] = make_float2(
-              gather<T::PLANE>(sm, i, f0, bw[2 * p], tw_[2 * p], vw_b, vw_t),
-              gather<T::PLANE>(sm, i, f1, bw[2 * p + 1], tw_[2 * p + 1], vw_b, vw_t));
+              gather<T::PLANE>(sm, i, f0, bw(2 * p), tw_(2 * p), vw_b, vw_t),
+              gather<T::PLANE>(sm, i, f1, bw(2 * p + 1), tw_(2 * p + 1), vw_b, vw_t));
       } else {
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
@@ -725,11 +748,11 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
         }
       }
       const float2 d = __fadd2_rn(h_varphi2(h_sum8x2(h[p])), neg2(vold[p]));
-      if (valid[2 * p]) {
+      if (valid(2 * p)) {
         num = __fmaf_rn(d.x, d.x, num);
         den = __fmaf_rn(vold[p].x, vold[p].x, den);
       }
-      if (valid[2 * p + 1]) {
+      if (valid(2 * p + 1)) {
         num = __fmaf_rn(d.y, d.y, num);
         den = __fmaf_rn(vold[p].y, vold[p].y, den);
       }
@@ -773,8 +796,8 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       h_star8x2(h[p], om, varphi, a, m1x, m1y, qs, hs);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        if (valid[2 * p]) sm[i * T::PLANE + at0 + o0] = hs[i].x;
-        if (valid[2 * p + 1]) sm[i * T::PLANE + at0 + o1] = hs[i].y;
+        if (valid(2 * p)) sm[i * T::PLANE + at0 + o0] = hs[i].x;
+        if (valid(2 * p + 1)) sm[i * T::PLANE + at0 + o1] = hs[i].y;
       }
     }
     if (rlayer1) {
@@ -797,12 +820,12 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
       const int f0 = at0 + 2 * p * T::ROWS * PXF, f1 = at0 + (2 * p + 1) * T::ROWS * PXF;
-      if (bw[2 * p] || tw_[2 * p] || bw[2 * p + 1] || tw_[2 * p + 1]) {
+      if (bw(2 * p) || tw_(2 * p) || bw(2 * p + 1) || tw_(2 * p + 1)) {
 #pragma unroll
         for (int i = 1; i < 9; ++i)
           h[p][i - 1] = make_float2(
-              gather<T::PLANE>(sm, i, f0, bw[2 * p], tw_[2 * p], vw_b, vw_t),
-              gather<T::PLANE>(sm, i, f1, bw[2 * p + 1], tw_[2 * p + 1], vw_b, vw_t));
+              gather<T::PLANE>(sm, i, f0, bw(2 * p), tw_(2 * p), vw_b, vw_t),
+              gather<T::PLANE>(sm, i, f1, bw(2 * p + 1), tw_(2 * p + 1), vw_b, vw_t));
       } else {
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
@@ -811,24 +834,13 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
         }
       }
       const float2 d = __fadd2_rn(h_varphi2(h_sum8x2(h[p])), neg2(vold[p]));
-      if (valid[2 * p]) {
+      if (valid(2 * p)) {
         num = __fmaf_rn(d.x, d.x, num);
         den = __fmaf_rn(vold[p].x, vold[p].x, den);
       }
-      if (valid[2 * p + 1]) {
+      if (valid(2 * p + 1)) {
         num = __fmaf_rn(d.y, d.y, num);
         den = __fmaf_rn(vold[p].y, vold[p].y, den);
-      }
-    }
-    // stage my band nodes' new state for export (the ring area is free now)
-#pragma unroll
-    for (int s = 0; s < NPT; ++s) {
-      const int ly = ly0 + s * T::ROWS;
-      if (valid[s] && (ly < 2 || ly >= th - 2 || lx < 2 || lx >= tw - 2)) {
-        const int sl = band_slot(lx, ly, tw, th);
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-          ring[i * T::PMAX + sl] = (s & 1) ? h[s >> 1][i].y : h[s >> 1][i].x;
       }
     }
 #pragma unroll
@@ -837,7 +849,7 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       den += __shfl_xor_sync(0xffffffffu, den, o);
     }
     if ((threadIdx.x & 31) == 0) s_w[warp] = make_float2(num, den);
-    __syncthreads();  // populations consumed, staging and warp sums visible
+    __syncthreads();  // warp sums visible (the populations stay for the export)
     if (threadIdx.x < 32) {
       constexpr int nwarps = T::THREADS / 32;
       float2 v = (int)threadIdx.x < nwarps ? s_w[threadIdx.x] : make_float2(0.0f, 0.0f);
@@ -849,11 +861,19 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       if (threadIdx.x == 0) pp[ntiles + tile] = v;
     }
     {
+      // export band: the new state of the tile's two outer rows and columns, gathered
+      // again from the second sub-iteration's post-collision populations (still in
+      // shared memory), one band slot per thread, coalesced
       float* exp_cur = exports + (size_t)(cyc & 1) * ntiles * pstride + (size_t)tile * pstride;
       const int nslots = 4 * tw + 4 * th - 16;
       for (int sl = threadIdx.x; sl < nslots; sl += T::THREADS) {
+        int x, y;
+        band_coords(sl, tw, th, x, y);
+        const int f = (y + 2) * PXF + x + 2;
+        const bool b = k.walls && ty0 + y == 0, t = k.walls && ty0 + y == ny - 1;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) exp_cur[i * T::PMAX + sl] = ring[i * T::PMAX + sl];
+        for (int i = 1; i < 9; ++i)
+          exp_cur[(i - 1) * T::PMAX + sl] = gather<T::PLANE>(sm, i, f, b, t, vw_b, vw_t);
       }
     }
     // all tiles' bands and both sub-iterations' partial sums are visible
@@ -917,9 +937,9 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       }
     }
     if (rexist) {
-      const float* src = exports + (size_t)(cyc & 1) * ntiles * pstride + (size_t)rnb * pstride;
+      const float* src = exports + (size_t)(cyc & 1) * ntiles * pstride + rsrc;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) ring[i * T::NR + threadIdx.x] = __ldcg(src + i * T::PMAX + rslot);
+      for (int i = 0; i < 8; ++i) ring[i * T::NR + threadIdx.x] = __ldcg(src + i * T::PMAX);
     }
     __syncthreads();
     done = s_done;
@@ -931,7 +951,7 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
   // the registers hold the final state: write it back in place
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
-    if (!valid[s]) continue;
+    if (!valid(s)) continue;
     const int g = (ty0 + ly0 + s * T::ROWS) * nx + tx0 + lx;
 #pragma unroll
     for (int i = 0; i < 8; ++i) hsrc[i * N + g] = (s & 1) ? h[s >> 1][i].y : h[s >> 1][i].x;
