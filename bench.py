@@ -77,9 +77,9 @@ KERNEL_FILES = {
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # of the bench workload (summaries under profiles/, named for the kernel and workload)
 RECORDED_TRAFFIC = {
-    # one potential solve (280 sub-iterations on the captured step): 21.002 MB read,
-    # 0.022 MB written
-    "k_poisson_resident": (21024768, "f8d316dc2d7b3368"),
+    # one potential solve of the two-step loop (280 sub-iterations on the captured step):
+    # 21.020 MB read, 0.043 MB written
+    "k_poisson_resident2": (21063168, "71e9c0953ad656ce"),
     # one coupled pass: 88.125 MB read, 20.214 MB written back during the launch (the
     # rest of its writes leave L2 later)
     "k_coupled": (108339456, "0513d32a7e00c46f"),
