@@ -80,9 +80,9 @@ RECORDED_TRAFFIC = {
     # one potential solve of the two-step loop (280 sub-iterations on the captured step):
     # 21.020 MB read, 0.043 MB written
     "k_poisson_resident2": (21063168, "71e9c0953ad656ce"),
-    # one coupled pass: 88.125 MB read, 20.214 MB written back during the launch (the
+    # one coupled pass: 88.131 MB read, 20.670 MB written back during the launch (the
     # rest of its writes leave L2 later)
-    "k_coupled": (108339456, "0513d32a7e00c46f"),
+    "k_coupled": (108800512, "73074597b0d0bf80"),
 }
 
 
