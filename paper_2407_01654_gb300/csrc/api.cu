@@ -68,7 +68,7 @@ Layout layout_for(const ehd_params& P, int fixed_ty = 0) {
     L.export_floats = 2 * L.rtiles * 8 * (size_t)g.pmax;
   }
   L.exports = take(sizeof(float) * (L.export_floats ? L.export_floats : 1));
-  // [2][tiles] partial sums (two-step loop: [2][2][tiles])
+  // [2][tiles] float2 partial sums (two-step loop: [2][tiles] float4, 16-byte aligned)
   L.rpartials = take(sizeof(float2) * 4 * (L.rtiles > 0 ? L.rtiles : 1));
   L.total = o;
   return L;

@@ -340,7 +340,7 @@ struct Buffers {
   Ctl* ctl;
   DevStats* stats;
   float* exports;    // resident loop: [2][tiles][8][pmax]
-  float2* rpartials; // resident loop: [2][tiles]
+  float2* rpartials; // resident loop: [2][tiles] float2; two-step loop: [2][tiles] float4
 };
 
 __host__ __device__ inline Pops pops_copy(const KParams& k, const Buffers& b, int c) {

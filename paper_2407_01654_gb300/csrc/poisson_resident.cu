@@ -440,6 +440,18 @@ struct Tile2 {
   static_assert(THREADS % 128 == 0, "whole warp quarters for TMEM");
 };
 
+// 16-byte global -> shared copy that bypasses L1 (the source was written by another SM
+// in this launch), completed by cp_async_wait_all in the issuing thread.  Both addresses
+// 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src_gmem) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  const size_t g = __cvta_generic_to_global(src_gmem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // Slot of node (x, y) in the two-node-wide export band of a w x h tile (w, h >= 4): the
 // two bottom rows, the two top rows, then the two left and two right columns between.
 __device__ __forceinline__ int band_slot(int x, int y, int w, int h) {
@@ -555,8 +567,9 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
   // shared memory: [8][PY][PXF] post-collision populations over tile and ring, [PY][PXF]
   // a, [PY][PXF] q, then [8][NR] ring state (also the export staging area)
   extern __shared__ float sm[];
-  __shared__ float2 s_w[T::THREADS / 32];
-  __shared__ int s_done;
+  __shared__ float2 s_w1[T::THREADS / 32], s_w2[T::THREADS / 32];  // warp sums per sub-iteration
+  __shared__ int s_done, s_ok;
+  __shared__ float4 s_pp[160];  // the deciding warp's copy of the tiles' sums
   __shared__ uint32_t s_taddr;
   __shared__ Nb s_nb[3][3];
 
@@ -616,6 +629,7 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       s_nb[dy + 1][dx + 1] = nb;
     }
   }
+  if (threadIdx.x == 0) s_done = 0;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -696,7 +710,27 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
   float rel = 0.0f;
   int done = 0;
   for (;;) {
-    float2* pp = rpartials + (size_t)(cyc & 1) * 2 * ntiles;
+    // ---- after the previous cycle's grid barrier: the deciding warp starts copying that
+    // cycle's per-tile sums and the ring threads import the ring for this one.  Every
+    // thread then collides, and the deciding warp applies the rule to the previous
+    // cycle's two sub-iterations; the collision is dropped if the rule stopped the loop
+    // (it writes shared memory only). ----
+    if (cyc > 0) {
+      if (warp == dwarp) {
+        // the previous cycle's sums of every tile (num and den of its two sub-iterations),
+        // copied while the warp collides its nodes; lane l takes tiles l, l + 32, ...
+        const float4* pp = reinterpret_cast<const float4*>(rpartials) + (size_t)((cyc - 1) & 1) * ntiles;
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int j = 0; j < 5; ++j)
+          if (lane + 32 * j < ntiles) cp_async16(&s_pp[lane + 32 * j], pp + lane + 32 * j);
+      }
+      if (rexist) {  // the thread's own ring slot: no CTA barrier needed before its collision
+        const float* src = exports + (size_t)((cyc - 1) & 1) * ntiles * pstride + rsrc;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) ring[i * T::NR + threadIdx.x] = __ldcg(src + i * T::PMAX);
+      }
+    }
     // ---- sub-iteration 1: collide tile and ring, stream into tile and inner ring ----
     float2 vold[2];
 #pragma unroll
@@ -716,6 +750,63 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
         if (valid(2 * p + 1)) sm[i * T::PLANE + at0 + o1] = hs[i].y;
       }
     }
+    if (cyc > 0 && warp == dwarp) {
+      // the rule, applied to the previous cycle's two sub-iterations in order
+      cp_async_wait_all();
+      const float4* pp = reinterpret_cast<const float4*>(rpartials) + (size_t)((cyc - 1) & 1) * ntiles;
+      const int lane = threadIdx.x & 31;
+      float a1 = 0.0f, b1 = 0.0f, a2 = 0.0f, b2 = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {  // absent tiles add +0: exact for these non-negative sums
+        const float4 v = lane + 32 * j < ntiles ? s_pp[lane + 32 * j] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        a1 += v.x;
+        b1 += v.y;
+        a2 += v.z;
+        b2 += v.w;
+      }
+      for (int t = lane + 160; t < ntiles; t += 32) {
+        const float4 v = __ldcg(pp + t);
+        a1 += v.x;
+        b1 += v.y;
+        a2 += v.z;
+        b2 += v.w;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        b1 += __shfl_xor_sync(0xffffffffu, b1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+      }
+      if (lane == 0) {
+        int d = 0;
+        for (int u = 0; u < 2 && !d; ++u) {
+          const int st = 2 * (cyc - 1) + 1 + u;
+          const float sa = u ? a2 : a1, sb = u ? b2 : b1;
+          float r;
+          if (sa == 0.0f && sb == 0.0f)
+            r = 0.0f;
+          else if (sb == 0.0f)
+            r = __int_as_float(0x7f800000);
+          else
+            r = sqrtf(sa / sb);
+          bool dn;
+          int cv;
+          if (fixed > 0) {
+            dn = st >= fixed;
+            cv = 1;
+          } else {
+            cv = (st >= min_iter) && ((double)r < tol);
+            dn = cv || st >= max_iter;
+          }
+          rel = r;
+          conv = cv;
+          it = st;
+          if (dn) d = u + 1;
+        }
+        s_done = d;
+      }
+    }
     if (rexist) {
       float hr[8];
 #pragma unroll
@@ -729,7 +820,9 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       for (int i = 1; i < 9; ++i)
         sm[(i - 1) * T::PLANE + rf] = h_star(i, hr[i - 1], om, varphi, a, m1x, m1y, qs);
     }
-    __syncthreads();
+    __syncthreads();  // post-collision populations and the rule's verdict visible
+    done = s_done;
+    if (done) break;
     float num = 0.0f, den = 0.0f;
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
@@ -770,18 +863,8 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       num += __shfl_xor_sync(0xffffffffu, num, o);
       den += __shfl_xor_sync(0xffffffffu, den, o);
     }
-    if ((threadIdx.x & 31) == 0) s_w[warp] = make_float2(num, den);
-    __syncthreads();  // populations consumed, inner ring state and warp sums visible
-    if (threadIdx.x < 32) {
-      constexpr int nwarps = T::THREADS / 32;
-      float2 v = (int)threadIdx.x < nwarps ? s_w[threadIdx.x] : make_float2(0.0f, 0.0f);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-      }
-      if (threadIdx.x == 0) pp[tile] = v;
-    }
+    if ((threadIdx.x & 31) == 0) s_w1[warp] = make_float2(num, den);
+    __syncthreads();  // populations consumed
     // ---- sub-iteration 2: collide tile and inner ring, stream into the tile ----
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
@@ -848,18 +931,7 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       num += __shfl_xor_sync(0xffffffffu, num, o);
       den += __shfl_xor_sync(0xffffffffu, den, o);
     }
-    if ((threadIdx.x & 31) == 0) s_w[warp] = make_float2(num, den);
-    __syncthreads();  // warp sums visible (the populations stay for the export)
-    if (threadIdx.x < 32) {
-      constexpr int nwarps = T::THREADS / 32;
-      float2 v = (int)threadIdx.x < nwarps ? s_w[threadIdx.x] : make_float2(0.0f, 0.0f);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-      }
-      if (threadIdx.x == 0) pp[ntiles + tile] = v;
-    }
+    if ((threadIdx.x & 31) == 0) s_w2[warp] = make_float2(num, den);
     {
       // export band: the new state of the tile's two outer rows and columns, gathered
       // again from the second sub-iteration's post-collision populations (still in
@@ -876,8 +948,41 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
           exp_cur[(i - 1) * T::PMAX + sl] = gather<T::PLANE>(sm, i, f, b, t, vw_b, vw_t);
       }
     }
-    // all tiles' bands and both sub-iterations' partial sums are visible
-    if (!grid_barrier(ctl, ntiles, target)) {
+    // ---- grid barrier.  Warp 0 reduces both sub-iterations' warp sums (warps in a fixed
+    // order) and its lane 0 publishes them, then releases the CTA's band writes (ordered
+    // before it by the CTA barrier) and waits, within a time limit, for every tile. ----
+    __syncthreads();
+    target += ntiles;
+    if (threadIdx.x < 32) {
+      constexpr int nwarps = T::THREADS / 32;
+      const bool in = (int)threadIdx.x < nwarps;
+      float2 v1 = in ? s_w1[threadIdx.x] : make_float2(0.0f, 0.0f);
+      float2 v2 = in ? s_w2[threadIdx.x] : make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v1.x += __shfl_xor_sync(0xffffffffu, v1.x, o);
+        v1.y += __shfl_xor_sync(0xffffffffu, v1.y, o);
+        v2.x += __shfl_xor_sync(0xffffffffu, v2.x, o);
+        v2.y += __shfl_xor_sync(0xffffffffu, v2.y, o);
+      }
+      if (threadIdx.x == 0) {
+        reinterpret_cast<float4*>(rpartials)[(size_t)(cyc & 1) * ntiles + tile] =
+            make_float4(v1.x, v1.y, v2.x, v2.y);
+        int ok = 1;
+        red_release_add(&ctl->bar_count, 1u);
+        const unsigned long long t0 = global_ns();
+        while ((int)(ld_acquire(&ctl->bar_count) - target) < 0) {
+          if (global_ns() - t0 > BARRIER_TIMEOUT_NS) {
+            atomicOr(&ctl->bar_error, 1);
+            ok = 0;
+            break;
+          }
+        }
+        s_ok = ok;
+      }
+    }
+    __syncthreads();  // every tile's band and sums visible (or the wait gave up)
+    if (!s_ok) {
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
       if (warp == 0) {
@@ -888,62 +993,6 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       }
       return;
     }
-    // the deciding warp applies the rule to both sub-iterations, in order, while the
-    // other threads import the ring for the next cycle
-    if (warp == dwarp) {
-      const int lane = threadIdx.x & 31;
-      float a1 = 0.0f, b1 = 0.0f, a2 = 0.0f, b2 = 0.0f;
-      for (int t = lane; t < ntiles; t += 32) {
-        const float2 v1 = __ldcg(pp + t), v2 = __ldcg(pp + ntiles + t);
-        a1 += v1.x;
-        b1 += v1.y;
-        a2 += v2.x;
-        b2 += v2.y;
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-        b1 += __shfl_xor_sync(0xffffffffu, b1, o);
-        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-        b2 += __shfl_xor_sync(0xffffffffu, b2, o);
-      }
-      if (lane == 0) {
-        int d = 0;
-        for (int u = 0; u < 2 && !d; ++u) {
-          const int st = 2 * cyc + 1 + u;
-          const float sa = u ? a2 : a1, sb = u ? b2 : b1;
-          float r;
-          if (sa == 0.0f && sb == 0.0f)
-            r = 0.0f;
-          else if (sb == 0.0f)
-            r = __int_as_float(0x7f800000);
-          else
-            r = sqrtf(sa / sb);
-          bool dn;
-          int cv;
-          if (fixed > 0) {
-            dn = st >= fixed;
-            cv = 1;
-          } else {
-            cv = (st >= min_iter) && ((double)r < tol);
-            dn = cv || st >= max_iter;
-          }
-          rel = r;
-          conv = cv;
-          it = st;
-          if (dn) d = u + 1;
-        }
-        s_done = d;
-      }
-    }
-    if (rexist) {
-      const float* src = exports + (size_t)(cyc & 1) * ntiles * pstride + rsrc;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) ring[i * T::NR + threadIdx.x] = __ldcg(src + i * T::PMAX);
-    }
-    __syncthreads();
-    done = s_done;
-    if (done) break;
     ++cyc;
   }
   if (done == 1) tmem_load32(taddr, h);  // the loop stopped after the first sub-iteration
