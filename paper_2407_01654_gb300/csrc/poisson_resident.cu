@@ -554,6 +554,19 @@ __device__ __forceinline__ float gather(const float* sm, int i, int f, bool bw, 
   return sm[(i - 1) * PLANE + f - cy(i) * PXF - cx(i)];
 }
 
+// The same population when the post-collision populations were written in the swapped
+// layout of a second sub-iteration (direction i of the node at f leaves in slot opp(i) of
+// the cell at f + c_i): it is slot opp(i) of the consuming node's own cell, and a node
+// next to a wall finds its own post-collision population opp(i) in slot i of the cell
+// beyond the wall.
+template <int PLANE>
+__device__ __forceinline__ float gather_swapped(const float* sm, int i, int f, bool bw,
+                                                bool tw_, float vw_b, float vw_t) {
+  if (cy(i) > 0 && bw) return h_wall(i, sm[(i - 1) * PLANE + f - cy(i) * PXF - cx(i)], vw_b);
+  if (cy(i) < 0 && tw_) return h_wall(i, sm[(i - 1) * PLANE + f - cy(i) * PXF - cx(i)], vw_t);
+  return sm[(opp(i) - 1) * PLANE + f];
+}
+
 }  // namespace
 
 template <int TY>
@@ -864,8 +877,10 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       den += __shfl_xor_sync(0xffffffffu, den, o);
     }
     if ((threadIdx.x & 31) == 0) s_w1[warp] = make_float2(num, den);
-    __syncthreads();  // populations consumed
-    // ---- sub-iteration 2: collide tile and inner ring, stream into the tile ----
+    // ---- sub-iteration 2: collide tile and inner ring, stream into the tile.  Direction
+    // i of the node at x goes to slot opp(i) of the cell at x + c_i, the one slot the
+    // thread of node x itself read in the first streaming, so no thread can still be
+    // reading a slot this collision overwrites and no CTA barrier is needed before it. ----
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
       const int o0 = 2 * p * T::ROWS * PXF, o1 = (2 * p + 1) * T::ROWS * PXF;
@@ -879,8 +894,9 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       h_star8x2(h[p], om, varphi, a, m1x, m1y, qs, hs);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        if (valid(2 * p)) sm[i * T::PLANE + at0 + o0] = hs[i].x;
-        if (valid(2 * p + 1)) sm[i * T::PLANE + at0 + o1] = hs[i].y;
+        const int sw = (opp(i + 1) - 1) * T::PLANE + cy(i + 1) * PXF + cx(i + 1);
+        if (valid(2 * p)) sm[sw + at0 + o0] = hs[i].x;
+        if (valid(2 * p + 1)) sm[sw + at0 + o1] = hs[i].y;
       }
     }
     if (rlayer1) {
@@ -894,7 +910,8 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       const float a = ca[rf];
 #pragma unroll
       for (int i = 1; i < 9; ++i)
-        sm[(i - 1) * T::PLANE + rf] = h_star(i, hr[i - 1], om, varphi, a, m1x, m1y, qs);
+        sm[(opp(i) - 1) * T::PLANE + cy(i) * PXF + cx(i) + rf] =
+            h_star(i, hr[i - 1], om, varphi, a, m1x, m1y, qs);
     }
     __syncthreads();
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -907,12 +924,12 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
 #pragma unroll
         for (int i = 1; i < 9; ++i)
           h[p][i - 1] = make_float2(
-              gather<T::PLANE>(sm, i, f0, bw(2 * p), tw_(2 * p), vw_b, vw_t),
-              gather<T::PLANE>(sm, i, f1, bw(2 * p + 1), tw_(2 * p + 1), vw_b, vw_t));
+              gather_swapped<T::PLANE>(sm, i, f0, bw(2 * p), tw_(2 * p), vw_b, vw_t),
+              gather_swapped<T::PLANE>(sm, i, f1, bw(2 * p + 1), tw_(2 * p + 1), vw_b, vw_t));
       } else {
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-          const int off = (i - 1) * T::PLANE - cy(i) * PXF - cx(i);
+          const int off = (opp(i) - 1) * T::PLANE;
           h[p][i - 1] = make_float2(sm[off + f0], sm[off + f1]);
         }
       }
@@ -935,7 +952,7 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
     {
       // export band: the new state of the tile's two outer rows and columns, gathered
       // again from the second sub-iteration's post-collision populations (still in
-      // shared memory), one band slot per thread, coalesced
+      // shared memory, swapped layout), one band slot per thread, coalesced
       float* exp_cur = exports + (size_t)(cyc & 1) * ntiles * pstride + (size_t)tile * pstride;
       const int nslots = 4 * tw + 4 * th - 16;
       for (int sl = threadIdx.x; sl < nslots; sl += T::THREADS) {
@@ -945,7 +962,7 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
         const bool b = k.walls && ty0 + y == 0, t = k.walls && ty0 + y == ny - 1;
 #pragma unroll
         for (int i = 1; i < 9; ++i)
-          exp_cur[(i - 1) * T::PMAX + sl] = gather<T::PLANE>(sm, i, f, b, t, vw_b, vw_t);
+          exp_cur[(i - 1) * T::PMAX + sl] = gather_swapped<T::PLANE>(sm, i, f, b, t, vw_b, vw_t);
       }
     }
     // ---- grid barrier.  Warp 0 reduces both sub-iterations' warp sums (warps in a fixed
