@@ -71,6 +71,7 @@ def peaks():
 KERNEL_FILES = {
     "k_poisson_resident": ("poisson_resident.cu", "ehd_internal.cuh"),
     "k_poisson_resident2": ("poisson_resident.cu", "ehd_internal.cuh"),
+    "k_poisson_resident3": ("poisson_resident.cu", "ehd_internal.cuh"),
     "k_coupled": ("kernels.cu", "ehd_internal.cuh"),
     "k_poisson": ("poisson.cu", "ehd_internal.cuh"),
 }
@@ -263,8 +264,8 @@ def run_gpu(args, rank, world):
     sim = ehd.Sim(p, stream=stream)
     sim.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
     loop_kind = sim.loop_kind()
-    resident = loop_kind in (2, 3)
-    rkernel = "k_poisson_resident2" if loop_kind == 3 else "k_poisson_resident"
+    resident = loop_kind in (2, 3, 4)
+    rkernel = {3: "k_poisson_resident2", 4: "k_poisson_resident3"}.get(loop_kind, "k_poisson_resident")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     sim.step(args.warmup)
     # the state the timed steps start from: the per-kernel profile below replays exactly
@@ -384,6 +385,8 @@ def run_gpu(args, rank, world):
                    "potential_loop": {1: "streaming (one launch per sub-iteration, graph WHILE node)",
                                       2: "resident (on chip, one cooperative launch per step)",
                                       3: "resident, two sub-iterations per halo exchange (on chip, "
+                                         "one cooperative launch per step)",
+                                      4: "resident, three sub-iterations per halo exchange (on chip, "
                                          "one cooperative launch per step)"}[loop_kind],
                    "schedule": dict(schedule, autotuned=True) if schedule else "built-in",
                    "l2": "flushed between timed steps (512 MiB device write outside the events)",

@@ -55,7 +55,13 @@ enum { EHD_FP32 = 0, EHD_FP16DEV = 1 };
  * STREAM runs one kernel per sub-iteration over populations in device memory; RESIDENT
  * runs the whole loop in one cooperative kernel with the populations held on chip (only
  * for lattices that fit, about 600k nodes on a GB300); AUTO picks RESIDENT when it fits. */
-enum { EHD_LOOP_AUTO = 0, EHD_LOOP_STREAM = 1, EHD_LOOP_RESIDENT = 2, EHD_LOOP_RESIDENT2 = 3 };
+enum {
+  EHD_LOOP_AUTO = 0,
+  EHD_LOOP_STREAM = 1,
+  EHD_LOOP_RESIDENT = 2,
+  EHD_LOOP_RESIDENT2 = 3,
+  EHD_LOOP_RESIDENT3 = 4
+};
 
 /* Field selection bits for ehd_read_fields. */
 enum {
@@ -105,9 +111,11 @@ typedef struct ehd_params {
   int32_t poisson_min_iter;     /* at least this many sub-iterations (>= 1)               */
   int32_t poisson_fixed_iter;   /* > 0: exactly this many sub-iterations, no stopping test*/
   int32_t poisson_loop;         /* EHD_LOOP_AUTO, EHD_LOOP_STREAM, EHD_LOOP_RESIDENT (the
-                                   whole loop on chip) or EHD_LOOP_RESIDENT2 (on chip, two
+                                   whole loop on chip), EHD_LOOP_RESIDENT2 (on chip, two
                                    sub-iterations per halo exchange; tiles of 24..64 rows,
-                                   every tile at least 4 x 4).  The states are the same   */
+                                   every tile at least 4 x 4) or EHD_LOOP_RESIDENT3 (three;
+                                   48..64 rows, every tile at least 6 x 6).  Every loop
+                                   gives the same states, bit for bit                    */
   int64_t start_step;           /* step counter after ehd_set_fields                      */
   int32_t tile_rows;            /* resident potential loop: 0 = tiles chosen from the
                                    lattice size (about 2048 nodes each, at most one per
@@ -191,8 +199,8 @@ int ehd_set_fields(ehd_sim* sim, const void* phi, const void* q, const void* ux,
  * when the statistics are read). */
 int ehd_step(ehd_sim* sim, int nsteps, ehd_stats* stats);
 
-/* Which potential loop this simulation runs: EHD_LOOP_STREAM, EHD_LOOP_RESIDENT or
- * EHD_LOOP_RESIDENT2 (negative: invalid handle). */
+/* Which potential loop this simulation runs: EHD_LOOP_STREAM, EHD_LOOP_RESIDENT,
+ * EHD_LOOP_RESIDENT2 or EHD_LOOP_RESIDENT3 (negative: invalid handle). */
 int ehd_loop_kind(const ehd_sim* sim);
 
 /* Statistics accumulated since they were last cleared (by ehd_step with stats, or by this

@@ -2,9 +2,9 @@
 
 For one lattice shape (nx, ny, walls, storage precision) it times every candidate
 schedule of the potential loop -- the streaming kernel (one launch per sub-iteration in a
-graph WHILE node), the resident on-chip loop and the on-chip loop with two sub-iterations
-per exchange, each with every tile height of 64-wide tiles (`tile_rows`; 0 = the built-in
-choice of about 2048 nodes per tile) -- on a short run with
+graph WHILE node), the resident on-chip loop and the on-chip loops with two and three
+sub-iterations per exchange, each with every tile height of 64-wide tiles (`tile_rows`;
+0 = the built-in choice of about 2048 nodes per tile) -- on a short run with
 a fixed number of sub-iterations, and returns the fastest as parameter overrides.  All
 candidates compute the same bits at a fixed sub-iteration count (the tests check this), so
 tuning changes speed only.  Results are cached per device and lattice shape in a JSON
@@ -22,7 +22,7 @@ import time
 import numpy as np
 
 TILE_ROWS = (0, 8, 16, 24, 32, 40, 48, 56, 64)
-LOOP_STREAM, LOOP_RESIDENT, LOOP_RESIDENT2 = 1, 2, 3
+LOOP_STREAM, LOOP_RESIDENT, LOOP_RESIDENT2, LOOP_RESIDENT3 = 1, 2, 3, 4
 
 
 def candidates(params):
@@ -36,9 +36,11 @@ def candidates(params):
     out = [{"poisson_loop": LOOP_STREAM, "tile_rows": 0},
            {"poisson_loop": LOOP_RESIDENT, "tile_rows": 0}]
     out += [{"poisson_loop": LOOP_RESIDENT, "tile_rows": r} for r in rows]
-    # two sub-iterations per exchange: tiles of 24 rows or more
+    # two sub-iterations per exchange: tiles of 24 rows or more; three: 48 or more
     out += [{"poisson_loop": LOOP_RESIDENT2, "tile_rows": 0}]
     out += [{"poisson_loop": LOOP_RESIDENT2, "tile_rows": r} for r in rows if r >= 24]
+    out += [{"poisson_loop": LOOP_RESIDENT3, "tile_rows": 0}]
+    out += [{"poisson_loop": LOOP_RESIDENT3, "tile_rows": r} for r in rows if r >= 48]
     return out
 
 

@@ -28,6 +28,12 @@ struct Layout {
 // fewer SMs the tiles are larger and fewer, which needs less export space.
 constexpr int DESIGN_SMS = 152;
 
+// Sub-iterations per halo exchange of the on-chip loop a poisson_loop value asks for (0:
+// one, the one-step loop; also for the automatic choice and the streaming loop).
+int loop_depth(int poisson_loop) {
+  return poisson_loop == EHD_LOOP_RESIDENT3 ? 3 : (poisson_loop == EHD_LOOP_RESIDENT2 ? 2 : 0);
+}
+
 Layout layout_for(const ehd_params& P, int fixed_ty = 0) {
   const int64_t N = (int64_t)P.nx * P.ny;
   Layout L{};
@@ -62,14 +68,14 @@ Layout layout_for(const ehd_params& P, int fixed_ty = 0) {
   kp.ny = P.ny;
   L.export_floats = 0;
   L.rtiles = 0;
-  if (resident_geometry(kp, DESIGN_SMS, &g, &th, &sm, fixed_ty,
-                        P.poisson_loop == EHD_LOOP_RESIDENT2)) {
+  if (resident_geometry(kp, DESIGN_SMS, &g, &th, &sm, fixed_ty, loop_depth(P.poisson_loop))) {
     L.rtiles = (size_t)g.ntx * g.nty;
     L.export_floats = 2 * L.rtiles * 8 * (size_t)g.pmax;
   }
   L.exports = take(sizeof(float) * (L.export_floats ? L.export_floats : 1));
-  // [2][tiles] float2 partial sums (two-step loop: [2][tiles] float4, 16-byte aligned)
-  L.rpartials = take(sizeof(float2) * 4 * (L.rtiles > 0 ? L.rtiles : 1));
+  // [2][tiles] float2 partial sums (multi-step loop: [2][tiles] one or two float4,
+  // 16-byte aligned)
+  L.rpartials = take(sizeof(float2) * 8 * (L.rtiles > 0 ? L.rtiles : 1));
   L.total = o;
   return L;
 }
@@ -94,7 +100,7 @@ int validate(const ehd_params* p) {
     return EHD_ERR_INVALID_ARG;
   if (p->poisson_fixed_iter == 0 && !(p->poisson_tol > 0)) return EHD_ERR_INVALID_ARG;
   if (p->ramp_steps < 0) return EHD_ERR_INVALID_ARG;
-  if (p->poisson_loop < EHD_LOOP_AUTO || p->poisson_loop > EHD_LOOP_RESIDENT2)
+  if (p->poisson_loop < EHD_LOOP_AUTO || p->poisson_loop > EHD_LOOP_RESIDENT3)
     return EHD_ERR_INVALID_ARG;
   if (p->tile_rows < 0 || p->tile_rows > 64 || p->tile_rows % 8 != 0)
     return EHD_ERR_INVALID_ARG;
@@ -460,14 +466,14 @@ int sim_create(const ehd_params* params, void* workspace, size_t workspace_bytes
       ResidentGeom g;
       int th;
       size_t sm;
-      const bool two = params->poisson_loop == EHD_LOOP_RESIDENT2;
-      if (resident_geometry(s->kp, use_sms, &g, &th, &sm, fixed_ty, two) &&
+      const int depth = loop_depth(params->poisson_loop);
+      if (resident_geometry(s->kp, use_sms, &g, &th, &sm, fixed_ty, depth) &&
           2 * (size_t)g.ntx * g.nty * 8 * g.pmax <= L.export_floats &&
           (size_t)g.ntx * g.nty <= L.rtiles &&
-          cudaFuncSetAttribute(resident_kernel(g.TY, two), cudaFuncAttributeMaxDynamicSharedMemorySize,
+          cudaFuncSetAttribute(resident_kernel(g.TY, depth), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)sm) == cudaSuccess) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_kernel(g.TY, two), th, sm) ==
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_kernel(g.TY, depth), th, sm) ==
                 cudaSuccess &&
             per_sm >= 1 && (long long)g.ntx * g.nty <= (long long)per_sm * sms) {
           s->resident_ok = true;
@@ -478,7 +484,8 @@ int sim_create(const ehd_params* params, void* workspace, size_t workspace_bytes
       }
     }
     cudaGetLastError();
-    if ((params->poisson_loop == EHD_LOOP_RESIDENT || params->poisson_loop == EHD_LOOP_RESIDENT2) &&
+    if ((params->poisson_loop == EHD_LOOP_RESIDENT || params->poisson_loop == EHD_LOOP_RESIDENT2 ||
+         params->poisson_loop == EHD_LOOP_RESIDENT3) &&
         !s->resident_ok) {
       ehd_destroy(s);
       return EHD_ERR_INVALID_ARG;  // the lattice does not fit on chip on this device
@@ -673,7 +680,8 @@ int ehd_diag_expire_barrier(ehd_sim* s) {
 int ehd_loop_kind(const ehd_sim* s) {
   if (!s) return -1;
   if (!s->resident_ok) return EHD_LOOP_STREAM;
-  return s->rg.two ? EHD_LOOP_RESIDENT2 : EHD_LOOP_RESIDENT;
+  return s->rg.depth == 3 ? EHD_LOOP_RESIDENT3
+                          : (s->rg.depth == 2 ? EHD_LOOP_RESIDENT2 : EHD_LOOP_RESIDENT);
 }
 
 int ehd_read_stats(ehd_sim* s, ehd_stats* out) {

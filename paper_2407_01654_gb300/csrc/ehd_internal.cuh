@@ -189,7 +189,7 @@ struct Ctl {
 // column / row may be smaller), pmax perimeter slots per tile.
 struct ResidentGeom {
   int TX, TY, ntx, nty, pmax;
-  int two;  // 1: two sub-iterations per exchange (two-node-wide ring and export band)
+  int depth;  // 0: one sub-iteration per exchange; 2, 3: that many (ring and band as wide)
 };
 
 struct DevStats {
@@ -340,7 +340,7 @@ struct Buffers {
   Ctl* ctl;
   DevStats* stats;
   float* exports;    // resident loop: [2][tiles][8][pmax]
-  float2* rpartials; // resident loop: [2][tiles] float2; two-step loop: [2][tiles] float4
+  float2* rpartials; // resident loop: [2][tiles] float2; D-step loop: [2][tiles][D / 2 + D % 2] float4
 };
 
 __host__ __device__ inline Pops pops_copy(const KParams& k, const Buffers& b, int c) {
@@ -391,10 +391,10 @@ cudaError_t add_coupled_batch_node(cudaGraph_t g, const cudaGraphNode_t* deps, s
 // Resident potential loop (poisson_resident.cu).  fixed_ty > 0: tiles of 64 x fixed_ty
 // (a multiple of 8 up to 64).
 bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* threads,
-                       size_t* smem, int fixed_ty = 0, bool two = false);
+                       size_t* smem, int fixed_ty = 0, int depth = 0);
 // The single-simulation kernel of a tile height (nullptr if none): heights 8..64 in
 // steps of 8; with two sub-iterations per exchange, 24..64.
-const void* resident_kernel(int tile_rows, bool two = false);
+const void* resident_kernel(int tile_rows, int depth = 0);
 const void* resident_batch_kernel(int tile_rows);  // 16, 32 or 64; else nullptr
 cudaError_t launch_poisson_resident(const KParams& kp, const ResidentGeom& g, int threads,
                                     size_t smem, const Buffers& b, cudaStream_t st);

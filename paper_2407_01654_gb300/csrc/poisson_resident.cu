@@ -1046,10 +1046,588 @@ __global__ void __launch_bounds__(Tile2<TY>::THREADS, 1)
   resident_loop2<TY>(k, rg, hbuf, aq, exports, rpartials, ctl, blockIdx.x, gridDim.x);
 }
 
-// The kernel of a tile height (nullptr: not a supported height); two: the loop with two
-// sub-iterations per exchange (heights 24 to 64).
-const void* resident_kernel(int ty, bool two) {
-  if (two) {
+// ---------------------------------------------------------------------------------------
+// D sub-iterations per exchange, written for any D (used for D = 3: the loop above is a
+// hand-scheduled D = 2 and measured 2 % faster than this form at D = 2, with the same
+// bits).  Sub-iteration u (0-based) of a cycle collides the tile and the ring layers
+// 1 .. D - u and streams into the tile and the layers 1 .. D - 1 - u, in the own layout
+// for even u and the swapped layout for odd u; the states after sub-iterations 0 .. D - 2
+// are parked in TMEM.  Every CTA reaches the same decisions and each state is the one
+// resident_loop produces, bit for bit.
+// ---------------------------------------------------------------------------------------
+namespace {
+
+// Compile-time shape of a 64 x TY tile with a D-node-wide ring.
+template <int TY, int D>
+struct TileD {
+  static_assert(D == 2 || D == 3, "two or three sub-iterations per exchange");
+  static_assert(TY % 8 == 0 && TY <= 64, "tile height: a multiple of 8 up to 64");
+  static constexpr int PX = TXR + 2 * D;            // frame row: tile row and ring
+  static constexpr int PY = TY + 2 * D;
+  static constexpr int PLANE = PY * PX;             // one direction over tile and ring
+  static constexpr int THREADS = TXR * TY / NPT;
+  static constexpr int ROWS = TY / NPT;
+  static constexpr int NR = 2 * D * PX + 2 * D * TY;     // ring nodes of a full tile
+  static constexpr int PMAX = 2 * D * TXR + 2 * D * TY;  // band slots (a full tile: 4 D^2 fewer)
+  static constexpr int SLOT_COLS = (THREADS / 128) * 32;  // TMEM columns of one parked state
+  static constexpr int TCOLS = pow2_at_least((D - 1) * SLOT_COLS);
+  static constexpr int SUMS4 = D == 2 ? 1 : 2;      // float4 of sums per tile and cycle
+  static_assert(THREADS >= NR, "one ring node per thread at most");
+  static_assert(THREADS % 128 == 0, "whole warp quarters for TMEM");
+  static_assert((D - 1) * SLOT_COLS <= 512, "the parked states fit in tensor memory");
+};
+
+// Slot of node (x, y) in the D-node-wide export band of a w x h tile (w, h >= 2 D): the
+// D bottom rows, the D top rows, then the D left and D right columns between.
+template <int D>
+__device__ __forceinline__ int band_slot_d(int x, int y, int w, int h) {
+  if (y < D) return y * w + x;
+  if (y >= h - D) return D * w + (y - (h - D)) * w + x;
+  if (x < D) return 2 * D * w + (y - D) * D + x;
+  return 2 * D * w + D * (h - 2 * D) + (y - D) * D + (x - (w - D));
+}
+
+// Inverse of band_slot: the node of band slot sl of a w x h tile.
+template <int D>
+__device__ __forceinline__ void band_coords_d(int sl, int w, int h, int& x, int& y) {
+  if (sl < 2 * D * w) {
+    int r = 0;
+    while (sl >= w) {
+      sl -= w;
+      ++r;
+    }
+    y = r < D ? r : h - 2 * D + r;
+    x = sl;
+    return;
+  }
+  sl -= 2 * D * w;
+  if (sl < D * (h - 2 * D)) {
+    y = D + sl / D;
+    x = sl % D;
+    return;
+  }
+  sl -= D * (h - 2 * D);
+  y = D + sl / D;
+  x = w - D + sl % D;
+}
+
+// Tile-relative coordinates of ring node r of a tw x th tile: D rows below, D rows above
+// (each tw + 2 D wide), then D columns left and D right (th high).
+template <int D>
+__device__ __forceinline__ void ring_coords_d(int r, int tw, int th, int& x, int& y) {
+  const int wd = tw + 2 * D;
+  if (r < 2 * D * wd) {
+    int k = 0;
+    while (r >= wd) {
+      r -= wd;
+      ++k;
+    }
+    y = k < D ? k - D : th + k - D;
+    x = r - D;
+    return;
+  }
+  r -= 2 * D * wd;
+  if (r < D * th) {
+    y = r / D;
+    x = -D + r % D;
+    return;
+  }
+  r -= D * th;
+  y = r / D;
+  x = tw + r % D;
+}
+
+// Post-stream population i of the node at frame index f of a frame PX wide.  Own layout
+// (swapped = false): direction i of the node at x sits in slot i of its own cell, so the
+// source is slot i of the cell at f - c_i; a node next to a wall (bw / tw_: on the bottom /
+// top lattice row of a walled lattice) takes the anti-bounce-back rule on its own
+// post-collision population opp(i).  Swapped layout: direction i of the node at x sits in
+// slot opp(i) of the cell at x + c_i, so the source is slot opp(i) of the consuming node's
+// own cell, and a node next to a wall finds its own population opp(i) in slot i of the cell
+// beyond the wall.
+template <int PLANE, int PX>
+__device__ __forceinline__ float gather_d(const float* sm, int i, int f, bool bw, bool tw_,
+                                          float vw_b, float vw_t, bool swapped) {
+  const int own = (opp(i) - 1) * PLANE + f;                // own cell, slot opp(i)
+  const int back = (i - 1) * PLANE + f - cy(i) * PX - cx(i);  // cell f - c_i, slot i
+  if (cy(i) > 0 && bw) return h_wall(i, sm[swapped ? back : own], vw_b);
+  if (cy(i) < 0 && tw_) return h_wall(i, sm[swapped ? back : own], vw_t);
+  return sm[swapped ? own : back];
+}
+
+// Where direction i of the node at frame index f goes after its collision.
+template <int PLANE, int PX>
+__device__ __forceinline__ int scatter_at(int i, int f, bool swapped) {
+  return swapped ? (opp(i) - 1) * PLANE + f + cy(i) * PX + cx(i) : (i - 1) * PLANE + f;
+}
+
+}  // namespace
+
+template <int TY, int D>
+__device__ __forceinline__ void resident_loopD(const KParams& k, const ResidentGeom& rg,
+                                               float* __restrict__ hbuf,
+                                               const float2* __restrict__ aq,
+                                               float* __restrict__ exports,
+                                               float2* __restrict__ rpartials, Ctl* ctl,
+                                               const int tile, const int ntiles) {
+  using T = TileD<TY, D>;
+  constexpr int PX = T::PX;
+  // shared memory: [8][PY][PX] post-collision populations over tile and ring, [PY][PX] a,
+  // [PY][PX] q, then [8][NR] ring state (each ring node belongs to one thread)
+  extern __shared__ __align__(16) float smd[];
+  float* sm = smd;
+  __shared__ float2 s_w[D][T::THREADS / 32];  // warp sums per sub-iteration
+  __shared__ int s_done, s_ok;
+  __shared__ float4 s_pp[160 * T::SUMS4];     // the deciding warp's copy of the tiles' sums
+  __shared__ uint32_t s_taddr;
+  __shared__ Nb s_nb[3][3];
+
+  const int nx = k.nx, ny = k.ny;
+  const size_t N = (size_t)k.N;
+  const int tcol = tile % rg.ntx, trow = tile / rg.ntx;
+  const int tx0 = tcol * TXR, ty0 = trow * TY;
+  const int tw = min(TXR, nx - tx0), th = min(TY, ny - ty0);
+  float* ca = sm + 8 * T::PLANE;
+  float* cq = ca + T::PLANE;
+  float* ring = cq + T::PLANE;
+  const int parity = ld_cg(&ctl->parity);
+  float* __restrict__ hsrc = hbuf + (size_t)parity * NH * N;
+  const float qshift = k.neutralize ? ld_cg(&ctl->mean_q) : 0.0f;
+  const float vw_b = ld_cg(&ctl->vw_b), vw_t = ld_cg(&ctl->vw_t);
+  const double tol = ctl->tol;
+  const int min_iter = ctl->min_iter, max_iter = ctl->max_iter, fixed = ctl->fixed_iter;
+  const float om = k.omega_h;
+  constexpr int pstride = 8 * T::PMAX;
+  const int warp = threadIdx.x >> 5;
+  constexpr int dwarp = T::THREADS / 32 - 1;
+
+  // TMEM for the parked states: warp w uses lanes 32 (w mod 4) .. + 31 and, for the state
+  // after sub-iteration u, columns u SLOT_COLS + 32 (w / 4) .. + 31
+  if (warp == 0) {
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_taddr);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst),
+                 "n"(T::TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+
+  // my tile nodes: column lx, rows ly0 + s ROWS
+  const int lx = threadIdx.x & (TXR - 1);
+  const int ly0 = threadIdx.x >> 6;
+  const int at0 = (ly0 + D) * PX + lx + D;  // frame index of node 0
+  const int nrows = lx < tw ? th : 0;
+
+  if (threadIdx.x < 9) {
+    const int dx = (int)threadIdx.x % 3 - 1, dy = (int)threadIdx.x / 3 - 1;
+    const int c = (tcol + dx + rg.ntx) % rg.ntx;
+    int r = trow + dy;
+    Nb nb;
+    if (r < 0 || r >= rg.nty) {
+      if (k.walls) {
+        nb.id = -1;
+        nb.w = nb.h = 0;
+        s_nb[dy + 1][dx + 1] = nb;
+        r = -1;
+      } else {
+        r = (r + rg.nty) % rg.nty;
+      }
+    }
+    if (r >= 0) {
+      nb.id = r * rg.ntx + c;
+      nb.w = min(TXR, nx - c * TXR);
+      nb.h = min(TY, ny - r * TY);
+      s_nb[dy + 1][dx + 1] = nb;
+    }
+  }
+  if (threadIdx.x == 0) s_done = 0;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = s_taddr + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * (warp >> 2));
+
+  // my ring node (thread r < number of ring nodes): frame index, layer (1 next to the
+  // tile .. D), wall rows, import source
+  const int nring = 2 * D * (tw + 2 * D) + 2 * D * th;
+  int rf = 0, rsrc = 0, rl = D + 1;  // rl > D: no ring node
+  bool rbw = false, rtw = false;
+  if ((int)threadIdx.x < nring) {
+    int x, y;
+    ring_coords_d<D>(threadIdx.x, tw, th, x, y);
+    rf = (y + D) * PX + x + D;
+    const int nbx = x < 0 ? 0 : (x >= tw ? 2 : 1);
+    const int nby = y < 0 ? 0 : (y >= th ? 2 : 1);
+    const Nb nb = s_nb[nby][nbx];
+    if (nb.id >= 0) {
+      const int olx = x < 0 ? nb.w + x : (x >= tw ? x - tw : x);
+      const int oly = y < 0 ? nb.h + y : (y >= th ? y - th : y);
+      rsrc = nb.id * pstride + band_slot_d<D>(olx, oly, nb.w, nb.h);
+      const int lxd = x < 0 ? -x : (x >= tw ? x - tw + 1 : 0);
+      const int lyd = y < 0 ? -y : (y >= th ? y - th + 1 : 0);
+      rl = lxd > lyd ? lxd : lyd;
+      const int gy = ty0 + y;
+      rbw = k.walls && gy == 0;
+      rtw = k.walls && gy == ny - 1;
+      // first import: the lattice's own post-stream state; coefficients once per solve
+      const int gx = (tx0 + x + nx) % nx;
+      const int g = ((gy + ny) % ny) * nx + gx;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) ring[i * T::NR + threadIdx.x] = hsrc[i * N + g];
+      const float2 c = aq[g];
+      ca[rf] = c.x;
+      cq[rf] = c.y - qshift;
+    }
+  }
+
+  // my tile nodes: state in registers (two packed pairs), coefficients in the frame.
+  // Nodes outside the lattice (partial tiles) compute with their pair but write nothing
+  // to shared memory: their cells may be ring nodes of this tile.
+  float2 h[2][8];
+  // per node: inside the lattice; on the bottom / top lattice row next to a wall
+  auto valid = [&](int s) { return ly0 + s * T::ROWS < nrows; };
+  auto bw = [&](int s) { return k.walls && ty0 + ly0 + s * T::ROWS == 0; };
+  auto tw_ = [&](int s) { return k.walls && ty0 + ly0 + s * T::ROWS == ny - 1; };
+#pragma unroll
+  for (int s = 0; s < NPT; ++s) {
+    const int ly = ly0 + s * T::ROWS;
+    float v[8];
+    float a = 0.0f, q = 0.0f;
+    if (valid(s)) {
+      const int g = (ty0 + ly) * nx + tx0 + lx;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = hsrc[i * N + g];
+      const float2 c = aq[g];
+      a = c.x;
+      q = c.y - qshift;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = 0.0f;
+    }
+    if (valid(s)) {  // a node outside the lattice may sit on a ring node's cell
+      ca[at0 + s * T::ROWS * PX] = a;
+      cq[at0 + s * T::ROWS * PX] = q;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (s & 1)
+        h[s >> 1][i].y = v[i];
+      else
+        h[s >> 1][i].x = v[i];
+    }
+  }
+  __syncthreads();
+
+  // collision of the tile nodes into the frame (own or swapped layout); varphi before it
+  // kept in vold for the rule
+  float2 vold[2];
+  auto collide_tile = [&](bool swapped) {
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int o0 = 2 * p * T::ROWS * PX, o1 = (2 * p + 1) * T::ROWS * PX;
+      const float2 varphi = h_varphi2(h_sum8x2(h[p]));
+      vold[p] = varphi;
+      float2 m1x, m1y;
+      h_moment1x2(h[p], m1x, m1y);
+      const float2 a = make_float2(ca[at0 + o0], ca[at0 + o1]);
+      const float2 qs = __fmul2_rn(f2(0.125f), make_float2(cq[at0 + o0], cq[at0 + o1]));
+      float2 hs[8];
+      h_star8x2(h[p], om, varphi, a, m1x, m1y, qs, hs);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int d = scatter_at<T::PLANE, PX>(i + 1, at0, swapped);
+        if (valid(2 * p)) sm[d + o0] = hs[i].x;
+        if (valid(2 * p + 1)) sm[d + o1] = hs[i].y;
+      }
+    }
+  };
+  // collision of my ring node (its state in the ring array)
+  auto collide_ring = [&](bool swapped) {
+    float hr[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) hr[i] = ring[i * T::NR + threadIdx.x];
+    const float varphi = h_varphi(h_sum8(hr));
+    float m1x, m1y;
+    h_moment1(hr, m1x, m1y);
+    const float qs = 0.125f * cq[rf];
+    const float a = ca[rf];
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+      sm[scatter_at<T::PLANE, PX>(i, rf, swapped)] =
+          h_star(i, hr[i - 1], om, varphi, a, m1x, m1y, qs);
+  };
+  // streaming into the tile nodes; returns the thread's (num, den) of the rule
+  auto stream_tile = [&](bool swapped) {
+    float num = 0.0f, den = 0.0f;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int f0 = at0 + 2 * p * T::ROWS * PX, f1 = at0 + (2 * p + 1) * T::ROWS * PX;
+      if (bw(2 * p) || tw_(2 * p) || bw(2 * p + 1) || tw_(2 * p + 1)) {
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+          h[p][i - 1] = make_float2(
+              gather_d<T::PLANE, PX>(sm, i, f0, bw(2 * p), tw_(2 * p), vw_b, vw_t, swapped),
+              gather_d<T::PLANE, PX>(sm, i, f1, bw(2 * p + 1), tw_(2 * p + 1), vw_b, vw_t,
+                                   swapped));
+      } else {
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+          const int off = swapped ? (opp(i) - 1) * T::PLANE : (i - 1) * T::PLANE - cy(i) * PX - cx(i);
+          h[p][i - 1] = make_float2(sm[off + f0], sm[off + f1]);
+        }
+      }
+      const float2 d = __fadd2_rn(h_varphi2(h_sum8x2(h[p])), neg2(vold[p]));
+      if (valid(2 * p)) {
+        num = __fmaf_rn(d.x, d.x, num);
+        den = __fmaf_rn(vold[p].x, vold[p].x, den);
+      }
+      if (valid(2 * p + 1)) {
+        num = __fmaf_rn(d.y, d.y, num);
+        den = __fmaf_rn(vold[p].y, vold[p].y, den);
+      }
+    }
+    return make_float2(num, den);
+  };
+
+  unsigned target = 0;
+  int cyc = 0, it = 0, conv = 0;
+  float rel = 0.0f;
+  int done = 0;
+  for (;;) {
+    // ---- after the previous cycle's grid barrier: the deciding warp starts copying that
+    // cycle's per-tile sums and the ring threads import the ring for this one.  Every
+    // thread then collides, and the deciding warp applies the rule to the previous
+    // cycle's D sub-iterations; the collision is dropped if the rule stopped the loop
+    // (it writes shared memory only). ----
+    if (cyc > 0) {
+      if (warp == dwarp) {
+        // the previous cycle's sums of every tile (num and den of its D sub-iterations),
+        // copied while the warp collides its nodes; lane l takes tiles l, l + 32, ...
+        const float4* pp = reinterpret_cast<const float4*>(rpartials) +
+                           (size_t)((cyc - 1) & 1) * ntiles * T::SUMS4;
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          const int t = lane + 32 * j;
+          if (t < ntiles) {
+#pragma unroll
+            for (int e = 0; e < T::SUMS4; ++e)
+              cp_async16(&s_pp[t * T::SUMS4 + e], pp + (size_t)t * T::SUMS4 + e);
+          }
+        }
+      }
+      if (rl <= D) {  // the thread's own ring slot: no CTA barrier needed before its collision
+        const float* src = exports + (size_t)((cyc - 1) & 1) * ntiles * pstride + rsrc;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) ring[i * T::NR + threadIdx.x] = __ldcg(src + i * T::PMAX);
+      }
+    }
+    // ---- sub-iteration 0: own layout; collide tile and all ring layers ----
+    collide_tile(false);
+    if (cyc > 0 && warp == dwarp) {
+      // the rule, applied to the previous cycle's sub-iterations in order
+      cp_async_wait_all();
+      const float4* pp = reinterpret_cast<const float4*>(rpartials) +
+                         (size_t)((cyc - 1) & 1) * ntiles * T::SUMS4;
+      const int lane = threadIdx.x & 31;
+      float sa[D], sb[D];
+#pragma unroll
+      for (int u = 0; u < D; ++u) sa[u] = sb[u] = 0.0f;
+      auto add = [&](int t, bool cached) {
+        const float4 v0 = cached ? s_pp[t * T::SUMS4] : __ldcg(pp + (size_t)t * T::SUMS4);
+        sa[0] += v0.x;
+        sb[0] += v0.y;
+        sa[1] += v0.z;
+        sb[1] += v0.w;
+        if constexpr (D == 3) {
+          const float4 v1 = cached ? s_pp[t * T::SUMS4 + 1] : __ldcg(pp + (size_t)t * T::SUMS4 + 1);
+          sa[2] += v1.x;
+          sb[2] += v1.y;
+        }
+      };
+      // lane l sums tiles l, l + 32, ... in that order
+#pragma unroll
+      for (int j = 0; j < 5; ++j)
+        if (lane + 32 * j < ntiles) add(lane + 32 * j, true);
+      for (int t = lane + 160; t < ntiles; t += 32) add(t, false);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int u = 0; u < D; ++u) {
+          sa[u] += __shfl_xor_sync(0xffffffffu, sa[u], o);
+          sb[u] += __shfl_xor_sync(0xffffffffu, sb[u], o);
+        }
+      }
+      if (lane == 0) {
+        int d = 0;
+#pragma unroll
+        for (int u = 0; u < D; ++u) {
+          if (d) break;
+          const int st = D * (cyc - 1) + 1 + u;
+          float r;
+          if (sa[u] == 0.0f && sb[u] == 0.0f)
+            r = 0.0f;
+          else if (sb[u] == 0.0f)
+            r = __int_as_float(0x7f800000);
+          else
+            r = sqrtf(sa[u] / sb[u]);
+          bool dn;
+          int cv;
+          if (fixed > 0) {
+            dn = st >= fixed;
+            cv = 1;
+          } else {
+            cv = (st >= min_iter) && ((double)r < tol);
+            dn = cv || st >= max_iter;
+          }
+          rel = r;
+          conv = cv;
+          it = st;
+          if (dn) d = u + 1;
+        }
+        s_done = d;
+      }
+    }
+    if (rl <= D) collide_ring(false);
+    __syncthreads();  // post-collision populations and the rule's verdict visible
+    done = s_done;
+    if (done) break;
+    // ---- sub-iterations 0 .. D - 1: stream (layout of the collision), collide the next
+    // with the other layout.  Sub-iteration u + 1 writes direction i of node x into a slot
+    // that, in the streaming of sub-iteration u, only the thread of node x itself read, so
+    // no CTA barrier is needed between a streaming and the next collision. ----
+#pragma unroll
+    for (int u = 0; u < D; ++u) {
+      const bool sw = (u & 1) != 0;
+      if (u > 0) {
+        collide_tile(sw);
+        if (rl <= D - u) collide_ring(sw);
+        __syncthreads();  // post-collision populations visible
+      }
+      float2 ws = stream_tile(sw);
+      if (rl <= D - 1 - u) {
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+          ring[(i - 1) * T::NR + threadIdx.x] =
+              gather_d<T::PLANE, PX>(sm, i, rf, rbw, rtw, vw_b, vw_t, sw);
+      }
+      // park the state after every sub-iteration but the last in TMEM (restored if the
+      // rule stops the loop there)
+      if (u < D - 1) tmem_store32(taddr + (uint32_t)(u * T::SLOT_COLS), h);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ws.x += __shfl_xor_sync(0xffffffffu, ws.x, o);
+        ws.y += __shfl_xor_sync(0xffffffffu, ws.y, o);
+      }
+      if ((threadIdx.x & 31) == 0) s_w[u][warp] = ws;
+    }
+    {
+      // export band: the new state of the tile's D outer rows and columns, gathered from
+      // the last sub-iteration's post-collision populations (still in shared memory), one
+      // band slot per thread, coalesced
+      constexpr bool swl = ((D - 1) & 1) != 0;
+      float* exp_cur = exports + (size_t)(cyc & 1) * ntiles * pstride + (size_t)tile * pstride;
+      const int nslots = 2 * D * (tw + th) - 4 * D * D;
+      for (int sl = threadIdx.x; sl < nslots; sl += T::THREADS) {
+        int x, y;
+        band_coords_d<D>(sl, tw, th, x, y);
+        const int f = (y + D) * PX + x + D;
+        const bool b = k.walls && ty0 + y == 0, t = k.walls && ty0 + y == ny - 1;
+#pragma unroll
+        for (int i = 1; i < 9; ++i)
+          exp_cur[(i - 1) * T::PMAX + sl] = gather_d<T::PLANE, PX>(sm, i, f, b, t, vw_b, vw_t, swl);
+      }
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    // ---- grid barrier.  Warp 0 reduces the sub-iterations' warp sums (warps in a fixed
+    // order) and its lane 0 publishes them, then releases the CTA's band writes (ordered
+    // before it by the CTA barrier) and waits, within a time limit, for every tile. ----
+    __syncthreads();
+    target += ntiles;
+    if (threadIdx.x < 32) {
+      constexpr int nwarps = T::THREADS / 32;
+      const bool in = (int)threadIdx.x < nwarps;
+      float2 v[D];
+#pragma unroll
+      for (int u = 0; u < D; ++u) v[u] = in ? s_w[u][threadIdx.x] : make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int u = 0; u < D; ++u) {
+          v[u].x += __shfl_xor_sync(0xffffffffu, v[u].x, o);
+          v[u].y += __shfl_xor_sync(0xffffffffu, v[u].y, o);
+        }
+      }
+      if (threadIdx.x == 0) {
+        float4* pp = reinterpret_cast<float4*>(rpartials) +
+                     ((size_t)(cyc & 1) * ntiles + tile) * T::SUMS4;
+        pp[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        if constexpr (D == 3) pp[1] = make_float4(v[2].x, v[2].y, 0.0f, 0.0f);
+        int ok = 1;
+        red_release_add(&ctl->bar_count, 1u);
+        const unsigned long long t0 = global_ns();
+        while ((int)(ld_acquire(&ctl->bar_count) - target) < 0) {
+          if (global_ns() - t0 > BARRIER_TIMEOUT_NS) {
+            atomicOr(&ctl->bar_error, 1);
+            ok = 0;
+            break;
+          }
+        }
+        s_ok = ok;
+      }
+    }
+    __syncthreads();  // every tile's band and sums visible (or the wait gave up)
+    if (!s_ok) {
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_taddr),
+                     "n"(T::TCOLS)
+                     : "memory");
+      }
+      return;
+    }
+    ++cyc;
+  }
+  // the loop stopped after sub-iteration done - 1 of the previous cycle: before the last
+  // one, its state is in TMEM
+  if (done < D) tmem_load32(taddr + (uint32_t)((done - 1) * T::SLOT_COLS), h);
+
+  // the registers hold the final state: write it back in place
+#pragma unroll
+  for (int s = 0; s < NPT; ++s) {
+    if (!valid(s)) continue;
+    const int g = (ty0 + ly0 + s * T::ROWS) * nx + tx0 + lx;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) hsrc[i * N + g] = (s & 1) ? h[s >> 1][i].y : h[s >> 1][i].x;
+  }
+  if (tile == 0 && (int)threadIdx.x == dwarp * 32) {
+    ctl->iter = it;
+    ctl->rel = (double)rel;
+    ctl->converged = conv;
+    ctl->done = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_taddr),
+                 "n"(T::TCOLS)
+                 : "memory");
+  }
+}
+
+template <int TY>
+__global__ void __launch_bounds__(TileD<TY, 3>::THREADS, 1)
+    k_poisson_resident3(KParams k, ResidentGeom rg, float* __restrict__ hbuf,
+                        const float2* __restrict__ aq, float* __restrict__ exports,
+                        float2* __restrict__ rpartials, Ctl* ctl) {
+  resident_loopD<TY, 3>(k, rg, hbuf, aq, exports, rpartials, ctl, blockIdx.x, gridDim.x);
+}
+
+// The kernel of a tile height and sub-iterations per exchange (0: the one-step loop;
+// 2: heights 24 to 64; 3: heights 48 to 64), or nullptr.
+const void* resident_kernel(int ty, int depth) {
+  if (depth == 2) {
     switch (ty) {
       case 24: return (const void*)k_poisson_resident2<24>;
       case 32: return (const void*)k_poisson_resident2<32>;
@@ -1060,6 +1638,15 @@ const void* resident_kernel(int ty, bool two) {
       default: return nullptr;
     }
   }
+  if (depth == 3) {
+    switch (ty) {
+      case 48: return (const void*)k_poisson_resident3<48>;
+      case 56: return (const void*)k_poisson_resident3<56>;
+      case 64: return (const void*)k_poisson_resident3<64>;
+      default: return nullptr;
+    }
+  }
+  if (depth != 0) return nullptr;
   switch (ty) {
     case 8: return (const void*)k_poisson_resident<8>;
     case 16: return (const void*)k_poisson_resident<16>;
@@ -1082,13 +1669,15 @@ const void* resident_batch_kernel(int ty) {
 }
 
 // Tile geometry for the resident loop, or false if the lattice does not fit on chip with
-// one tile per SM.  Heights are rounded up to a multiple of 8.  two: the loop with two
-// sub-iterations per exchange, which needs heights of at least 24 and every tile at least
-// 4 x 4 (its export band is two nodes wide).
+// one tile per SM.  Heights are rounded up to a multiple of 8.  depth: sub-iterations per
+// exchange of the multi-step loop (0: the one-step loop), whose D-node-wide ring and band
+// need every tile at least 2 D x 2 D and heights of at least 24 (D = 2) or 48 (D = 3).
 bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* threads,
-                       size_t* smem, int fixed_ty, bool two) {
+                       size_t* smem, int fixed_ty, int depth) {
+  if (depth != 0 && depth != 2 && depth != 3) return false;
   const long long N = (long long)kp.nx * kp.ny;
   const int ntx = (kp.nx + TXR - 1) / TXR;
+  const int min_ty = depth == 3 ? 48 : (depth == 2 ? 24 : 8);
   int TY, nty;
   if (fixed_ty > 0) {
     // fixed 64 x fixed_ty tiles (autotuned schedules; batches: a simulation tiles the
@@ -1106,7 +1695,7 @@ bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* thr
     if (nty > num_sms / ntx) nty = num_sms / ntx;
     TY = (kp.ny + nty - 1) / nty;
     TY = (TY + 7) / 8 * 8;
-    if (two && TY < 24) TY = 24;
+    if (TY < min_ty) TY = min_ty;
     if (TY > 64) return false;
     nty = (kp.ny + TY - 1) / TY;
   }
@@ -1114,14 +1703,15 @@ bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* thr
   g->TY = TY;
   g->ntx = ntx;
   g->nty = nty;
-  g->two = two ? 1 : 0;
+  g->depth = depth;
   *threads = TXR * TY / NPT;
-  if (two) {
-    if (TY < 24 || kp.nx < 4 || kp.ny < 4 || kp.nx - (ntx - 1) * TXR < 4 ||
-        kp.ny - (nty - 1) * TY < 4)
+  if (depth != 0) {
+    const int D = depth, px = TXR + 2 * D;
+    if (TY < min_ty || kp.nx < 2 * D || kp.ny < 2 * D || kp.nx - (ntx - 1) * TXR < 2 * D ||
+        kp.ny - (nty - 1) * TY < 2 * D)
       return false;
-    g->pmax = 4 * TXR + 4 * TY;
-    *smem = sizeof(float) * (10 * (size_t)(TY + 4) * PXF + 8 * (size_t)(4 * PXF + 4 * TY));
+    g->pmax = 2 * D * TXR + 2 * D * TY;
+    *smem = sizeof(float) * (10 * (size_t)(TY + 2 * D) * px + 8 * (size_t)(2 * D * px + 2 * D * TY));
   } else {
     g->pmax = 2 * TXR + 2 * TY;
     *smem = sizeof(float) * (8 * (size_t)(TY + 2) * RX + 2 * (size_t)TY * TXR);
@@ -1131,7 +1721,7 @@ bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* thr
 
 cudaError_t launch_poisson_resident(const KParams& kp, const ResidentGeom& g, int threads,
                                     size_t smem, const Buffers& b, cudaStream_t st) {
-  const void* f = resident_kernel(g.TY, g.two != 0);
+  const void* f = resident_kernel(g.TY, g.depth);
   if (!f) return cudaErrorInvalidValue;
   KParams k = kp;
   ResidentGeom gg = g;
@@ -1148,7 +1738,7 @@ cudaError_t add_poisson_resident_node(cudaGraph_t graph, const cudaGraphNode_t* 
                                       cudaGraphNode_t* out, const KParams& kp,
                                       const ResidentGeom& g, int threads, size_t smem,
                                       const Buffers& b) {
-  const void* f = resident_kernel(g.TY, g.two != 0);
+  const void* f = resident_kernel(g.TY, g.depth);
   if (!f) return cudaErrorInvalidValue;
   KParams k = kp;
   ResidentGeom gg = g;

@@ -286,13 +286,13 @@ class Sim:
         _check(lib().ehd_diag_expire_barrier(self._h), "ehd_diag_expire_barrier")
 
     def loop_kind(self):
-        """1 streaming loop, 2 on-chip loop, 3 on-chip loop with two sub-iterations per
-        exchange."""
+        """1 streaming loop, 2 on-chip loop, 3 / 4 on-chip loop with two / three
+        sub-iterations per exchange."""
         return int(lib().ehd_loop_kind(self._h))
 
     def uses_resident_loop(self):
         """True when the potential loop runs on chip (one cooperative launch per solve)."""
-        return self.loop_kind() in (2, 3)
+        return self.loop_kind() in (2, 3, 4)
 
     def read_stats(self):
         st = Stats()

@@ -13,9 +13,11 @@ def test_candidates_cover_both_loops_and_fitting_tile_heights():
     res = [x["tile_rows"] for x in c if x["poisson_loop"] == 2]
     assert res == [0, 8, 16, 24]  # heights up to the first one covering all 20 rows
     assert [x["tile_rows"] for x in c if x["poisson_loop"] == 3] == [0, 24]
+    assert [x["tile_rows"] for x in c if x["poisson_loop"] == 4] == [0]
     c = autotune.candidates(wl.make_params(nx=512, ny=1024))
     assert [x["tile_rows"] for x in c if x["poisson_loop"] == 2] == [0, 8, 16, 24, 32, 40, 48, 56, 64]
     assert [x["tile_rows"] for x in c if x["poisson_loop"] == 3] == [0, 24, 32, 40, 48, 56, 64]
+    assert [x["tile_rows"] for x in c if x["poisson_loop"] == 4] == [0, 48, 56, 64]
 
 
 def test_pick_fastest_skips_failures_and_keeps_first_on_ties():

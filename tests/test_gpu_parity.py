@@ -20,7 +20,7 @@ GROUPS = {"phi": ("phi",), "q": ("q",), "varphi": ("varphi",), "E": ("Ex", "Ey")
 TOL_FIXED = 1e-5
 TOL_RULE = 1e-3
 LOOPS = [pytest.param(1, id="stream"), pytest.param(2, id="resident"),
-         pytest.param(3, id="resident2")]
+         pytest.param(3, id="resident2"), pytest.param(4, id="resident3")]
 
 
 @pytest.fixture(scope="module")
@@ -41,13 +41,13 @@ def rel(a, b):
 
 
 def run_pair(gpu, params, fields, steps, p0=None):
-    if params.get("poisson_loop") == 3:
-        # the two-step loop needs every tile at least 4 x 4; the library refuses others
+    if params.get("poisson_loop") in (3, 4):
+        # the D-step loops need every tile at least 2D x 2D; the library refuses others
         try:
             gpu.Sim(params).close()
         except gpu.EhdError as e:
             if e.code == 1:
-                pytest.skip("lattice has a tile narrower than 4 nodes (two-step loop)")
+                pytest.skip("lattice has a tile narrower than 2D nodes (D-step loop)")
             raise
     o = orc.Sim(params)
     o.set_fields(fields["phi"], fields["q"], fields["ux"], fields["uy"], p0)
@@ -258,14 +258,16 @@ def test_graph_and_host_loop_agree(gpu):
         assert np.array_equal(fa[k], fb[k]), k
 
 
-@pytest.mark.parametrize("fixed", [7, 8])
+@pytest.mark.parametrize("fixed", [7, 8, 9])
 def test_stream_and_resident_loops_bitwise(gpu, fixed):
-    """The streaming loop, the on-chip loop and the on-chip loop with two sub-iterations
-    per exchange do the same arithmetic per node: with a fixed sub-iteration count (odd:
-    the two-step loop restores its parked state; even: it does not) their states are
-    bitwise equal."""
+    """The streaming loop, the on-chip loop and the on-chip loops with two and three
+    sub-iterations per exchange do the same arithmetic per node: with a fixed
+    sub-iteration count their states are bitwise equal.  7, 8, 9 cover every way a
+    multi-step loop can end: the two-step loop restores its parked state at 7 and 9, not
+    at 8; the three-step loop restores the first parked state at 7, the second at 8, none
+    at 9."""
     out = []
-    for loop in (1, 2, 3):
+    for loop in (1, 2, 3, 4):
         p, f = droplet_box(150, 70, 14.0, seed=12, poisson_fixed_iter=fixed, poisson_loop=loop)
         g = gpu.Sim(p)
         g.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
@@ -273,17 +275,18 @@ def test_stream_and_resident_loops_bitwise(gpu, fixed):
         assert g.loop_kind() == loop
         out.append(g.read_fields())
     for k in FIELDS:
-        assert np.array_equal(out[0][k], out[1][k]), k
-        assert np.array_equal(out[1][k], out[2][k]), k
+        for o in out[1:]:
+            assert np.array_equal(out[0][k], o[k]), k
 
 
 @pytest.mark.parametrize("periodic", [False, True])
-def test_two_step_loop_matches_one_step_with_the_rule(gpu, periodic):
-    """With the paper's stopping rule the two on-chip loops take the same decisions (the
-    same FP32 sums in the same order): identical sub-iteration counts and states over 25
-    steps, on a ragged lattice with partial tiles, walled and periodic."""
+def test_multi_step_loops_match_one_step_with_the_rule(gpu, periodic):
+    """With the paper's stopping rule the on-chip loops with one, two and three
+    sub-iterations per exchange take the same decisions (the same FP32 sums in the same
+    order): identical sub-iteration counts and states over 25 steps, on a ragged lattice
+    with partial tiles, walled and periodic."""
     res = []
-    for loop in (2, 3):
+    for loop in (2, 3, 4):
         p, f = droplet_box(150, 70, 14.0, seed=13, poisson_loop=loop)
         if periodic:
             p["walls_y"], p["neutralize_charge"] = 0, 1
@@ -291,9 +294,10 @@ def test_two_step_loop_matches_one_step_with_the_rule(gpu, periodic):
         g.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
         ks = [g.step(1)["poisson_iters_total"] for _ in range(25)]
         res.append((ks, g.read_fields()))
-    assert res[0][0] == res[1][0]
-    for k in FIELDS:
-        assert np.array_equal(res[0][1][k], res[1][1][k]), k
+    for r in res[1:]:
+        assert res[0][0] == r[0]
+        for k in FIELDS:
+            assert np.array_equal(res[0][1][k], r[1][k]), k
 
 
 FP16_BAR = 5e-3
