@@ -34,6 +34,8 @@
 // limit is never reached in normal operation).
 #include "ehd_internal.cuh"
 
+#include <type_traits>
+
 namespace ehd {
 
 namespace {
@@ -58,28 +60,10 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   return v;
 }
 
-// Grid barrier for co-resident CTAs.  `target` counts the arrivals this CTA waits for;
-// returns false on timeout (error flag set).
-__device__ __forceinline__ bool grid_barrier(Ctl* sync, unsigned nblocks, unsigned& target) {
-  __shared__ int s_ok;
-  __syncthreads();  // the CTA's writes happen before thread 0's release
-  target += nblocks;
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    red_release_add(&sync->bar_count, 1u);
-    const unsigned long long t0 = global_ns();
-    while ((int)(ld_acquire(&sync->bar_count) - target) < 0) {
-      if (global_ns() - t0 > BARRIER_TIMEOUT_NS) {
-        atomicOr(&sync->bar_error, 1);
-        ok = 0;
-        break;
-      }
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
+// The grid barriers of the loops below (co-resident CTAs): after a CTA barrier, thread 0
+// adds one arrival with release semantics and polls the count with acquire loads until
+// it reaches `target` (the arrivals it waits for), within BARRIER_TIMEOUT_NS; a timeout
+// sets Ctl::bar_error and the CTA leaves its loop.
 
 __device__ __forceinline__ int perim_slot(int lx, int ly, int w, int h) {
   if (ly == 0) return lx;
@@ -119,7 +103,7 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
   using T = Tile<TY>;
   extern __shared__ float sm[];  // [8][RY][RX] populations, then [TY*64] a, [TY*64] q
   __shared__ float2 s_w[T::THREADS / 32];
-  __shared__ int s_done;
+  __shared__ int s_done, s_ok;
   __shared__ Nb s_nb[3][3];
 
   const int nx = k.nx, ny = k.ny;
@@ -207,7 +191,20 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
   float rel = 0.0f;
   int conv = 0;
   constexpr int dwarp = T::THREADS / 32 - 1;  // the warp that reduces the tiles' sums
-  for (;;) {
+  // One sub-iteration; returns 0 to go on, 1 when the rule stopped the loop at the previous
+  // one, 2 when the grid barrier timed out.  Sub-iterations alternate between two layouts
+  // of the shared populations (SW: sub-iteration it odd).  Own layout: direction i of the
+  // node at x sits in slot i of its own cell and streams from slot i of the cell x - c_i.
+  // Swapped layout: it goes to slot opp(i) of the cell x + c_i, and streams from slot
+  // opp(i) of the node's own cell.  A slot the collision of sub-iteration it + 1 writes was
+  // read in the streaming of sub-iteration it only by the writing thread itself, so no CTA
+  // barrier separates a streaming from the next collision.
+  auto sub_iteration = [&](auto swc) -> int {
+    constexpr bool SW = decltype(swc)::value;
+    // where direction i of the node at shared index f lies after the collision
+    auto slot = [](int i, int f) {
+      return SW ? (opp(i) - 1) * T::PLANE + f + cy(i) * RX + cx(i) : (i - 1) * T::PLANE + f;
+    };
     // 1. collide into the tile's shared populations; keep varphi^k per node
     float2 vold[2];
 #pragma unroll
@@ -223,8 +220,8 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
       h_star8x2(h[p], om, varphi, a, m1x, m1y, qs, hs);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        sm[i * T::PLANE + at0 + o0 * RX] = hs[i].x;
-        sm[i * T::PLANE + at0 + o1 * RX] = hs[i].y;
+        sm[slot(i + 1, at0) + o0 * RX] = hs[i].x;
+        sm[slot(i + 1, at0) + o1 * RX] = hs[i].y;
       }
     }
     __syncthreads();
@@ -240,11 +237,41 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
         else { ex = tw - 1; ey = sl - 2 * tw - th; }
         const int at = (ey + 1) * RX + ex + 1;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) exp_cur[i * T::PMAX + sl] = sm[i * T::PLANE + at];
+        for (int i = 1; i < 9; ++i) exp_cur[(i - 1) * T::PMAX + sl] = sm[slot(i, at)];
       }
     }
-    // 2. all tiles' exports (and the previous sub-iteration's partial sums) are visible
-    if (!grid_barrier(ctl, ntiles, target)) return;
+    // 2. grid barrier: warp 0 reduces the previous sub-iteration's warp sums (warps in a
+    // fixed order) and its lane 0 publishes them, then releases the CTA's exports (ordered
+    // before it by the CTA barrier) and waits, within a time limit, for every tile
+    __syncthreads();
+    target += ntiles;
+    if (threadIdx.x < 32) {
+      if (it > 0) {
+        constexpr int nwarps = T::THREADS / 32;
+        float2 v = (int)threadIdx.x < nwarps ? s_w[threadIdx.x] : make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+          v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+        }
+        if (threadIdx.x == 0) rpartials[(size_t)((it - 1) & 1) * ntiles + tile] = v;
+      }
+      if (threadIdx.x == 0) {
+        int ok = 1;
+        red_release_add(&ctl->bar_count, 1u);
+        const unsigned long long t0 = global_ns();
+        while ((int)(ld_acquire(&ctl->bar_count) - target) < 0) {
+          if (global_ns() - t0 > BARRIER_TIMEOUT_NS) {
+            atomicOr(&ctl->bar_error, 1);
+            ok = 0;
+            break;
+          }
+        }
+        s_ok = ok;
+      }
+    }
+    __syncthreads();  // every tile's exports and sums visible (or the wait gave up)
+    if (!s_ok) return 2;
     // 3. the deciding warp reduces the previous sub-iteration's sums (tiles in a fixed
     // order) and one lane applies the stopping rule, while the other warps fill the ring
     if (it > 0 && (int)(threadIdx.x >> 5) == dwarp) {
@@ -280,7 +307,7 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
       }
     }
     // 4a. ring: for every boundary node and direction whose source lies outside the tile,
-    // put the source value where the uniform gather will read it
+    // put the source value where the streaming will read it
     {
       const float* exp_all = exports + (size_t)(it & 1) * ntiles * pstride;
       const int nring = 6 * (tw + th);
@@ -311,23 +338,25 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
         const int nbx = sxl < 0 ? 0 : (sxl >= tw ? 2 : 1);
         const int nby = syl < 0 ? 0 : (syl >= th ? 2 : 1);
         const Nb nb = s_nb[nby][nbx];
+        const int bf = (by + 1) * RX + bx + 1;  // the consuming node's cell
         float v;
         if (nb.id < 0) {
-          // beyond a wall: anti-bounce-back on the consuming node's own population
+          // beyond a wall: anti-bounce-back on the consuming node's own population opp(i)
           const float vw = nby == 0 ? vw_b : vw_t;
-          v = h_wall(i, sm[(opp(i) - 1) * T::PLANE + (by + 1) * RX + bx + 1], vw);
+          v = h_wall(i, sm[slot(opp(i), bf)], vw);
         } else {
           const int olx = nbx == 0 ? nb.w - 1 : (nbx == 2 ? 0 : sxl);
           const int oly = nby == 0 ? nb.h - 1 : (nby == 2 ? 0 : syl);
           v = __ldcg(exp_all + (size_t)nb.id * pstride + (i - 1) * T::PMAX +
                      perim_slot(olx, oly, nb.w, nb.h));
         }
-        sm[(i - 1) * T::PLANE + (syl + 1) * RX + sxl + 1] = v;
+        // where the streaming of the consuming node reads direction i
+        sm[SW ? (opp(i) - 1) * T::PLANE + bf : (i - 1) * T::PLANE + (syl + 1) * RX + sxl + 1] = v;
       }
     }
     __syncthreads();
     // the registers still hold the state the decision was about
-    if (it > 0 && s_done) break;
+    if (it > 0 && s_done) return 1;
     // 4b. stream: every source is now in shared memory
     float num = 0.0f, den = 0.0f;
 #pragma unroll
@@ -335,7 +364,7 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
       const int o0 = 2 * p * T::ROWS, o1 = (2 * p + 1) * T::ROWS;
 #pragma unroll
       for (int i = 1; i < 9; ++i) {
-        const int off = (i - 1) * T::PLANE + at0 - cy(i) * RX - cx(i);
+        const int off = SW ? (opp(i) - 1) * T::PLANE + at0 : (i - 1) * T::PLANE + at0 - cy(i) * RX - cx(i);
         h[p][i - 1] = make_float2(sm[off + o0 * RX], sm[off + o1 * RX]);
       }
       const float2 d = __fadd2_rn(h_varphi2(h_sum8x2(h[p])), neg2(vold[p]));
@@ -353,19 +382,18 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
       num += __shfl_xor_sync(0xffffffffu, num, o);
       den += __shfl_xor_sync(0xffffffffu, den, o);
     }
+    // reduced by warp 0 inside the next grid barrier
     if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = make_float2(num, den);
-    __syncthreads();  // shared populations consumed; warp sums visible
-    if (threadIdx.x < 32) {
-      constexpr int nwarps = T::THREADS / 32;
-      float2 v = (int)threadIdx.x < nwarps ? s_w[threadIdx.x] : make_float2(0.0f, 0.0f);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-      }
-      if (threadIdx.x == 0) rpartials[(size_t)(it & 1) * ntiles + tile] = v;
-    }
     ++it;
+    return 0;
+  };
+  for (;;) {
+    int r = sub_iteration(std::false_type{});
+    if (r == 2) return;
+    if (r == 1) break;
+    r = sub_iteration(std::true_type{});
+    if (r == 2) return;
+    if (r == 1) break;
   }
 
   // the registers hold the final state: write it back in place
