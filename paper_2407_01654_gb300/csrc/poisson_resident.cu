@@ -439,10 +439,13 @@ __global__ void __launch_bounds__(Tile<TY>::THREADS, Tile<TY>::MIN_BLOCKS)
 // CTA advances its tile by two sub-iterations between grid barriers: it imports a
 // two-node-wide ring of its neighbours' post-stream state, collides tile and ring in the
 // first sub-iteration (streaming into the tile and the ring's inner layer), collides tile
-// and inner layer in the second, then exports its own two-node-wide band.  The stopping
-// rule is applied to both sub-iterations after the barrier, in order; when the first one
-// already ends the loop, the state it produced is restored from tensor memory (TMEM),
-// where every thread parks its four nodes' populations after the first sub-iteration.
+// and inner layer in the second (swapped layout, so no CTA barrier separates the first
+// streaming from the second collision), then exports its own two-node-wide band.  The
+// stopping rule is applied to both sub-iterations, in order, once every tile's sums are
+// in (after the next cycle's first collision, which is dropped if the loop stops); when
+// the first one already ends the loop, the state it produced is restored from tensor
+// memory (TMEM), where every thread parks its four nodes' populations after the first
+// sub-iteration.
 // Every CTA reaches the same decisions and each state is the one resident_loop produces,
 // bit for bit.  Half the grid barriers and halo round trips of resident_loop.
 // ---------------------------------------------------------------------------------------
