@@ -32,12 +32,15 @@ def run(ehd, p, f, steps):
     return st, out
 
 
-def test_barrier_timeout_is_reported_and_the_context_recovers(gpu):
-    p, f, _ = wl.droplet(N=96, r=15.0, R=3.0, S=0.5, Ca=0.2, poisson_fixed_iter=5)
+@pytest.mark.parametrize("loop", [2, 3, 4], ids=["one-step", "two-step", "three-step"])
+def test_barrier_timeout_is_reported_and_the_context_recovers(gpu, loop):
+    """Each on-chip loop has its own grid barrier; each gives up within the limit."""
+    p, f, _ = wl.droplet(N=96, r=15.0, R=3.0, S=0.5, Ca=0.2, poisson_fixed_iter=5,
+                         poisson_loop=loop)
     st0, ref = run(gpu, p, f, 6)
     assert st0["status"] == 0
     s = gpu.Sim(p)
-    assert s.uses_resident_loop()
+    assert s.loop_kind() == loop
     s.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
     s.step(2)
     s.diag_expire_barrier()
