@@ -467,17 +467,27 @@ __device__ __forceinline__ void coupled_body(const KParams& k, StepState* ss, in
   hist[5 * (size_t)N + idx] = Fy;
 }
 
-// 128 threads, at least 7 CTAs per SM (at most 72 registers): the pass is bound by
-// memory latency, and 7 resident CTAs run it 2.5 % faster than the 6 that 80 registers
-// allow (8 CTAs, 64 registers, spill and run slower).
+// 128 threads.  The FP32 form (specialised below): at least 7 CTAs per SM (at most
+// 72 registers); the pass is bound by memory latency, and 7 resident CTAs run it 2.5 %
+// faster than the 6 that 80 registers allow (8 CTAs at 64 registers spill more and run
+// slower).  The FP16-storage form keeps the registers it needs.
 template <bool HALF>
-__global__ void __launch_bounds__(128, 7) k_coupled(KParams k, StepState* ss, int cur, Pops pin,
+__global__ void __launch_bounds__(128) k_coupled(KParams k, StepState* ss, int cur, Pops pin,
                                                  Pops pout,
                                                  const float* __restrict__ phi_f,
                                                  const float* __restrict__ hbuf,
                                                  float* __restrict__ hist, const Ctl* ctl,
                                                  DevStats* stats) {
   coupled_body<HALF>(k, ss, cur, pin, pout, phi_f, hbuf, hist, ctl, stats, blockIdx.x);
+}
+template <>
+__global__ void __launch_bounds__(128, 7) k_coupled<false>(KParams k, StepState* ss, int cur,
+                                                           Pops pin, Pops pout,
+                                                           const float* __restrict__ phi_f,
+                                                           const float* __restrict__ hbuf,
+                                                           float* __restrict__ hist,
+                                                           const Ctl* ctl, DevStats* stats) {
+  coupled_body<false>(k, ss, cur, pin, pout, phi_f, hbuf, hist, ctl, stats, blockIdx.x);
 }
 
 // ------------------------------------------------------------------------------------
@@ -498,7 +508,7 @@ __global__ void __launch_bounds__(256) k_moments_batch(const StepSlot* __restric
                         S.tol, S.min_iter, S.max_iter, S.fixed_iter, w.y, S.mblocks);
 }
 
-__global__ void __launch_bounds__(128, 7) k_coupled_batch(const StepSlot* __restrict__ slots,
+__global__ void __launch_bounds__(128) k_coupled_batch(const StepSlot* __restrict__ slots,
                                                        const int2* __restrict__ work, int cur) {
   const int2 w = work[blockIdx.x];
   const StepSlot& S = slots[w.x];
