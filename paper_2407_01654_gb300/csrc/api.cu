@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/ehd.h"
@@ -311,6 +312,36 @@ void ensure_graphs(ehd_sim* s) {
 
 // Copies one input field into the staging area; returns its largest magnitude in *amax
 // (used to choose the FP16 storage scales).
+// dst[j][i] = (To)src[j][i] for j < nf, i < n: the conversions between the caller's
+// double arrays and the float32 staging buffers, split over up to 8 host threads when
+// there are at least 2^20 values in all (below that, starting threads costs more than
+// they save).
+template <typename To, typename From>
+void convert(To* const* dst, const From* const* src, int nf, size_t n) {
+  const size_t total = (size_t)nf * n;
+  const unsigned hw = std::thread::hardware_concurrency();
+  const size_t nt = total < ((size_t)1 << 20) ? 1 : (hw < 2 ? 1 : (hw < 8 ? hw : 8));
+  auto part = [&](size_t t) {
+    const size_t a = total * t / nt, b = total * (t + 1) / nt;
+    for (size_t k = a; k < b;) {  // flat index k = j n + i
+      const size_t j = k / n, i0 = k - j * n, i1 = (b - j * n < n) ? b - j * n : n;
+      To* d = dst[j];
+      const From* f = src[j];
+      for (size_t i = i0; i < i1; ++i) d[i] = (To)f[i];
+      k = j * n + i1;
+    }
+  };
+  if (nt == 1) {
+    part(0);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(nt - 1);
+  for (size_t t = 1; t < nt; ++t) th.emplace_back(part, t);
+  part(0);
+  for (auto& x : th) x.join();
+}
+
 int stage_in(ehd_sim* s, const void* src, int slot, int mem, double* amax) {
   const size_t N = (size_t)s->kp.N;
   float* dst = s->b.io + slot * N;
@@ -324,7 +355,7 @@ int stage_in(ehd_sim* s, const void* src, int slot, int mem, double* amax) {
     }
   } else {
     const double* d = static_cast<const double*>(src);
-    for (size_t i = 0; i < N; ++i) stage[i] = (float)d[i];
+    convert(&stage, &d, 1, N);
     EHD_CUDA(cudaMemcpyAsync(dst, stage, N * sizeof(float), cudaMemcpyHostToDevice,
                              s->stream));
   }
@@ -718,11 +749,13 @@ int ehd_read_fields(ehd_sim* s, unsigned mask, void* const* out, int mem) {
   }
   EHD_CUDA(cudaStreamSynchronize(s->stream));
   if (mem == EHD_HOST) {
+    double* dst[EHD_NUM_FIELDS];
+    const float* src[EHD_NUM_FIELDS];
     for (int j = 0; j < nf; ++j) {
-      double* d = static_cast<double*>(out[j]);
-      const float* f = s->h_stage + j * N;
-      for (size_t i = 0; i < N; ++i) d[i] = (double)f[i];
+      dst[j] = static_cast<double*>(out[j]);
+      src[j] = s->h_stage + j * N;
     }
+    convert(dst, src, nf, N);
   }
   return EHD_OK;
 }

@@ -158,30 +158,34 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
   // read by a lattice node or rewritten by the ring fill before it is.
   float2 h[2][8];
   bool valid[NPT];
+  float2 c4[NPT];
+  // every load is issued before any is used (a node outside the lattice loads node 0 of
+  // the lattice and then starts from zero)
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
     valid[s] = ly0 + s * T::ROWS < nrows;
-    float v[8];
-    float a = 0.0f, q = 0.0f;
-    if (valid[s]) {
-      const int g = (ty0 + ly0 + s * T::ROWS) * nx + tx0 + lx;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = hsrc[i * N + g];
-      const float2 c = aq[g];
-      a = c.x;
-      q = c.y - qshift;
-    } else {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = 0.0f;
-    }
-    ca[j0 + s * T::ROWS * TXR] = a;
-    cq[j0 + s * T::ROWS * TXR] = q;
+    const int g = valid[s] ? (ty0 + ly0 + s * T::ROWS) * nx + tx0 + lx : 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       if (s & 1)
-        h[s >> 1][i].y = v[i];
+        h[s >> 1][i].y = hsrc[i * N + g];
       else
-        h[s >> 1][i].x = v[i];
+        h[s >> 1][i].x = hsrc[i * N + g];
+    }
+    c4[s] = aq[g];
+  }
+#pragma unroll
+  for (int s = 0; s < NPT; ++s) {
+    ca[j0 + s * T::ROWS * TXR] = valid[s] ? c4[s].x : 0.0f;
+    cq[j0 + s * T::ROWS * TXR] = valid[s] ? c4[s].y - qshift : 0.0f;
+    if (!valid[s]) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (s & 1)
+          h[s >> 1][i].y = 0.0f;
+        else
+          h[s >> 1][i].x = 0.0f;
+      }
     }
   }
   __syncthreads();
