@@ -322,7 +322,10 @@ int ehd_batch_create(size_t hbm_budget, int max_slots, double steady_tol, int64_
                      void* arena, void* stream, ehd_batch** out);
 /* Admits a request (host double fields [ny][nx], as ehd_set_fields).  EHD_ERR_BUSY when no
  * slot, arena space or on-chip tile capacity is free; the batch is then unchanged.
- * EHD_ERR_INVALID_ARG for the conventional potential scheme (batches run the paper's). */
+ * EHD_ERR_INVALID_ARG for the conventional potential scheme (batches run the paper's) and
+ * for poisson_loop = EHD_LOOP_STREAM.  A batch runs every slot's potential loop on chip
+ * with one sub-iteration per exchange, whatever on-chip loop params asks for (every loop
+ * gives the same states); params' tile_rows is replaced by the batch's. */
 int ehd_batch_admit(ehd_batch* b, const ehd_params* params, const double* phi, const double* q,
                     const double* ux, const double* uy, int64_t request_id, int* slot);
 /* The batch's schedule (no counterpart in the paper; a launch choice): every slot's

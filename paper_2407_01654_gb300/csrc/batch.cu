@@ -396,6 +396,11 @@ int ehd_batch_admit(ehd_batch* b, const ehd_params* params, const double* phi, c
   if (params->nx < 1 || params->ny < 1) return EHD_ERR_INVALID_ARG;
   // batches run the on-chip loop, which implements the paper's scheme only
   if (params->potential_scheme != EHD_SCHEME_IMPROVED) return EHD_ERR_INVALID_ARG;
+  if (params->poisson_loop == EHD_LOOP_STREAM) return EHD_ERR_INVALID_ARG;
+  // the shared launch runs the one-step on-chip loop for every slot (the same states as
+  // the multi-step loops): the slot is laid out for it
+  ehd_params pslot = *params;
+  pslot.poisson_loop = EHD_LOOP_RESIDENT;
   int idx = -1;
   for (int i = 0; i < (int)b->slots.size(); ++i)
     if (!b->slots[i].live) {
@@ -407,13 +412,13 @@ int ehd_batch_admit(ehd_batch* b, const ehd_params* params, const double* phi, c
   if (b->tiles_used + ntiles > b->tile_capacity) return EHD_ERR_BUSY;
   const size_t N = (size_t)params->nx * params->ny;
   const int nblocks = (int)((N + STEADY_THREADS - 1) / STEADY_THREADS);
-  const size_t ws = al256(sim_workspace_bytes(params, b->rows));
+  const size_t ws = al256(sim_workspace_bytes(&pslot, b->rows));
   const size_t snap = al256(sizeof(float) * 3 * N);
   const size_t part = al256(sizeof(double) * 4 * (size_t)nblocks);
   size_t off;
   if (!arena_alloc(b, ws + snap + part, &off)) return EHD_ERR_BUSY;
   ehd_sim* s = nullptr;
-  int st = sim_create(params, b->arena + off, ws, b->stream, b->rows, &s);
+  int st = sim_create(&pslot, b->arena + off, ws, b->stream, b->rows, &s);
   if (st != EHD_OK) {
     arena_free(b, off);
     return st;

@@ -94,6 +94,29 @@ def test_admission_refusals_and_retire(gpu):
     assert sum(a is not None for a in admitted) == cap // 128
 
 
+def test_admission_normalises_the_potential_loop(gpu):
+    """A batch runs every slot's potential loop on chip with one sub-iteration per
+    exchange: requests asking for the two- or three-step loop are admitted (whatever the
+    batch's tile height) and compute the same fields; one asking for the streaming loop
+    is refused as an invalid argument, not as a full batch."""
+    p, f = request(96, 7, poisson_fixed_iter=4)
+    res = []
+    for loop in (2, 3, 4):
+        b = gpu.Batch(256 << 20, max_slots=2)
+        s = b.admit({**p, "poisson_loop": loop}, f, 0)
+        assert s is not None
+        b.run(30)
+        res.append(b.read_fields(s))
+    for r in res[1:]:
+        for k in FIELDS:
+            assert np.array_equal(r[k], res[0][k]), k
+    b = gpu.Batch(64 << 20, max_slots=2)
+    with pytest.raises(gpu.EhdError) as e:
+        b.admit({**p, "poisson_loop": 1}, f, 0)
+    assert e.value.code == 1
+    assert b.info()["live_slots"] == 0
+
+
 def test_step_cap_and_steadiness(gpu):
     """Status reporting: channel flow started at its steady profile is steady (relative
     change of u over a window well below 1e-3); a droplet request that is still moving is
