@@ -81,9 +81,9 @@ RECORDED_TRAFFIC = {
     # one potential solve of the two-step loop (280 sub-iterations on the captured step):
     # 21.023 MB read, 0.080 MB written
     "k_poisson_resident2": (21102848, "a51b04a5b7fd6260"),
-    # one coupled pass: 88.131 MB read, 20.670 MB written back during the launch (the
+    # one coupled pass: 88.137 MB read, 20.969 MB written back during the launch (the
     # rest of its writes leave L2 later)
-    "k_coupled": (108800512, "73074597b0d0bf80"),
+    "k_coupled": (109106688, "2f7b2e9f86a2c539"),
 }
 
 
