@@ -147,8 +147,8 @@ def test_full_size_sessile(gpu, loop):
                                          (3, 7, 1), (33, 17, 0), (31, 18, 1), (130, 3, 1)])
 def test_edge_sizes(gpu, nx, ny, walls, loop):
     """Degenerate and ragged lattices (single node, single row between walls, sizes not
-    multiples of the tile) match the oracle.  (The two-step loop needs tiles of at least
-    4 x 4 and the library refuses it for smaller lattices.)"""
+    multiples of the tile) match the oracle.  (The two- and three-step loops need tiles of
+    at least 4 x 4 and 6 x 6; the library refuses them for smaller lattices.)"""
     if loop == 3 and (nx < 4 or ny < 4):
         pytest.skip("two-step loop needs at least 4 x 4 tiles")
     p = wl.make_params(nx=nx, ny=ny, walls_y=walls, rho_l=2.0, rho_v=1.0, mu_l=0.1,
