@@ -123,13 +123,15 @@ typedef struct ehd_params {
                                    (as many per SM as fit), e.g. picked by an autotuner;
                                    other values: EHD_ERR_INVALID_ARG.  Results
                                    do not depend on the tiling at a fixed sub-iteration
-                                   count.  Batches always tile 64 x 32                    */
+                                   count.  A batch tiles every slot with its own height
+                                   (ehd_batch_set_schedule)                               */
   int32_t potential_scheme;     /* EHD_SCHEME_IMPROVED: the paper's potential LBE with the
                                    large-ratio forcing (Eq. weq53); EHD_SCHEME_CONVENTIONAL:
                                    the conventional scheme of Sec. 3.3 (no forcing,
                                    eps(phi) = chi c_s^2 (tau_varphi - 1/2)), kept as the
-                                   paper's comparison baseline; it always runs the
-                                   streaming loop                                         */
+                                   paper's comparison baseline; it runs on the streaming
+                                   loop and the one- and two-step on-chip loops
+                                   (EHD_LOOP_RESIDENT3 with it: EHD_ERR_INVALID_ARG)      */
   double chi;                   /* conventional scheme: the artificial factor chi > 0     */
   int32_t field_mode;           /* E used in hbar, F and R (and returned): 0 the local
                                    first moment of the converged h (Eq. eqA.16); 1 the

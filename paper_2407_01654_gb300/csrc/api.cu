@@ -491,20 +491,23 @@ int sim_create(const ehd_params* params, void* workspace, size_t workspace_bytes
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess &&
-        coop && L.export_floats && params->poisson_loop != EHD_LOOP_STREAM &&
-        params->potential_scheme == EHD_SCHEME_IMPROVED) {
+        coop && L.export_floats && params->poisson_loop != EHD_LOOP_STREAM) {
       const int use_sms = sms < DESIGN_SMS ? sms : DESIGN_SMS;
       ResidentGeom g;
       int th;
       size_t sm;
       const int depth = loop_depth(params->poisson_loop);
+      // the conventional scheme runs on the one- and two-step loops
+      const bool conv = params->potential_scheme == EHD_SCHEME_CONVENTIONAL;
+      const void* fk = nullptr;
       if (resident_geometry(s->kp, use_sms, &g, &th, &sm, fixed_ty, depth) &&
+          (fk = resident_kernel(g.TY, depth, conv)) != nullptr &&
           2 * (size_t)g.ntx * g.nty * 8 * g.pmax <= L.export_floats &&
           (size_t)g.ntx * g.nty <= L.rtiles &&
-          cudaFuncSetAttribute(resident_kernel(g.TY, depth), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)sm) == cudaSuccess) {
+          cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) ==
+              cudaSuccess) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, resident_kernel(g.TY, depth), th, sm) ==
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fk, th, sm) ==
                 cudaSuccess &&
             per_sm >= 1 && (long long)g.ntx * g.nty <= (long long)per_sm * sms) {
           s->resident_ok = true;

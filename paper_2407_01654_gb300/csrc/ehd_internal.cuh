@@ -314,6 +314,16 @@ __device__ __forceinline__ void h_star8x2(const float2 (&h)[8], float om, float2
     out[i - 1] = __fadd2_rn(v, qs);
   }
 }
+// h_star_conv on two nodes at once: om_x their 1 / tau_varphi, qs their q / (8 chi).
+__device__ __forceinline__ void h_star_conv8x2(const float2 (&h)[8], float2 om_x, float2 varphi,
+                                               float2 qs, float2 (&out)[8]) {
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    float2 v = __ffma2_rn(f2(-wgt(i)), varphi, h[i - 1]);
+    v = __ffma2_rn(neg2(om_x), v, h[i - 1]);
+    out[i - 1] = __fadd2_rn(v, qs);
+  }
+}
 
 // Stopping sums: (varphi^{k+1} - varphi^k)^2 and (varphi^k)^2 added to num, den.
 __device__ __forceinline__ void h_change(float vnew, float vold, float& num, float& den) {
@@ -394,7 +404,7 @@ bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* thr
                        size_t* smem, int fixed_ty = 0, int depth = 0);
 // The single-simulation kernel of a tile height (nullptr if none): heights 8..64 in
 // steps of 8; with two sub-iterations per exchange, 24..64.
-const void* resident_kernel(int tile_rows, int depth = 0);
+const void* resident_kernel(int tile_rows, int depth = 0, bool conv = false);
 const void* resident_batch_kernel(int tile_rows);  // 16, 32 or 64; else nullptr
 cudaError_t launch_poisson_resident(const KParams& kp, const ResidentGeom& g, int threads,
                                     size_t smem, const Buffers& b, cudaStream_t st);

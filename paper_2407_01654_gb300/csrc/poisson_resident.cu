@@ -93,7 +93,9 @@ struct Tile {
 }  // namespace
 
 // The loop for one tile of one simulation; `tile` of `ntiles` tiles of that simulation.
-template <int TY>
+// CONV: the conventional potential collision (Sec. 3.3; per-node 1 / tau_varphi in the
+// coefficient array, q / chi as the source) instead of the paper's.
+template <int TY, bool CONV>
 __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGeom& rg,
                                               float* __restrict__ hbuf,
                                               const float2* __restrict__ aq,
@@ -177,7 +179,8 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
     ca[j0 + s * T::ROWS * TXR] = valid[s] ? c4[s].x : 0.0f;
-    cq[j0 + s * T::ROWS * TXR] = valid[s] ? c4[s].y - qshift : 0.0f;
+    const float qn = __fsub_rn(c4[s].y, qshift);
+    cq[j0 + s * T::ROWS * TXR] = valid[s] ? (CONV ? __fmul_rn(qn, k.inv_chi) : qn) : 0.0f;
     if (!valid[s]) {
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
@@ -221,7 +224,10 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
       const float2 a = make_float2(ca[j0 + o0 * TXR], ca[j0 + o1 * TXR]);
       const float2 qs = __fmul2_rn(f2(0.125f), make_float2(cq[j0 + o0 * TXR], cq[j0 + o1 * TXR]));
       float2 hs[8];
-      h_star8x2(h[p], om, varphi, a, m1x, m1y, qs, hs);
+      if constexpr (CONV)
+        h_star_conv8x2(h[p], a, varphi, qs, hs);
+      else
+        h_star8x2(h[p], om, varphi, a, m1x, m1y, qs, hs);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         sm[slot(i + 1, at0) + o0 * RX] = hs[i].x;
@@ -416,12 +422,12 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
   }
 }
 
-template <int TY>
+template <int TY, bool CONV>
 __global__ void __launch_bounds__(Tile<TY>::THREADS, Tile<TY>::MIN_BLOCKS)
     k_poisson_resident(KParams k, ResidentGeom rg, float* __restrict__ hbuf,
                        const float2* __restrict__ aq, float* __restrict__ exports,
                        float2* __restrict__ rpartials, Ctl* ctl) {
-  resident_loop<TY>(k, rg, hbuf, aq, exports, rpartials, ctl, blockIdx.x, gridDim.x);
+  resident_loop<TY, CONV>(k, rg, hbuf, aq, exports, rpartials, ctl, blockIdx.x, gridDim.x);
 }
 
 // Several simulations in one cooperative launch, all tiled 64 x TY: CTA b runs tile
@@ -434,7 +440,7 @@ __global__ void __launch_bounds__(Tile<TY>::THREADS, Tile<TY>::MIN_BLOCKS)
                              const int2* __restrict__ work) {
   const int2 w = work[blockIdx.x];
   const ResidentSlot& S = slots[w.x];
-  resident_loop<TY>(S.k, S.rg, S.h, S.aq, S.exports, S.rpartials, S.ctl, w.y,
+  resident_loop<TY, false>(S.k, S.rg, S.h, S.aq, S.exports, S.rpartials, S.ctl, w.y,
                     S.rg.ntx * S.rg.nty);
 }
 
@@ -604,7 +610,7 @@ __device__ __forceinline__ float gather_swapped(const float* sm, int i, int f, b
 
 }  // namespace
 
-template <int TY>
+template <int TY, bool CONV>
 __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentGeom& rg,
                                                float* __restrict__ hbuf,
                                                const float2* __restrict__ aq,
@@ -711,7 +717,8 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       for (int i = 0; i < 8; ++i) ring[i * T::NR + threadIdx.x] = hsrc[i * N + g];
       const float2 c = aq[g];
       ca[rf] = c.x;
-      cq[rf] = c.y - qshift;
+      const float qn = __fsub_rn(c.y, qshift);
+      cq[rf] = CONV ? __fmul_rn(qn, k.inv_chi) : qn;
     }
   }
 
@@ -734,7 +741,8 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       for (int i = 0; i < 8; ++i) v[i] = hsrc[i * N + g];
       const float2 c = aq[g];
       a = c.x;
-      q = c.y - qshift;
+      q = __fsub_rn(c.y, qshift);
+      if (CONV) q = __fmul_rn(q, k.inv_chi);
     } else {
 #pragma unroll
       for (int i = 0; i < 8; ++i) v[i] = 0.0f;
@@ -791,7 +799,10 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       const float2 a = make_float2(ca[at0 + o0], ca[at0 + o1]);
       const float2 qs = __fmul2_rn(f2(0.125f), make_float2(cq[at0 + o0], cq[at0 + o1]));
       float2 hs[8];
-      h_star8x2(h[p], om, varphi, a, m1x, m1y, qs, hs);
+      if constexpr (CONV)
+        h_star_conv8x2(h[p], a, varphi, qs, hs);
+      else
+        h_star8x2(h[p], om, varphi, a, m1x, m1y, qs, hs);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         if (valid(2 * p)) sm[i * T::PLANE + at0 + o0] = hs[i].x;
@@ -866,7 +877,8 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       const float a = ca[rf];
 #pragma unroll
       for (int i = 1; i < 9; ++i)
-        sm[(i - 1) * T::PLANE + rf] = h_star(i, hr[i - 1], om, varphi, a, m1x, m1y, qs);
+        sm[(i - 1) * T::PLANE + rf] = CONV ? h_star_conv(i, hr[i - 1], a, varphi, qs)
+                                           : h_star(i, hr[i - 1], om, varphi, a, m1x, m1y, qs);
     }
     __syncthreads();  // post-collision populations and the rule's verdict visible
     done = s_done;
@@ -926,7 +938,10 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       const float2 a = make_float2(ca[at0 + o0], ca[at0 + o1]);
       const float2 qs = __fmul2_rn(f2(0.125f), make_float2(cq[at0 + o0], cq[at0 + o1]));
       float2 hs[8];
-      h_star8x2(h[p], om, varphi, a, m1x, m1y, qs, hs);
+      if constexpr (CONV)
+        h_star_conv8x2(h[p], a, varphi, qs, hs);
+      else
+        h_star8x2(h[p], om, varphi, a, m1x, m1y, qs, hs);
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int sw = (opp(i + 1) - 1) * T::PLANE + cy(i + 1) * PXF + cx(i + 1);
@@ -946,7 +961,8 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
 #pragma unroll
       for (int i = 1; i < 9; ++i)
         sm[(opp(i) - 1) * T::PLANE + cy(i) * PXF + cx(i) + rf] =
-            h_star(i, hr[i - 1], om, varphi, a, m1x, m1y, qs);
+            CONV ? h_star_conv(i, hr[i - 1], a, varphi, qs)
+                 : h_star(i, hr[i - 1], om, varphi, a, m1x, m1y, qs);
     }
     __syncthreads();
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -1073,12 +1089,12 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
   }
 }
 
-template <int TY>
+template <int TY, bool CONV>
 __global__ void __launch_bounds__(Tile2<TY>::THREADS, 1)
     k_poisson_resident2(KParams k, ResidentGeom rg, float* __restrict__ hbuf,
                         const float2* __restrict__ aq, float* __restrict__ exports,
                         float2* __restrict__ rpartials, Ctl* ctl) {
-  resident_loop2<TY>(k, rg, hbuf, aq, exports, rpartials, ctl, blockIdx.x, gridDim.x);
+  resident_loop2<TY, CONV>(k, rg, hbuf, aq, exports, rpartials, ctl, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1659,21 +1675,24 @@ __global__ void __launch_bounds__(TileD<TY, 3>::THREADS, 1)
   resident_loopD<TY, 3>(k, rg, hbuf, aq, exports, rpartials, ctl, blockIdx.x, gridDim.x);
 }
 
-// The kernel of a tile height and sub-iterations per exchange (0: the one-step loop;
-// 2: heights 24 to 64; 3: heights 48 to 64), or nullptr.
-const void* resident_kernel(int ty, int depth) {
+// The kernel of a tile height, sub-iterations per exchange (0: the one-step loop;
+// 2: heights 24 to 64; 3: heights 48 to 64) and potential scheme (conv: the conventional
+// one, on the one- and two-step loops), or nullptr.
+template <bool CONV>
+const void* resident_kernel_of(int ty, int depth) {
   if (depth == 2) {
     switch (ty) {
-      case 24: return (const void*)k_poisson_resident2<24>;
-      case 32: return (const void*)k_poisson_resident2<32>;
-      case 40: return (const void*)k_poisson_resident2<40>;
-      case 48: return (const void*)k_poisson_resident2<48>;
-      case 56: return (const void*)k_poisson_resident2<56>;
-      case 64: return (const void*)k_poisson_resident2<64>;
+      case 24: return (const void*)k_poisson_resident2<24, CONV>;
+      case 32: return (const void*)k_poisson_resident2<32, CONV>;
+      case 40: return (const void*)k_poisson_resident2<40, CONV>;
+      case 48: return (const void*)k_poisson_resident2<48, CONV>;
+      case 56: return (const void*)k_poisson_resident2<56, CONV>;
+      case 64: return (const void*)k_poisson_resident2<64, CONV>;
       default: return nullptr;
     }
   }
   if (depth == 3) {
+    if (CONV) return nullptr;
     switch (ty) {
       case 48: return (const void*)k_poisson_resident3<48>;
       case 56: return (const void*)k_poisson_resident3<56>;
@@ -1683,16 +1702,19 @@ const void* resident_kernel(int ty, int depth) {
   }
   if (depth != 0) return nullptr;
   switch (ty) {
-    case 8: return (const void*)k_poisson_resident<8>;
-    case 16: return (const void*)k_poisson_resident<16>;
-    case 24: return (const void*)k_poisson_resident<24>;
-    case 32: return (const void*)k_poisson_resident<32>;
-    case 40: return (const void*)k_poisson_resident<40>;
-    case 48: return (const void*)k_poisson_resident<48>;
-    case 56: return (const void*)k_poisson_resident<56>;
-    case 64: return (const void*)k_poisson_resident<64>;
+    case 8: return (const void*)k_poisson_resident<8, CONV>;
+    case 16: return (const void*)k_poisson_resident<16, CONV>;
+    case 24: return (const void*)k_poisson_resident<24, CONV>;
+    case 32: return (const void*)k_poisson_resident<32, CONV>;
+    case 40: return (const void*)k_poisson_resident<40, CONV>;
+    case 48: return (const void*)k_poisson_resident<48, CONV>;
+    case 56: return (const void*)k_poisson_resident<56, CONV>;
+    case 64: return (const void*)k_poisson_resident<64, CONV>;
     default: return nullptr;
   }
+}
+const void* resident_kernel(int ty, int depth, bool conv) {
+  return conv ? resident_kernel_of<true>(ty, depth) : resident_kernel_of<false>(ty, depth);
 }
 const void* resident_batch_kernel(int ty) {
   switch (ty) {
@@ -1756,7 +1778,7 @@ bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* thr
 
 cudaError_t launch_poisson_resident(const KParams& kp, const ResidentGeom& g, int threads,
                                     size_t smem, const Buffers& b, cudaStream_t st) {
-  const void* f = resident_kernel(g.TY, g.depth);
+  const void* f = resident_kernel(g.TY, g.depth, kp.scheme == 1);
   if (!f) return cudaErrorInvalidValue;
   KParams k = kp;
   ResidentGeom gg = g;
@@ -1773,7 +1795,7 @@ cudaError_t add_poisson_resident_node(cudaGraph_t graph, const cudaGraphNode_t* 
                                       cudaGraphNode_t* out, const KParams& kp,
                                       const ResidentGeom& g, int threads, size_t smem,
                                       const Buffers& b) {
-  const void* f = resident_kernel(g.TY, g.depth);
+  const void* f = resident_kernel(g.TY, g.depth, kp.scheme == 1);
   if (!f) return cudaErrorInvalidValue;
   KParams k = kp;
   ResidentGeom gg = g;

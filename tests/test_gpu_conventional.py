@@ -8,18 +8,49 @@ import pytest
 import analytic as an
 from oracle import ehd as orc
 from paper_2407_01654_gb300 import workloads as wl
-from test_gpu_parity import TOL_FIXED, TOL_RULE, assert_fields, droplet_box, gpu, run_pair  # noqa: F401
+from test_gpu_parity import (FIELDS, TOL_FIXED, TOL_RULE, assert_fields, droplet_box,  # noqa: F401
+                             gpu, run_pair)
 
 pytestmark = pytest.mark.gpu
 
 
-def test_droplet_fixed_k(gpu):
+@pytest.mark.parametrize("loop", [1, 2, 3], ids=["stream", "resident", "resident2"])
+def test_droplet_fixed_k(gpu, loop):
     """Ragged 70 x 45 droplet in a field, chi = 2, 100 steps of 4 sub-iterations: every
-    field within 1e-5 of the oracle; the library runs the streaming loop."""
-    p, f = droplet_box(70, 45, 11.0, seed=2, poisson_fixed_iter=4, potential_scheme=1, chi=2.0)
+    field within 1e-5 of the oracle, on the streaming loop and on the one- and two-step
+    on-chip loops."""
+    p, f = droplet_box(70, 45, 11.0, seed=2, poisson_fixed_iter=4, potential_scheme=1, chi=2.0,
+                       poisson_loop=loop)
     o, g, fo, fg, so, sg = run_pair(gpu, p, f, 100)
     assert_fields(fo, fg, TOL_FIXED)
-    assert not g.uses_resident_loop() and sg["status"] == 0
+    assert g.loop_kind() == loop and sg["status"] == 0
+
+
+def test_loops_compute_the_same_bits(gpu):
+    """The conventional collision in the streaming loop and in the one- and two-step
+    on-chip loops is the same arithmetic: at a fixed K of 7 (the two-step loop restores
+    its parked state) the states after 12 steps on a ragged lattice are bitwise equal."""
+    out = []
+    for loop in (1, 2, 3):
+        p, f = droplet_box(150, 70, 14.0, seed=12, poisson_fixed_iter=7, potential_scheme=1,
+                           chi=3.0, poisson_loop=loop)
+        g = gpu.Sim(p)
+        g.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
+        g.step(12)
+        assert g.loop_kind() == loop
+        out.append(g.read_fields())
+    for k in FIELDS:
+        for o in out[1:]:
+            assert np.array_equal(out[0][k], o[k]), k
+
+
+def test_three_step_loop_refuses_the_conventional_scheme(gpu):
+    """The three-step loop implements the paper's scheme only: asking for it with the
+    conventional scheme is an invalid argument."""
+    p, _ = droplet_box(150, 70, 14.0, seed=12, potential_scheme=1, chi=3.0, poisson_loop=4)
+    with pytest.raises(gpu.EhdError) as e:
+        gpu.Sim(p)
+    assert e.value.code == 1
 
 
 def test_sessile_rule(gpu):
