@@ -80,7 +80,7 @@ KERNEL_FILES = {
 RECORDED_TRAFFIC = {
     # one potential solve of the two-step loop (280 sub-iterations on the captured step):
     # 21.030 MB read, 0.076 MB written
-    "k_poisson_resident2": (21106176, "9941e3293935289a"),
+    "k_poisson_resident2": (21106176, "419d0b415696813c"),
     # one coupled pass: 88.137 MB read, 20.969 MB written back during the launch (the
     # rest of its writes leave L2 later)
     "k_coupled": (109106688, "2f7b2e9f86a2c539"),

@@ -119,7 +119,8 @@ typedef struct ehd_params {
   int64_t start_step;           /* step counter after ehd_set_fields                      */
   int32_t tile_rows;            /* resident potential loop: 0 = tiles chosen from the
                                    lattice size (about 2048 nodes each, at most one per
-                                   SM); 8, 16, ..., 64 = tiles of 64 x tile_rows nodes
+                                   SM, enough rows of tiles for tiles of at most 64 rows);
+                                   8, 16, ..., 64 = tiles of 64 x tile_rows nodes
                                    (as many per SM as fit), e.g. picked by an autotuner;
                                    other values: EHD_ERR_INVALID_ARG.  Results
                                    do not depend on the tiling at a fixed sub-iteration

@@ -1753,7 +1753,15 @@ bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* thr
     TY = (kp.ny + nty - 1) / nty;
     TY = (TY + 7) / 8 * 8;
     if (TY < min_ty) TY = min_ty;
-    if (TY > 64) return false;
+    if (TY > 64) {
+      // a narrow, tall lattice: as many rows of tiles as 64-row tiles need
+      nty = (kp.ny + 63) / 64;
+      if (nty > num_sms / ntx) return false;
+      TY = (kp.ny + nty - 1) / nty;
+      TY = (TY + 7) / 8 * 8;
+      if (TY < min_ty) TY = min_ty;
+      if (TY > 64) return false;
+    }
     nty = (kp.ny + TY - 1) / TY;
   }
   g->TX = TXR;
