@@ -83,7 +83,7 @@ RECORDED_TRAFFIC = {
     "k_poisson_resident2": (21106176, "419d0b415696813c"),
     # one coupled pass: 88.137 MB read, 20.969 MB written back during the launch (the
     # rest of its writes leave L2 later)
-    "k_coupled": (109106688, "2f7b2e9f86a2c539"),
+    "k_coupled": (109106688, "3bcd59efcd78de5f"),
 }
 
 
