@@ -76,3 +76,26 @@ def test_create_rejects_bad_parameters(L, change, code):
     h = ctypes.c_void_p()
     assert L.ehd_create(ctypes.byref(p), None, 0, None, ctypes.byref(h)) == code
     assert not h.value
+
+
+def workspace(L, **kw):
+    p = ehd.Params.from_dict(wl.make_params(**kw))
+    nb = ctypes.c_size_t()
+    assert L.ehd_workspace_bytes(ctypes.byref(p), ctypes.byref(nb)) == 0
+    return nb.value
+
+
+def test_workspace_holds_the_export_bands_of_each_on_chip_loop(L):
+    """Host geometry (no GPU): the workspace reserves, per tile and per copy of the
+    double buffer, 8 directions of the export band of the on-chip loop asked for — one,
+    two or three nodes wide (2, 4, 6 x (64 + TY) slots).  At 512 x 1024 the tiles are
+    8 x 19 of 64 x 56; a narrow, tall 4 x 256 lattice gets 4 tiles of 4 x 64; a lattice
+    too large for the chip gets none, whatever the loop."""
+    w = {loop: workspace(L, nx=512, ny=1024, poisson_loop=loop) for loop in (2, 3, 4)}
+    band = 2 * 152 * 8 * 4  # bytes per band slot over all tiles and both copies
+    assert w[3] - w[2] == band * (4 - 2) * (64 + 56)
+    assert w[4] - w[3] == band * (6 - 4) * (64 + 56)
+    t = {loop: workspace(L, nx=4, ny=256, poisson_loop=loop) for loop in (2, 3)}
+    assert t[3] - t[2] == 2 * 4 * 8 * 4 * (4 - 2) * (64 + 64)
+    big = {loop: workspace(L, nx=1024, ny=1024, poisson_loop=loop) for loop in (2, 3, 4)}
+    assert big[2] == big[3] == big[4]
