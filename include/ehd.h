@@ -72,9 +72,12 @@ enum {
   EHD_F_EY = 1u << 4,
   EHD_F_UX = 1u << 5,      /* velocity, rho u = sum c f + F/2 (Eq. weq43)                */
   EHD_F_UY = 1u << 6,
-  EHD_F_P = 1u << 7        /* hydrodynamic pressure (Eq. eq32)                            */
+  EHD_F_P = 1u << 7,       /* hydrodynamic pressure (Eq. eq32)                            */
+  EHD_F_MU = 1u << 8       /* chemical potential hbar (Eq. weq31) of the current phi (its
+                              Laplacian with the current wall rule) and the field E that
+                              EX / EY return (that of the last potential solve)           */
 };
-#define EHD_NUM_FIELDS 8
+#define EHD_NUM_FIELDS 9
 
 /* Potential LBE schemes (ehd_params.potential_scheme). */
 enum { EHD_SCHEME_IMPROVED = 0, EHD_SCHEME_CONVENTIONAL = 1 };
@@ -222,8 +225,9 @@ int ehd_solve_potential(ehd_sim* sim, double tol, int max_iter, int* iters,
 /* Macroscopic fields of the current state.  For each bit set in `mask`, in bit order,
  * the next pointer of `out` receives a [ny][nx] array.  PHI, Q, UX, UY and P are those of
  * the current populations; VARPHI, EX and EY those of the last potential solve (which,
- * after a step, used that step's phi and q).  mem: EHD_HOST (double) or EHD_DEVICE
- * (float32). */
+ * after a step, used that step's phi and q); MU combines the two (current phi, last
+ * solve's E).  mem: EHD_HOST (double) or EHD_DEVICE (float32).
+ * Errors: EHD_ERR_INVALID_ARG (null pointer, a bit beyond EHD_F_MU, bad mem). */
 int ehd_read_fields(ehd_sim* sim, unsigned mask, void* const* out, int mem);
 
 /* Complete state (populations, potential distribution, lagged quantities, step counter)
@@ -257,8 +261,9 @@ int ehd_profile_read(ehd_sim* sim, ehd_kernel_times* out);
  *   h_work   device float32 [8][ny][nx], overwritten (the loop alternates between the two);
  *   stream   cudaStream_t (NULL: default stream); the call synchronises it.
  * Its only scratch (per-CTA FP64 partial sums and the loop control) is a fixed device
- * array inside the library: lattices of at most 2,097,152 nodes (4096 tiles of 32 x 16)
- * are accepted, larger ones return EHD_ERR_TOO_LARGE.  The first call on each device
+ * array inside the library: a lattice is accepted when its tiling into 32 x 16 tiles has
+ * at most 4096 tiles, ceil(nx / 32) * ceil(ny / 16) <= 4096 (at most 2,097,152 nodes);
+ * other lattices return EHD_ERR_TOO_LARGE before any work is queued.  The first call on each device
  * looks the array up (with that device current) and should come before any stream
  * capture.  All calls share the array: calls that overlap on the GPU race and must be
  * serialised by the caller.  No cudaMalloc, cudaFree or other allocating routine is

@@ -569,7 +569,7 @@ def poisson_solve(P, h, phi, q, varphi_w, tol=None, max_iter=None, fixed_iter=No
 # ---------------------------------------------------------------------------------
 
 
-FIELD_NAMES = ("phi", "q", "varphi", "Ex", "Ey", "ux", "uy", "p")
+FIELD_NAMES = ("phi", "q", "varphi", "Ex", "Ey", "ux", "uy", "p", "mu")
 
 
 @dataclass
@@ -785,6 +785,9 @@ class Sim:
         phi, q, ux, uy, p are those of the current populations (level n); varphi, Ex,
         Ey are those of the last potential solve, which used phi^{n-1}, q^{n-1} after a
         step (Algorithm 1 solves the potential at the start of each step).
+        reading: mu, the chemical potential hbar of Eq. weq31 for output, takes the
+        current phi (its Laplacian with the current wall rule) and the field Ex, Ey
+        returned here (the last solve's); at a steady state the two levels coincide.
         """
         P = self.P
         phi, q, rho, ux, uy = self._moments()
@@ -794,5 +797,6 @@ class Sim:
         p = self._pressure(phi, rho, ux, uy, gx, gy)
         varphi = varphi_of(self.h)
         Ex, Ey = electric_field(P, self.h, self.phi_poisson, self.vw_poisson)
+        mu = chemical_potential(P, phi, laplacian(ext), Ex, Ey)
         return {"phi": phi, "q": q, "varphi": varphi, "Ex": Ex, "Ey": Ey,
-                "ux": ux, "uy": uy, "p": p}
+                "ux": ux, "uy": uy, "p": p, "mu": mu}

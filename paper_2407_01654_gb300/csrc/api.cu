@@ -84,8 +84,13 @@ Layout layout_for(const ehd_params& P, int fixed_ty = 0) {
 bool sizes_ok(const ehd_params* p) {
   if (p->nx < 1 || p->ny < 1) return false;
   const int64_t N = (int64_t)p->nx * p->ny;
-  // the one-pass reductions hold one partial per CTA
+  // the one-pass reductions hold one partial per CTA: the moments pass (at most one per
+  // 256 nodes) and the streaming potential kernel (one per 64 x 16 tile, which for narrow
+  // lattices is far more than N / 256)
   if ((N + 255) / 256 > MAX_PARTIALS) return false;
+  if (stream_tiles(p->nx, p->ny) > MAX_PARTIALS) return false;
+  // the kernels index nodes with 32-bit integers
+  if (N > 0x7fffffffLL) return false;
   return true;
 }
 
@@ -507,9 +512,15 @@ int sim_create(const ehd_params* params, void* workspace, size_t workspace_bytes
           cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) ==
               cudaSuccess) {
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fk, th, sm) ==
-                cudaSuccess &&
-            per_sm >= 1 && (long long)g.ntx * g.nty <= (long long)per_sm * sms) {
+        // the multi-step loops hold tensor memory for the whole launch: CTAs that share
+        // an SM must fit its 512 columns together, or a CTA would wait in tcgen05.alloc
+        // for one that only leaves at the end of the loop
+        const int tcols = resident_tmem_columns(g.TY, depth);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fk, th, sm) != cudaSuccess)
+          per_sm = 0;
+        if (tcols < 0) per_sm = 0;
+        if (tcols > 0 && per_sm > 512 / tcols) per_sm = 512 / tcols;
+        if (per_sm >= 1 && (long long)g.ntx * g.nty <= (long long)per_sm * sms) {
           s->resident_ok = true;
           s->rg = g;
           s->rthreads = th;
@@ -731,7 +742,8 @@ int ehd_read_stats(ehd_sim* s, ehd_stats* out) {
 }
 
 int ehd_read_fields(ehd_sim* s, unsigned mask, void* const* out, int mem) {
-  if (!s || !out || (mem != EHD_HOST && mem != EHD_DEVICE) || (mask & ~0xffu)) return EHD_ERR_INVALID_ARG;
+  if (!s || !out || (mem != EHD_HOST && mem != EHD_DEVICE) || (mask & ~((1u << EHD_NUM_FIELDS) - 1u)))
+    return EHD_ERR_INVALID_ARG;
   if (!mask) return EHD_OK;
   int nf = 0;
   for (int b = 0; b < EHD_NUM_FIELDS; ++b)
@@ -864,6 +876,8 @@ int ehd_load_state(ehd_sim* s, const void* buf, size_t bytes) {
   p += sizeof(float) * NHIST * N;
   EHD_CUDA(cudaMemcpyAsync(s->b.phi, p, sizeof(float) * N, cudaMemcpyHostToDevice, s->stream));
   EHD_CUDA(cudaMemsetAsync(&s->b.ctl->parity, 0, sizeof(int), s->stream));
+  // the restored state is judged on its own: a non-finite flag of the replaced one goes
+  EHD_CUDA(cudaMemsetAsync(&s->b.ctl->nonfinite, 0, sizeof(int), s->stream));
   s->n = hd.n;
   s->history_valid = hd.history_valid != 0;
   s->last_k = hd.last_k;

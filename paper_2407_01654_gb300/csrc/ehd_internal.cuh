@@ -17,7 +17,7 @@
 //   aq[N]           float2 per node: (a, q) with a = eps_hat / (c_s^2 tau_h (eps_hat +
 //                   c_s^2 tau_h)), the coefficient of the potential forcing once
 //                   grad varphi is written with the local first moment (Eq. eqA.16);
-//   io[8][N]        staging area for field input / output;
+//   io[9][N]        staging area for field input / output;
 //   partials[]      per-CTA FP64 partial sums;
 //   ctl, stats      loop control and statistics (device structs below).
 #pragma once
@@ -32,8 +32,14 @@ constexpr int Q9 = 9;
 constexpr int NPOP = 27;   // g, l, f
 constexpr int NH = 8;      // h_1..h_8
 constexpr int NHIST = 8;
-constexpr int NIO = 8;
+constexpr int NIO = 9;   // field staging slots: one per ehd_read_fields bit
 constexpr int MAX_PARTIALS = 1 << 16;
+// Tiles of the streaming potential kernel (one CTA and one FP64 partial pair each).
+constexpr int STREAM_TX = 64;
+constexpr int STREAM_TY = 16;
+__host__ __device__ constexpr long long stream_tiles(int nx, int ny) {
+  return (long long)((nx + STREAM_TX - 1) / STREAM_TX) * ((ny + STREAM_TY - 1) / STREAM_TY);
+}
 // The moments pass runs at most this many CTAs of 256 threads (one wave on the GPU), each
 // thread striding over the lattice, so the per-CTA reduction tails overlap.
 constexpr int MOMENTS_MAX_BLOCKS = 1216;
@@ -344,7 +350,7 @@ struct Buffers {
   float* hist;       // [6][N]
   float* phi;        // [N]
   float2* aq;        // [N]
-  float* io;         // [8][N]
+  float* io;         // [9][N]
   float* tmp;        // [N]
   double2* partials; // [MAX_PARTIALS]
   Ctl* ctl;
@@ -406,6 +412,9 @@ bool resident_geometry(const KParams& kp, int num_sms, ResidentGeom* g, int* thr
 // steps of 8; with two sub-iterations per exchange, 24..64.
 const void* resident_kernel(int tile_rows, int depth = 0, bool conv = false);
 const void* resident_batch_kernel(int tile_rows);  // 16, 32 or 64; else nullptr
+// Tensor-memory columns (of the SM's 512) one CTA of that loop allocates: 0 for the
+// one-step loop, -1 for a shape with no kernel.
+int resident_tmem_columns(int tile_rows, int depth);
 cudaError_t launch_poisson_resident(const KParams& kp, const ResidentGeom& g, int threads,
                                     size_t smem, const Buffers& b, cudaStream_t st);
 cudaError_t add_poisson_resident_node(cudaGraph_t graph, const cudaGraphNode_t* deps, size_t nd,

@@ -263,6 +263,10 @@ __device__ __forceinline__ void moments_body(const KParams& k, const StepState* 
     sb += __shfl_xor_sync(0xffffffffu, sb, o);
   }
   if (lane == 0) {
+    // a non-finite phi or q (flagged by any CTA before its ticket) can never satisfy the
+    // stopping rule: the solve then makes one sub-iteration and reports not converged,
+    // and the call reports EHD_ERR_NONFINITE
+    const bool bad_state = ld_cg(&ctl->nonfinite) != 0;
     ctl->sum_phi = sa;
     ctl->sum_q = sb;
     ctl->mean_q = (float)(sb / (double)N);
@@ -271,9 +275,9 @@ __device__ __forceinline__ void moments_body(const KParams& k, const StepState* 
     ctl->converged = 0;
     ctl->rel = 0.0;
     ctl->tol = tol;
-    ctl->min_iter = min_iter;
-    ctl->max_iter = max_iter;
-    ctl->fixed_iter = fixed_iter;
+    ctl->min_iter = bad_state ? 1 : min_iter;
+    ctl->max_iter = bad_state ? 1 : max_iter;
+    ctl->fixed_iter = bad_state ? 0 : fixed_iter;
     ctl->vw_b = ss->vw_b;
     ctl->vw_t = ss->vw_t;
     ctl->ticket_m = 0u;
@@ -608,10 +612,13 @@ __global__ void k_fields(KParams k, const StepState* __restrict__ ss, Pops pops,
     Ex = m1x * inv_den;
     Ey = m1y * inv_den;
   }
-  const float vals[8] = {phi, q, varphi, Ex, Ey, ux, uy, p};
+  // chemical potential (Eq. weq31) of the current phi with the last solve's field
+  const float mu = k.beta4 * phi * (phi - 0.5f) * (phi - 1.0f) - k.kappa * lap -
+                   0.5f * deps_of(k, phi) * (Ex * Ex + Ey * Ey);
+  const float vals[NIO] = {phi, q, varphi, Ex, Ey, ux, uy, p, mu};
   int slot = 0;
 #pragma unroll
-  for (int b = 0; b < 8; ++b) {
+  for (int b = 0; b < NIO; ++b) {
     if (mask & (1u << b)) {
       io[slot * (size_t)N + idx] = vals[b];
       ++slot;

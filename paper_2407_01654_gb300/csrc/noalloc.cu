@@ -11,9 +11,11 @@
 // the process.
 //
 // Limits and behaviour:
-//   * at most NA_MAX_CTAS = 4096 tiles of 32 x 16 nodes, i.e. lattices of up to
-//     4096 * 512 = 2,097,152 nodes with nx and ny fitting that tiling; larger lattices are
-//     rejected with EHD_ERR_TOO_LARGE before anything is queued;
+//   * the lattice's tiling into 32 x 16 tiles may have at most NA_MAX_CTAS = 4096 tiles,
+//     ceil(nx / 32) * ceil(ny / 16) <= 4096 (so at most 2,097,152 nodes, fewer when the
+//     sizes are not multiples of the tile); other lattices are rejected with
+//     EHD_ERR_TOO_LARGE before anything is queued.  Every kernel of the solve runs at
+//     most that many CTAs, one scratch partial each;
 //   * the first call on a device looks up the array's device address (once, with that
 //     device current); make that first call before any stream capture begins;
 //   * every call shares the one array and clears the loop control before it starts; two
@@ -70,15 +72,18 @@ __global__ void k_na_setup(NoAllocScratch* sc, double tol, int min_iter, int max
 }
 
 // Mean of q over the lattice (for the neutralised source), FP64, last CTA writes it.
+// At most NA_MAX_CTAS CTAs (one partial each in the fixed scratch), each thread striding
+// over the lattice.
 __global__ void __launch_bounds__(256) k_na_mean(int N, const float* __restrict__ q,
                                                  NoAllocScratch* sc) {
   __shared__ double s_w[8];
   __shared__ int s_last;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  float v = idx < N ? q[idx] : 0.0f;
+  double v = 0.0;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x)
+    v += (double)q[idx];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = (double)v;
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     double a = 0.0;
@@ -299,7 +304,8 @@ extern "C" int ehd_potential_solve_noalloc(const ehd_params* params, const float
                               P.poisson_fixed_iter, vw_b, vw_t);
   if (cudaGetLastError() != cudaSuccess) return EHD_ERR_CUDA;
   if (k.neutralize) {
-    k_na_mean<<<(k.N + 255) / 256, 256, 0, s>>>(k.N, q, sc);
+    const int mean_blocks = (k.N + 255) / 256 < NA_MAX_CTAS ? (k.N + 255) / 256 : NA_MAX_CTAS;
+    k_na_mean<<<mean_blocks, 256, 0, s>>>(k.N, q, sc);
     if (cudaGetLastError() != cudaSuccess) return EHD_ERR_CUDA;
   }
   const dim3 grid(gx, gy);

@@ -27,8 +27,8 @@ namespace {
 // GB300 this ran 1.7x faster per sub-iteration than 32 x 16 tiles of 256 threads (the
 // same bits; 128 x 16, 128 x 8, 64 x 32, 64 x 8 and 64 x 16 with 64 or 256 threads were
 // all slower).
-constexpr int TX = 64;
-constexpr int TY = 16;
+constexpr int TX = STREAM_TX;
+constexpr int TY = STREAM_TY;
 constexpr int THREADS = 128;
 constexpr int RX = TX + 2;
 constexpr int RY = TY + 2;
@@ -187,8 +187,8 @@ __global__ void __launch_bounds__(THREADS, 8) k_poisson(KParams k, float* __rest
 }
 
 cudaError_t launch_poisson(const KParams& kp, const Buffers& b, cudaStream_t st) {
+  if (stream_tiles(kp.nx, kp.ny) > MAX_PARTIALS) return cudaErrorInvalidValue;
   dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY);
-  if ((int)(grid.x * grid.y) > MAX_PARTIALS) return cudaErrorInvalidValue;
   k_poisson<<<grid, THREADS, 0, st>>>(kp, b.h, b.aq, b.partials, b.ctl,
                                       (cudaGraphConditionalHandle)0, 0);
   return cudaGetLastError();
@@ -196,6 +196,8 @@ cudaError_t launch_poisson(const KParams& kp, const Buffers& b, cudaStream_t st)
 
 cudaError_t add_poisson_node(cudaGraph_t g, cudaGraphNode_t* out, const KParams& kp,
                              const Buffers& b, cudaGraphConditionalHandle cond) {
+  // one FP64 partial pair per CTA: the grid must fit the partials region
+  if (stream_tiles(kp.nx, kp.ny) > MAX_PARTIALS) return cudaErrorInvalidValue;
   KParams k = kp;
   float* h = b.h;
   const float2* aq = b.aq;

@@ -1716,6 +1716,25 @@ const void* resident_kernel_of(int ty, int depth) {
 const void* resident_kernel(int ty, int depth, bool conv) {
   return conv ? resident_kernel_of<true>(ty, depth) : resident_kernel_of<false>(ty, depth);
 }
+
+// Tensor-memory columns one CTA of the multi-step loop allocates (tcgen05.alloc; 0 for
+// the one-step loop, which parks nothing), or -1 for a shape with no kernel.
+int resident_tmem_columns(int ty, int depth) {
+  if (depth == 0) return 0;
+  if (!resident_kernel(ty, depth, false)) return -1;
+  switch (depth == 2 ? ty : 1000 + ty) {
+    case 24: return Tile2<24>::TCOLS;
+    case 32: return Tile2<32>::TCOLS;
+    case 40: return Tile2<40>::TCOLS;
+    case 48: return Tile2<48>::TCOLS;
+    case 56: return Tile2<56>::TCOLS;
+    case 64: return Tile2<64>::TCOLS;
+    case 1048: return TileD<48, 3>::TCOLS;
+    case 1056: return TileD<56, 3>::TCOLS;
+    case 1064: return TileD<64, 3>::TCOLS;
+    default: return -1;
+  }
+}
 const void* resident_batch_kernel(int ty) {
   switch (ty) {
     case 16: return (const void*)k_poisson_resident_batch<16>;

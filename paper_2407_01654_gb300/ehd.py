@@ -20,7 +20,7 @@ STATUS = {0: "EHD_OK", 1: "EHD_ERR_INVALID_ARG", 2: "EHD_ERR_UNSTABLE_PARAMS",
           3: "EHD_ERR_NOMEM", 4: "EHD_ERR_NOT_CONVERGED", 5: "EHD_ERR_NONFINITE",
           6: "EHD_ERR_BUSY", 7: "EHD_ERR_CUDA", 8: "EHD_ERR_TOO_LARGE", 9: "EHD_ERR_TIMEOUT"}
 EHD_HOST, EHD_DEVICE = 0, 1
-FIELDS = ("phi", "q", "varphi", "Ex", "Ey", "ux", "uy", "p")
+FIELDS = ("phi", "q", "varphi", "Ex", "Ey", "ux", "uy", "p", "mu")
 
 
 class EhdError(RuntimeError):
@@ -267,7 +267,7 @@ class Sim:
         if p is None:
             ptrs.append(None)
         code = lib().ehd_set_fields(self._h, *ptrs, mem)
-        if code not in (EHD_OK, 4):
+        if code not in (EHD_OK, 4, 5):
             _check(code, "ehd_set_fields")
         return code
 
@@ -308,7 +308,7 @@ class Sim:
         rel = ctypes.c_double()
         code = lib().ehd_solve_potential(self._h, float(tol), int(max_iter), ctypes.byref(it),
                                          ctypes.byref(rel))
-        if code not in (EHD_OK, 4):
+        if code not in (EHD_OK, 4, 5):
             _check(code, "ehd_solve_potential")
         return it.value, rel.value, code
 

@@ -99,3 +99,23 @@ def test_workspace_holds_the_export_bands_of_each_on_chip_loop(L):
     assert t[3] - t[2] == 2 * 4 * 8 * 4 * (4 - 2) * (64 + 64)
     big = {loop: workspace(L, nx=1024, ny=1024, poisson_loop=loop) for loop in (2, 3, 4)}
     assert big[2] == big[3] == big[4]
+
+
+@pytest.mark.parametrize("nx,ny,ok", [
+    (4, 16 * 65536, True),        # 65536 streaming tiles of 64 x 16: the limit
+    (4, 16 * 65536 + 1, False),   # one tile row more: N / 256 is far below the limit
+    (12, 16 * 65544, False),      # 65544 tiles, while N / 256 = 49158 is within its limit
+    (8192, 2048, True),           # 16.8 M nodes, 16384 tiles
+])
+def test_size_validation_counts_streaming_tiles(L, nx, ny, ok):
+    """A lattice is refused (EHD_ERR_INVALID_ARG, from the host-side checks alone) when the
+    streaming potential kernel would need more CTAs than the per-CTA partial sums region
+    holds, ceil(nx / 64) * ceil(ny / 16) > 65536 -- for narrow, tall lattices that is far
+    more than one CTA per 256 nodes."""
+    p = ehd.Params.from_dict(wl.make_params(nx=nx, ny=ny))
+    nb = ctypes.c_size_t()
+    assert L.ehd_workspace_bytes(ctypes.byref(p), ctypes.byref(nb)) == (0 if ok else 1)
+    if not ok:
+        h = ctypes.c_void_p()
+        assert L.ehd_create(ctypes.byref(p), None, 0, None, ctypes.byref(h)) == 1
+        assert not h.value

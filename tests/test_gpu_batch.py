@@ -67,6 +67,35 @@ def test_batch_slot_matches_single_simulation(gpu):
         assert np.array_equal(got[k], ref[k]), k
 
 
+def test_batch_slots_match_oracle(gpu):
+    """Each slot of a mixed batch against the FP64 oracle directly: an FP32 slot and an
+    FP16-deviation slot of different sizes and parameters, admitted together, 100 steps at
+    a fixed sub-iteration count.  FP32 slot: relative L2 <= 1e-5 per field (the chemical
+    potential against its terms' scale, times the Laplacian's gain); FP16 slot: <= 5e-3
+    per field, the bar of the FP16 storage parity test."""
+    from oracle import ehd as orc
+    from test_gpu_parity import FP16_BAR, GROUPS, MU_GAIN, TOL_FIXED, mu_error, rel
+    pa, fa = request(64, 21, poisson_fixed_iter=3)
+    pb, fb = request(48, 22, poisson_fixed_iter=3, precision=1)
+    b = gpu.Batch(256 << 20, max_slots=4)
+    sa = b.admit(pa, fa, 0)
+    sb = b.admit(pb, fb, 1)
+    assert sa is not None and sb is not None
+    b.run(100)
+    for slot, (p, f), bar in ((sa, (pa, fa), TOL_FIXED), (sb, (pb, fb), FP16_BAR)):
+        o = orc.Sim(p)
+        o.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
+        o.step(100)
+        fo, fg = o.fields(), b.read_fields(slot)
+        errs = {g: rel(np.stack([fg[k] for k in ks]), np.stack([fo[k] for k in ks]))
+                for g, ks in GROUPS.items()}
+        errs["mu"] = mu_error(o.P, fo, fg) / MU_GAIN
+        print("batch slot vs oracle", "fp16" if p["precision"] else "fp32",
+              {k: f"{v:.2e}" for k, v in errs.items()})
+        assert all(v <= bar for v in errs.values()), errs
+    assert all(st["steps"] == 100 for st in b.poll())
+
+
 def test_admission_refusals_and_retire(gpu):
     """Admission is refused (the batch unchanged) when the arena, the slot count or the
     on-chip tile capacity would overflow; retiring frees the room again."""

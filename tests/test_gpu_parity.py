@@ -13,6 +13,7 @@ from paper_2407_01654_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 FIELDS = ("phi", "q", "varphi", "Ex", "Ey", "ux", "uy", "p")
+ALL_FIELDS = FIELDS + ("mu",)
 # vector fields are compared as vectors (the relative L2 of one component alone is
 # ill-conditioned where that component is near zero)
 GROUPS = {"phi": ("phi",), "q": ("q",), "varphi": ("varphi",), "E": ("Ex", "Ey"),
@@ -70,9 +71,30 @@ def droplet_box(nx, ny, r, seed, **over):
     return p, wl.perturbed(p, f, seed=seed, u_amp=3e-3, q_amp=1e-3)
 
 
-def assert_fields(fo, fg, tol):
+# The chemical potential hbar (Eq. weq31) is a difference of nearly equal terms at an
+# interface (4 beta phi (phi - 1/2)(phi - 1) against kappa lap(phi)), so its error is
+# measured against the size of those terms, and its bar is the Laplacian stencil's gain
+# (the sum of its weights' magnitudes, 10/3 + 4 (2/3) + 4 (1/6) = 20/3) times the bar
+# that phi itself meets.
+MU_GAIN = 20.0 / 3.0
+
+
+def mu_error(P, fo, fg):
+    """||mu_gpu - mu_oracle|| / (||bulk|| + ||kappa lap phi|| + ||field term||), the terms
+    taken from the oracle's fields (kappa lap phi = bulk - field term - mu)."""
+    phi = fo["phi"]
+    bulk = 4.0 * P.beta * phi * (phi - 0.5) * (phi - 1.0)
+    field = 0.5 * orc.deps_dphi(P, phi) * (fo["Ex"] ** 2 + fo["Ey"] ** 2)
+    lap_term = bulk - field - fo["mu"]
+    scale = np.linalg.norm(bulk) + np.linalg.norm(lap_term) + np.linalg.norm(field)
+    return float(np.linalg.norm(fg["mu"] - fo["mu"]) / scale) if scale > 0 else 0.0
+
+
+def assert_fields(fo, fg, tol, P=None):
     bad = {g: rel(np.stack([fg[k] for k in ks]), np.stack([fo[k] for k in ks]))
            for g, ks in GROUPS.items()}
+    if P is not None and "mu" in fo and "mu" in fg:
+        bad["mu"] = mu_error(P, fo, fg) / MU_GAIN
     assert all(v <= tol for v in bad.values()), bad
 
 
@@ -81,7 +103,7 @@ def test_droplet_fixed_k(gpu, loop):
     """Droplet in a field, walls, ragged 70 x 45, 100 steps, 3 sub-iterations per step."""
     p, f = droplet_box(70, 45, 11.0, seed=1, poisson_fixed_iter=3, poisson_loop=loop)
     o, g, fo, fg, so, sg = run_pair(gpu, p, f, 100)
-    assert_fields(fo, fg, TOL_FIXED)
+    assert_fields(fo, fg, TOL_FIXED, o.P)
     assert sg["poisson_iters_total"] == 300 and sg["status"] == 0
     assert abs(sg["sum_phi"] - fo["phi"].sum()) < 1e-5 * abs(fo["phi"].sum()) + 1e-3
 
@@ -94,7 +116,7 @@ def test_sessile_ramp_fixed_k(gpu, loop):
                               voltage=0.3, ew=0.4, poisson_fixed_iter=2, poisson_loop=loop)
     f = wl.perturbed(p, f, seed=2, u_amp=2e-3, q_amp=1e-3)
     o, g, fo, fg, so, sg = run_pair(gpu, p, f, 100)
-    assert_fields(fo, fg, TOL_FIXED)
+    assert_fields(fo, fg, TOL_FIXED, o.P)
     assert sg["step"] == 110
 
 
@@ -111,7 +133,7 @@ def test_periodic_neutralised_fixed_k(gpu, loop):
     z = np.zeros((ny, nx))
     f = wl.perturbed(p, dict(phi=phi, q=z + 2e-4, ux=z, uy=z), seed=3)
     o, g, fo, fg, so, sg = run_pair(gpu, p, f, 100)
-    assert_fields(fo, fg, TOL_FIXED)
+    assert_fields(fo, fg, TOL_FIXED, o.P)
 
 
 @pytest.mark.parametrize("loop", LOOPS)
@@ -128,7 +150,7 @@ def test_stopping_rule_mode(gpu, loop):
         ko.append(o.step(1).poisson_iters[0])
         kg.append(g.step(1)["poisson_iters_total"])
     assert sum(abs(a - b) for a, b in zip(ko, kg)) <= 0.1 * sum(ko) + 3
-    assert_fields(o.fields(), g.read_fields(), TOL_RULE)
+    assert_fields(o.fields(), g.read_fields(), TOL_RULE, o.P)
 
 
 @pytest.mark.parametrize("loop", LOOPS)
@@ -139,7 +161,7 @@ def test_full_size_sessile(gpu, loop):
                               poisson_loop=loop)
     f = wl.perturbed(p, f, seed=5, u_amp=1e-3, q_amp=1e-4)
     o, g, fo, fg, so, sg = run_pair(gpu, p, f, 10)
-    assert_fields(fo, fg, TOL_FIXED)
+    assert_fields(fo, fg, TOL_FIXED, o.P)
 
 
 @pytest.mark.parametrize("loop", LOOPS)
@@ -187,7 +209,7 @@ def test_device_io_matches_host_io(gpu):
     b.step(5)
     fa = a.read_fields()
     fb = b.read_fields(device=True)
-    for k in FIELDS:
+    for k in ALL_FIELDS:
         assert np.array_equal(fa[k].astype(np.float32), fb[k].cpu().numpy()), k
 
 
@@ -206,7 +228,7 @@ def test_save_load_bit_exact(gpu):
     c.load_state(blob)
     c.step(20)
     fa, fc = a.read_fields(), c.read_fields()
-    for k in FIELDS:
+    for k in ALL_FIELDS:
         assert np.array_equal(fa[k], fc[k]), k
 
 
@@ -230,7 +252,7 @@ def test_deterministic(gpu):
         g.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
         st = g.step(15)
         out.append((g.read_fields(), st))
-    for k in FIELDS:
+    for k in ALL_FIELDS:
         assert np.array_equal(out[0][0][k], out[1][0][k])
     assert out[0][1]["sum_q"] == out[1][1]["sum_q"]
 
@@ -254,7 +276,7 @@ def test_graph_and_host_loop_agree(gpu):
         assert prof["potential"]["launches"] == sb["poisson_iters_total"]
     assert prof["coupled"]["launches"] == 25
     fa, fb = a.read_fields(), b.read_fields()
-    for k in FIELDS:
+    for k in ALL_FIELDS:
         assert np.array_equal(fa[k], fb[k]), k
 
 
@@ -274,7 +296,7 @@ def test_stream_and_resident_loops_bitwise(gpu, fixed):
         g.step(12)
         assert g.loop_kind() == loop
         out.append(g.read_fields())
-    for k in FIELDS:
+    for k in ALL_FIELDS:
         for o in out[1:]:
             assert np.array_equal(out[0][k], o[k]), k
 
@@ -296,7 +318,7 @@ def test_multi_step_loops_match_one_step_with_the_rule(gpu, periodic):
         res.append((ks, g.read_fields()))
     for r in res[1:]:
         assert res[0][0] == r[0]
-        for k in FIELDS:
+        for k in ALL_FIELDS:
             assert np.array_equal(res[0][1][k], r[1][k]), k
 
 
@@ -334,5 +356,5 @@ def test_fp16_save_load_bit_exact(gpu):
     c.load_state(b.save_state())
     c.step(15)
     fa, fc = a.read_fields(), c.read_fields()
-    for k in FIELDS:
+    for k in ALL_FIELDS:
         assert np.array_equal(fa[k], fc[k]), k

@@ -3,7 +3,9 @@
 These complement the oracle parity tests: the GPU runs the configurations the oracle is
 too slow for (tens of thousands of steps, 256^2 lattices) and is checked against the
 closed forms and the paper's printed numbers."""
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -54,7 +56,11 @@ def test_planar_layers_config1(gpu):
 def test_gaussian_bell_config2_second_order(gpu):
     """Charge relaxation and diffusion of a Gaussian bell (Sec. 6.2) on 64^2, 128^2 and
     256^2 periodic lattices: second-order convergence to the closed form, and the same
-    errors as the FP64 oracle (0.00981 at 64^2, 0.00245 at 128^2) to 1 %."""
+    errors as the FP64 oracle to 1 % (tests/golden/gaussian_bell_errors.json, written by
+    tests/golden/make_gaussian_bell_errors.py from the oracle alone)."""
+    golden = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                         "gaussian_bell_errors.json")))
+    want = {r["N"]: r["rel_l2"] for r in golden["rows"]}
     errs = []
     for N in (64, 128, 256):
         p, f, n, s0 = wl.gaussian_bell(N)
@@ -64,7 +70,8 @@ def test_gaussian_bell_config2_second_order(gpu):
         qa = an.gaussian_bell(N, n, s0, f["q"].max(), p["alpha"], p["sigma_v"], p["eps_v"])
         errs.append(an.rel_l2(g.read_fields(("q",))["q"], qa))
     assert math.log2(errs[0] / errs[1]) > 1.9 and math.log2(errs[1] / errs[2]) > 1.9
-    assert abs(errs[0] / 0.009811 - 1) < 0.01 and abs(errs[1] / 0.002445 - 1) < 0.01
+    for N, e in zip((64, 128, 256), errs):
+        assert abs(e / want[N] - 1) < 0.01, (N, e, want[N])
 
 
 def deformation(phi):

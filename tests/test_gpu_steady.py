@@ -1,0 +1,75 @@
+"""Steady fields against the FP64 oracle: the two-layer planar set-up of Sec. 6.1 (4 x 64,
+permittivity ratio 10, conductivity ratio 0.1, fixed wall potentials) run to its steady
+state, 20 000 steps with the paper's stopping rule (tolerance 1e-5) on both sides.  Bar
+(the benchmark spec): relative L2 <= 1e-3 per field on steady fields.
+
+At the steady state the fluid is at rest (u is zero up to a decaying transient of about
+1e-8), so u is compared on an absolute scale: the RMS difference must stay below 1e-3 of
+the problem's electric velocity scale U_E = eps_l E^2 L / mu with E = delta varphi / L.
+The chemical potential uses the same bar scaled by the Laplacian's gain (test_gpu_parity).
+"""
+import numpy as np
+import pytest
+
+from oracle import ehd as orc
+from paper_2407_01654_gb300 import workloads as wl
+from test_gpu_parity import MU_GAIN, mu_error, rel
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 20000
+TOL_STEADY = 1e-3
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_01654_gb300 import build
+    build.build()
+    from paper_2407_01654_gb300 import ehd
+    return ehd
+
+
+@pytest.fixture(scope="module")
+def oracle_steady():
+    """The oracle's steady state (about a minute of CPU time), shared by the loops."""
+    p, f = wl.planar_layers()
+    o = orc.Sim(p)
+    o.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
+    st = o.step(STEPS)
+    return p, f, o, o.fields(), st
+
+
+@pytest.mark.parametrize("loop", [pytest.param(1, id="stream"), pytest.param(2, id="resident"),
+                                  pytest.param(3, id="resident2")])
+def test_planar_layers_steady_fields_match_oracle(gpu, oracle_steady, loop):
+    p, f, o, fo, so = oracle_steady
+    g = gpu.Sim(dict(p, poisson_loop=loop))
+    g.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
+    sg = g.step(STEPS)
+    assert g.loop_kind() == loop
+    assert sg["status"] == 0 and sg["step"] == STEPS
+    fg = g.read_fields()
+    # the state is steady: a further 500 steps leave phi, q, varphi and E unchanged to 1e-4
+    g.step(500)
+    later = g.read_fields()
+    for k in ("phi", "q", "varphi", "Ey"):
+        assert rel(later[k], fg[k]) < 1e-4, k
+    # both sides settled to one sub-iteration per step, after about the same total
+    assert so.poisson_iters[-100:] == [1] * 100
+    assert sg["poisson_iters_max"] >= 1
+    assert abs(sg["poisson_iters_total"] - sum(so.poisson_iters)) <= 0.05 * sum(so.poisson_iters)
+    errs = {}
+    for grp, ks in (("phi", ("phi",)), ("q", ("q",)), ("varphi", ("varphi",)),
+                    ("E", ("Ex", "Ey")), ("p", ("p",))):
+        errs[grp] = rel(np.stack([fg[k] for k in ks]), np.stack([fo[k] for k in ks]))
+    errs["mu"] = mu_error(o.P, fo, fg) / MU_GAIN
+    L = p["ny"]
+    E = p["varphi_bottom"] / L
+    u_e = p["eps_l"] * E * E * L / p["mu_l"]
+    du = np.sqrt(np.mean((fg["ux"] - fo["ux"]) ** 2 + (fg["uy"] - fo["uy"]) ** 2))
+    errs["u/U_E"] = du / u_e
+    print("steady planar layers, loop", loop, {k: f"{v:.2e}" for k, v in errs.items()})
+    assert all(v <= TOL_STEADY for v in errs.values()), errs

@@ -300,3 +300,48 @@ def test_electric_chemical_potential_is_variational():
     bulk = ehd.chemical_potential(P, phi, z, 0.0, 0.0)
     psi = lambda ph: P.beta * ph ** 2 * (ph - 1) ** 2
     assert np.allclose(bulk, (psi(phi + d) - psi(phi - d)) / (2 * d), rtol=1e-7)
+
+
+def test_fields_mu_flat_interface_at_rest_is_near_zero():
+    """The output chemical potential of a flat tanh interface with no field: the profile
+    0.5 + 0.5 tanh(2 y / W) makes the bulk term 4 beta phi (phi - 1/2)(phi - 1) and
+    kappa lap(phi) cancel exactly in the continuum (Sec. 2.2), so the discrete hbar is
+    O(1/W^2) of either term (second order: doubling W divides it by about four); a
+    dropped kappa term or a wrong sign leaves it O(1)."""
+    ratios = []
+    for W in (8.0, 16.0):
+        P0, f = wl.planar_layers(nx=4, ny=int(12 * W), varphi_high=0.0, width=W)
+        sim = ehd.Sim(P0)
+        sim.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
+        F = sim.fields()
+        P = sim.P
+        phi = F["phi"]
+        bulk = 4.0 * P.beta * phi * (phi - 0.5) * (phi - 1.0)
+        assert np.abs(bulk).max() > 1e-3 * P.beta
+        ratios.append(np.abs(F["mu"]).max() / np.abs(bulk).max())
+    assert ratios[0] < 0.05
+    assert 3.5 < ratios[0] / ratios[1] < 4.5
+
+
+def test_fields_mu_uniform_phase_in_uniform_field():
+    """A uniform phase phi = c between electrodes: eps is uniform, the potential is linear
+    and E = (varphi_b - varphi_t) / ny everywhere, the Laplacian of phi vanishes (90 degree
+    walls), so hbar = 4 beta c (c - 1/2)(c - 1) - eps'(c) E^2 / 2 exactly (Eq. weq31).
+    (A fixed, long potential loop: the linear start already has the right potential, so
+    the relative-change rule would stop before the first moment, which carries E, has
+    developed.)"""
+    c, vb = 0.3, 0.2
+    P0 = wl.make_params(nx=3, ny=20, walls_y=1, eps_l=6.0, eps_v=1.0, sigma_l=0.0,
+                        sigma_v=0.0, gamma=0.01, width=4.0, varphi_bottom=vb, varphi_top=0.0,
+                        poisson_fixed_iter=6000)
+    z = np.zeros((20, 3))
+    sim = ehd.Sim(P0)
+    sim.set_fields(z + c, z, z, z)
+    F = sim.fields()
+    P = sim.P
+    E = vb / 20.0
+    assert np.allclose(F["Ey"], E, rtol=1e-6, atol=0)
+    want = 4.0 * P.beta * c * (c - 0.5) * (c - 1.0) - 0.5 * ehd.deps_dphi(P, c) * E * E
+    field_part = 0.5 * ehd.deps_dphi(P, c) * E * E
+    assert abs(field_part) > 1e-3 * abs(want)
+    assert np.allclose(F["mu"], want, rtol=0, atol=1e-6 * abs(field_part))

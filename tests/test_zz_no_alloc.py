@@ -47,15 +47,20 @@ def regular_solve(ehd, p, phi, q):
     return out
 
 
-def noalloc_solve(torch, ehd, p, phi, q):
-    ny, nx = phi.shape
-    # initial populations as the regular solve sets them: equilibrium of the potential
-    # interpolated linearly between the walls (0 when y is periodic)
+def linear_start(p, nx, ny):
+    """The potential the regular solve starts from: interpolated linearly between the
+    walls (0 when y is periodic), [ny][nx]."""
     if p["walls_y"]:
         lin = p["varphi_bottom"] + (p["varphi_top"] - p["varphi_bottom"]) * (np.arange(ny) + 0.5) / ny
     else:
         lin = np.zeros(ny)
-    h0 = W[:, None, None] * np.repeat(lin[:, None], nx, axis=1)[None]
+    return np.repeat(lin[:, None], nx, axis=1)
+
+
+def noalloc_solve(torch, ehd, p, phi, q):
+    ny, nx = phi.shape
+    # initial populations as the regular solve sets them: equilibrium of the linear start
+    h0 = W[:, None, None] * linear_start(p, nx, ny)[None]
     dev = dict(dtype=torch.float32, device="cuda")
     h = torch.tensor(h0, **dev).contiguous()
     hw = torch.empty_like(h)
@@ -68,8 +73,9 @@ def noalloc_solve(torch, ehd, p, phi, q):
                                                  tq.data_ptr(), h.data_ptr(), hw.data_ptr(),
                                                  stream, ctypes.byref(it), ctypes.byref(rel))
     assert code == 0, ehd.STATUS.get(code, code)
-    assert it.value == p["poisson_fixed_iter"]
-    return h.double().cpu().numpy().sum(axis=0) * (9.0 / 5.0)
+    if p["poisson_fixed_iter"] > 0:
+        assert it.value == p["poisson_fixed_iter"]
+    return h.double().cpu().numpy().sum(axis=0) * (9.0 / 5.0), it.value
 
 
 def rel_l2(a, b):
@@ -83,7 +89,42 @@ def test_noalloc_matches_regular_solve_twice(env):
     for seed, (nx, ny, walls) in enumerate(((70, 45, 1), (66, 40, 0))):
         p, phi, q = case(seed, nx, ny, walls)
         ref = regular_solve(ehd, p, phi, q)
-        got = noalloc_solve(torch, ehd, p, phi, q)
+        got, _ = noalloc_solve(torch, ehd, p, phi, q)
+        assert rel_l2(got, ref) <= 1e-5
+
+
+def test_noalloc_stopping_rule_matches_oracle(env):
+    """With the paper's stopping rule (relative change below 1e-5, Algorithm 1) the
+    no-allocation solve, whose host loop queues sub-iterations in growing chunks, stops
+    within rounding of where the FP64 oracle's loop (oracle.ehd.poisson_solve) stops, and
+    its potential matches the oracle's within 1e-3 (walls with wall potentials, then a
+    periodic lattice with a neutralised source)."""
+    from oracle import ehd as orc
+    torch, ehd = env
+    for seed, (nx, ny, walls) in enumerate(((70, 45, 1), (66, 40, 0))):
+        p, phi, q = case(10 + seed, nx, ny, walls)
+        p["poisson_fixed_iter"] = 0
+        P = orc.Params.from_dict(p)
+        h0 = orc.h_eq(linear_start(p, nx, ny))
+        vw = (p["varphi_bottom"], p["varphi_top"]) if walls else (0.0, 0.0)
+        h, it_o, _, ok = orc.poisson_solve(P, h0, phi, q, vw)
+        assert ok and it_o > 20
+        got, it_g = noalloc_solve(torch, ehd, p, phi, q)
+        assert abs(it_g - it_o) <= max(2, 0.01 * it_o), (it_g, it_o)
+        assert rel_l2(got, orc.varphi_of(h)) <= 1e-3
+
+
+def test_noalloc_near_scratch_limit_with_neutralised_source(env):
+    """A periodic lattice at the scratch limit (1024 x 2048: exactly 4096 tiles of 32 x 16,
+    2,097,152 nodes) with a neutralised source, whose mean pass strides over the lattice
+    with at most 4096 CTAs: the potential after a few sub-iterations matches the regular
+    solve within 1e-5, twice in a row."""
+    torch, ehd = env
+    p, phi, q = case(30, 1024, 2048, 0)
+    p["poisson_fixed_iter"] = 4
+    ref = regular_solve(ehd, p, phi, q)
+    for _ in range(2):
+        got, _ = noalloc_solve(torch, ehd, p, phi, q)
         assert rel_l2(got, ref) <= 1e-5
 
 
