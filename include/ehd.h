@@ -205,6 +205,13 @@ int ehd_set_fields(ehd_sim* sim, const void* phi, const void* q, const void* ux,
  * when the statistics are read). */
 int ehd_step(ehd_sim* sim, int nsteps, ehd_stats* stats);
 
+/* Launch mode of later ehd_step calls (no counterpart in the paper): enable != 0 (the
+ * default) launches each step as one captured CUDA graph; enable == 0 queues the step's
+ * kernels one by one from the host, with the streaming loop's stopping rule checked on
+ * the host between chunks of launches.  Both run the same kernels and give the same
+ * states, bit for bit.  Errors: EHD_ERR_INVALID_ARG (null handle). */
+int ehd_use_graphs(ehd_sim* sim, int enable);
+
 /* Which potential loop this simulation runs: EHD_LOOP_STREAM, EHD_LOOP_RESIDENT,
  * EHD_LOOP_RESIDENT2 or EHD_LOOP_RESIDENT3 (negative: invalid handle). */
 int ehd_loop_kind(const ehd_sim* sim);
@@ -280,6 +287,14 @@ int ehd_potential_solve_noalloc(const ehd_params* params, const float* phi, cons
  * simulation does not use the on-chip loop. */
 int ehd_diag_expire_barrier(ehd_sim* sim);
 
+/* Measurement helper (no counterpart in the paper): the shared-memory bandwidth of the
+ * current device in bytes per second (loads plus stores, all SMs, 16-byte conflict-free
+ * accesses, best of four timed launches after one warm-up), the ceiling of the on-chip
+ * potential loop's per-node data movement.  Queues its launches on `stream` (NULL:
+ * default stream) and synchronises it.  Allocates no device memory.
+ * Errors: EHD_ERR_INVALID_ARG (null pointer), EHD_ERR_CUDA. */
+int ehd_diag_smem_bandwidth(void* stream, double* bytes_per_second);
+
 /* Releases the simulation (and its workspace if the library allocated it). */
 void ehd_destroy(ehd_sim* sim);
 
@@ -353,6 +368,41 @@ int ehd_batch_read_fields(ehd_batch* b, int slot, unsigned mask, void* const* ou
 int ehd_batch_retire(ehd_batch* b, int slot);
 int ehd_batch_info(ehd_batch* b, ehd_batch_info_t* info);
 void ehd_batch_destroy(ehd_batch* b);
+
+/* ---------------------------------------------------------------------------------------
+ * Slab decomposition of one lattice: the coupled step of Algorithm 1 computed by nslabs
+ * bands of consecutive rows, each with its own device buffers (one ghost row below and
+ * one above), exchanging what crosses each cut -- after the moments pass one row of phi and
+ * of the potential coefficients each way, after every potential sub-iteration the 8
+ * potential populations of the boundary rows, after the coupled pass the 9 populations
+ * (3 directions of g, l and f) pushed across -- and combining the global sums (the
+ * stopping rule's, and the FP64 sums of phi and q) in a fixed slab order, so every slab
+ * takes the same stopping decision.  It is the layout of a lattice spread over several
+ * devices, not a step of the method; here every slab lives on the current device and the
+ * exchange is a gather kernel between the slabs' buffers.  With a fixed sub-iteration
+ * count the fields equal the single-lattice run's bit for bit (except a neutralised
+ * source, whose mean charge is summed in another order); with the stopping rule the
+ * combined sums round differently, so a decision within rounding of the tolerance can
+ * differ.  FP32 storage only; the streaming potential loop.
+ * --------------------------------------------------------------------------------------- */
+typedef struct ehd_slabs ehd_slabs;
+
+/* Splits params' lattice into nslabs slabs of ny / nslabs rows (the remainder spread over
+ * the slabs), 1 <= nslabs <= 64 and <= ny, on `stream`.  The library allocates every
+ * buffer.  Errors: EHD_ERR_INVALID_ARG (also for FP16 storage), EHD_ERR_UNSTABLE_PARAMS,
+ * EHD_ERR_NOMEM, EHD_ERR_CUDA. */
+int ehd_slabs_create(const ehd_params* params, int nslabs, void* stream, ehd_slabs** out);
+/* As ehd_set_fields, host double arrays [ny][nx] of the whole lattice (p nullable). */
+int ehd_slabs_set_fields(ehd_slabs* t, const double* phi, const double* q, const double* ux,
+                         const double* uy, const double* p);
+/* As ehd_step (the statistics are those of the whole lattice); synchronises the stream. */
+int ehd_slabs_step(ehd_slabs* t, int nsteps, ehd_stats* stats);
+/* As ehd_read_fields to host double arrays [ny][nx] of the whole lattice. */
+int ehd_slabs_read_fields(ehd_slabs* t, unsigned mask, double* const* out);
+/* Bytes crossing all cuts per potential sub-iteration and per step (the rest of the
+ * exchange), as a multi-device run would send them.  Either pointer may be NULL. */
+int ehd_slabs_exchange_bytes(const ehd_slabs* t, size_t* per_sub_iteration, size_t* per_step);
+void ehd_slabs_destroy(ehd_slabs* t);
 
 /* Static description of a status code. */
 const char* ehd_error_string(int code);

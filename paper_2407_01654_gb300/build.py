@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libehd.so")
-SOURCES = ["kernels.cu", "poisson.cu", "poisson_resident.cu", "noalloc.cu", "batch.cu", "api.cu"]
+SOURCES = ["kernels.cu", "poisson.cu", "poisson_resident.cu", "noalloc.cu", "batch.cu", "api.cu",
+           "diag.cu", "slabs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

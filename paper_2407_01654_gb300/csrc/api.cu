@@ -25,9 +25,20 @@ struct Layout {
   size_t export_floats, rtiles;
 };
 
-// Design target for the resident loop's tiling: the GB300's SM count.  On a device with
-// fewer SMs the tiles are larger and fewer, which needs less export space.
-constexpr int DESIGN_SMS = 152;
+// SM count the resident loop tiles for: the current device's (every SM gets tiles), or
+// the GB300's 152 when no device can be queried (e.g. sizing a workspace on a host
+// without a GPU).  The export space reserved for it covers that many tiles.
+constexpr int DEFAULT_SMS = 152;
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1) {
+    cudaGetLastError();
+    return DEFAULT_SMS;
+  }
+  return sms;
+}
 
 // Sub-iterations per halo exchange of the on-chip loop a poisson_loop value asks for (0:
 // one, the one-step loop; also for the automatic choice and the streaming loop).
@@ -69,7 +80,7 @@ Layout layout_for(const ehd_params& P, int fixed_ty = 0) {
   kp.ny = P.ny;
   L.export_floats = 0;
   L.rtiles = 0;
-  if (resident_geometry(kp, DESIGN_SMS, &g, &th, &sm, fixed_ty, loop_depth(P.poisson_loop))) {
+  if (resident_geometry(kp, device_sms(), &g, &th, &sm, fixed_ty, loop_depth(P.poisson_loop))) {
     L.rtiles = (size_t)g.ntx * g.nty;
     L.export_floats = 2 * L.rtiles * 8 * (size_t)g.pmax;
   }
@@ -141,6 +152,13 @@ KParams make_kparams(const ehd_params& P) {
   k.nx = P.nx;
   k.ny = P.ny;
   k.N = P.nx * P.ny;
+  k.nint = k.N;
+  k.row0 = 0;
+  k.halo_lo = 0;
+  k.halo_hi = 0;
+  k.slab = 0;
+  k.y_global0 = 0;
+  k.ny_global = P.ny;
   k.walls = P.walls_y;
   k.neutralize = P.neutralize_charge ? 1 : 0;
   k.rho_v = (float)P.rho_v;
@@ -497,7 +515,7 @@ int sim_create(const ehd_params* params, void* workspace, size_t workspace_bytes
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess &&
         coop && L.export_floats && params->poisson_loop != EHD_LOOP_STREAM) {
-      const int use_sms = sms < DESIGN_SMS ? sms : DESIGN_SMS;
+      const int use_sms = sms;
       ResidentGeom g;
       int th;
       size_t sm;
@@ -686,10 +704,10 @@ int ehd_step(ehd_sim* s, int nsteps, ehd_stats* out) {
     if (reset_stats(s) != EHD_OK) return EHD_ERR_CUDA;
     s->stats_live = true;
   }
-  if (!s->profiling) ensure_graphs(s);
+  if (!s->profiling && !s->no_graphs) ensure_graphs(s);
   for (int k = 0; k < nsteps; ++k) {
     // an armed diagnostic runs its step from the host (the graph has no slot for it)
-    const bool use_graphs = s->graphs_ok && !s->profiling && !s->expire_barrier;
+    const bool use_graphs = s->graphs_ok && !s->profiling && !s->expire_barrier && !s->no_graphs;
     if (use_graphs) {
       // the whole step, potential loop included, without returning to the host
       EHD_CUDA(cudaGraphLaunch(s->exec[s->cur], s->stream));
@@ -714,6 +732,12 @@ int ehd_step(ehd_sim* s, int nsteps, ehd_stats* out) {
     if (st == EHD_ERR_NONFINITE || st == EHD_ERR_CUDA || st == EHD_ERR_TIMEOUT) status = st;
   }
   return status;
+}
+
+int ehd_use_graphs(ehd_sim* s, int enable) {
+  if (!s) return EHD_ERR_INVALID_ARG;
+  s->no_graphs = enable == 0;
+  return EHD_OK;
 }
 
 int ehd_diag_expire_barrier(ehd_sim* s) {

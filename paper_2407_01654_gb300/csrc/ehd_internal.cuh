@@ -68,7 +68,15 @@ __host__ __device__ constexpr float ch_k(int i) {
 // Coefficients of one simulation, single precision, computed on the host from the
 // double-precision parameters.
 struct KParams {
-  int nx, ny, N, walls;
+  int nx, ny, N, walls;     // N: nodes per stored field (interior rows, plus ghost rows in a
+                            // slab); walls applies to the sides without a ghost row
+  int nint;                 // interior nodes nx * ny (= N outside slabs)
+  int row0;                 // stored row of interior row 0: 1 in a slab (a ghost row below)
+  int halo_lo, halo_hi;     // 1: the row below interior row 0 / above row ny-1 is a ghost row
+                            // holding the neighbouring slab's values (slab decomposition)
+  int slab;                 // 1: one slab of a decomposed lattice (reductions are combined
+                            // across slabs by separate kernels)
+  int y_global0, ny_global; // the slab's first row and the height of the whole lattice
   int neutralize;
   float rho_v, drho;        // rho = rho_v + drho phi
   float mu_v, dmu;          // mu = mu_v + dmu phi
@@ -189,6 +197,7 @@ struct Ctl {
   unsigned bar_count;       // grid barrier of the resident potential loop: arrivals in
                             // the current solve (reset with the loop control)
   int bar_error;            // a barrier wait timed out (sticky)
+  double slab_num, slab_den;// one slab's stopping sums of its last sub-iteration
 };
 
 // Tiling of the resident potential loop: ntx x nty tiles of TX x TY nodes (the last
@@ -434,6 +443,11 @@ cudaError_t launch_stats_reset(const Buffers& b, cudaStream_t st);
 cudaError_t launch_expire_barrier(const Buffers& b, cudaStream_t st);
 cudaError_t launch_fields(const KParams& kp, const Buffers& b, int cur, unsigned mask,
                           cudaStream_t st);
+cudaError_t launch_phi_now(const KParams& kp, const Buffers& b, int cur, cudaStream_t st);
+cudaError_t launch_fields_from_phi(const KParams& kp, const Buffers& b, int cur, unsigned mask,
+                                   cudaStream_t st);
+cudaError_t add_poisson_node_nocond(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
+                                    cudaGraphNode_t* out, const KParams& kp, const Buffers& b);
 
 // Graph nodes of the per-step kernels (argument values are copied into the node).
 cudaError_t add_moments_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,

@@ -11,9 +11,11 @@ namespace ehd {
 namespace {
 
 
-// phi at the 3x3 neighbourhood of (x, y); rows outside a wall are ghost values from the
-// wetting rule n_w.grad(phi) = -sqrt(2 beta/kappa) cos(theta) (phi - phi^2) (Eq. weq68):
-// ghost = phi_wall_row + a cos(theta) phi (1 - phi) with the first fluid row's value.
+// phi at the 3x3 neighbourhood of interior node (x, y); rows outside a wall are ghost
+// values from the wetting rule n_w.grad(phi) = -sqrt(2 beta/kappa) cos(theta) (phi - phi^2)
+// (Eq. weq68): ghost = phi_wall_row + a cos(theta) phi (1 - phi) with the first fluid row's
+// value.  In a slab, the row beyond a cut is the stored ghost row (the neighbouring slab's
+// values).
 struct Stencil {
   float c, e, w, n, s, ne, nw, se, sw;
 };
@@ -26,28 +28,31 @@ __device__ __forceinline__ Stencil load_stencil(const KParams& k, const StepStat
   const int xm = x == 0 ? nx - 1 : x - 1;
   const int xp = x + 1 == nx ? 0 : x + 1;
   Stencil s;
-  const float* row = phi + (size_t)y * nx;
+  const float* row = phi + (size_t)(y + k.row0) * nx;
   s.c = __ldg(row + x);
   s.e = __ldg(row + xp);
   s.w = __ldg(row + xm);
-  if (k.walls && y + 1 == ny) {
+  if (k.walls && !k.halo_hi && y + 1 == ny) {
     const float a = k.wet_a * sa.cos_t;
     s.n = ghost(s.c, a);
     s.ne = ghost(s.e, a);
     s.nw = ghost(s.w, a);
   } else {
-    const float* r = phi + (size_t)(y + 1 == ny ? 0 : y + 1) * nx;
+    // the row above: wrapped, or the stored ghost row beyond a cut (interior row ny)
+    const int ry = y + 1 == ny ? (k.halo_hi ? ny : 0) : y + 1;
+    const float* r = phi + (size_t)(ry + k.row0) * nx;
     s.n = __ldg(r + x);
     s.ne = __ldg(r + xp);
     s.nw = __ldg(r + xm);
   }
-  if (k.walls && y == 0) {
+  if (k.walls && !k.halo_lo && y == 0) {
     const float a = k.wet_a * sa.cos_b;
     s.s = ghost(s.c, a);
     s.se = ghost(s.e, a);
     s.sw = ghost(s.w, a);
   } else {
-    const float* r = phi + (size_t)(y == 0 ? ny - 1 : y - 1) * nx;
+    const int ry = y == 0 ? (k.halo_lo ? -1 : ny - 1) : y - 1;
+    const float* r = phi + (size_t)(ry + k.row0) * nx;
     s.s = __ldg(r + x);
     s.se = __ldg(r + xp);
     s.sw = __ldg(r + xm);
@@ -81,26 +86,26 @@ __device__ __forceinline__ Stencil load_varphi_stencil(const KParams& k,
   const int xm = x == 0 ? nx - 1 : x - 1;
   const int xp = x + 1 == nx ? 0 : x + 1;
   Stencil s;
-  const int row = y * nx;
+  const int row = (y + k.row0) * nx;
   s.c = varphi_node(hs, N, row + x);
   s.e = varphi_node(hs, N, row + xp);
   s.w = varphi_node(hs, N, row + xm);
-  if (k.walls && y + 1 == ny) {
+  if (k.walls && !k.halo_hi && y + 1 == ny) {
     s.n = 2.0f * vw_t - s.c;
     s.ne = 2.0f * vw_t - s.e;
     s.nw = 2.0f * vw_t - s.w;
   } else {
-    const int r = (y + 1 == ny ? 0 : y + 1) * nx;
+    const int r = ((y + 1 == ny ? (k.halo_hi ? ny : 0) : y + 1) + k.row0) * nx;
     s.n = varphi_node(hs, N, r + x);
     s.ne = varphi_node(hs, N, r + xp);
     s.nw = varphi_node(hs, N, r + xm);
   }
-  if (k.walls && y == 0) {
+  if (k.walls && !k.halo_lo && y == 0) {
     s.s = 2.0f * vw_b - s.c;
     s.se = 2.0f * vw_b - s.e;
     s.sw = 2.0f * vw_b - s.w;
   } else {
-    const int r = (y == 0 ? ny - 1 : y - 1) * nx;
+    const int r = ((y == 0 ? (k.halo_lo ? -1 : ny - 1) : y - 1) + k.row0) * nx;
     s.s = varphi_node(hs, N, r + x);
     s.se = varphi_node(hs, N, r + xp);
     s.sw = varphi_node(hs, N, r + xm);
@@ -108,23 +113,25 @@ __device__ __forceinline__ Stencil load_varphi_stencil(const KParams& k,
   return s;
 }
 
-// Index of the node a population leaving (x, y) in direction i lands on, and the
-// direction it lands in: periodic in x; at a wall, half-way bounce-back returns it to
-// (x, y) in the opposite direction.
+// Stored index of the node a population leaving interior node (x, y) in direction i lands
+// on, and the direction it lands in: periodic in x; at a wall, half-way bounce-back
+// returns it to (x, y) in the opposite direction; beyond a slab's cut it lands in the
+// ghost row, from which the exchange hands it to the neighbouring slab.
 __device__ __forceinline__ int push_target(const KParams& k, int x, int y, int i, int& dir) {
   int ty = y + cy(i);
   dir = i;
-  if (k.walls) {
-    if (ty < 0 || ty >= k.ny) {
-      dir = opp(i);
-      return y * k.nx + x;
+  if (ty < 0 || ty >= k.ny) {
+    if (!(ty < 0 ? k.halo_lo : k.halo_hi)) {
+      if (k.walls) {
+        dir = opp(i);
+        return (y + k.row0) * k.nx + x;
+      }
+      ty = ty < 0 ? k.ny - 1 : 0;
     }
-  } else {
-    ty = ty < 0 ? k.ny - 1 : (ty >= k.ny ? 0 : ty);
   }
   int tx = x + cx(i);
   tx = tx < 0 ? k.nx - 1 : (tx >= k.nx ? 0 : tx);
-  return ty * k.nx + tx;
+  return (ty + k.row0) * k.nx + tx;
 }
 
 // FP32 warp sum.
@@ -143,10 +150,11 @@ template <bool HALF>
 __global__ void k_init(KParams k, const StepState* __restrict__ ss, const float* __restrict__ in,
                        int have_p, Pops pops, float* __restrict__ h, float* __restrict__ hist) {
   const int N = k.N;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= N) return;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;  // interior node
+  if (i0 >= k.nint) return;
   const StepState sa = *ss;
-  const int y = idx / k.nx, x = idx - y * k.nx;
+  const int y = i0 / k.nx, x = i0 - y * k.nx;
+  const int idx = i0 + k.row0 * k.nx;                      // its stored index
   const float* phi0 = in;
   const float q = __ldg(in + N + idx);
   const float ux = __ldg(in + 2 * N + idx);
@@ -168,9 +176,10 @@ __global__ void k_init(KParams k, const StepState* __restrict__ ss, const float*
     st_pop<HALF>(k, pops, 1, i, idx, wgt(i) * q * (1.0f + 3.0f * cu));
     st_pop<HALF>(k, pops, 2, i, idx, (i == 0 ? (wgt(0) - 1.0f) : wgt(i)) * 3.0f * p + rho * si);
   }
-  // potential at equilibrium with the linear wall interpolation (0 when periodic)
+  // potential at equilibrium with the linear wall interpolation (0 when periodic); in a
+  // slab, y and ny are those of the whole lattice
   float vlin = 0.0f;
-  if (k.walls) vlin = sa.vw_b + (sa.vw_t - sa.vw_b) * ((y + 0.5f) / (float)k.ny);
+  if (k.walls) vlin = sa.vw_b + (sa.vw_t - sa.vw_b) * ((y + k.y_global0 + 0.5f) / (float)k.ny_global);
 #pragma unroll
   for (int i = 1; i < 9; ++i) h[(i - 1) * (size_t)N + idx] = wgt(i) * vlin;
 #pragma unroll
@@ -199,7 +208,9 @@ __device__ __forceinline__ void moments_body(const KParams& k, const StepState* 
   const int N = k.N;
   float phi_acc = 0.0f, q_acc = 0.0f;
   int bad = 0;
-  for (int idx = bid * blockDim.x + threadIdx.x; idx < N; idx += nblk * blockDim.x) {
+  const int off = k.row0 * k.nx;  // stored index of interior node 0
+  for (int i0 = bid * blockDim.x + threadIdx.x; i0 < k.nint; i0 += nblk * blockDim.x) {
+    const int idx = i0 + off;
     float phi = 0.0f, q = 0.0f;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -269,7 +280,7 @@ __device__ __forceinline__ void moments_body(const KParams& k, const StepState* 
     const bool bad_state = ld_cg(&ctl->nonfinite) != 0;
     ctl->sum_phi = sa;
     ctl->sum_q = sb;
-    ctl->mean_q = (float)(sb / (double)N);
+    ctl->mean_q = (float)(sb / (double)k.nint);
     ctl->iter = 0;
     ctl->done = 0;
     ctl->converged = 0;
@@ -332,9 +343,10 @@ __device__ __forceinline__ void coupled_body(const KParams& k, StepState* ss, in
     stats->barrier_error |= ld_cg(&ctl->bar_error);
     stats->steps += 1;
   }
-  const int idx = bid * blockDim.x + threadIdx.x;
-  if (idx >= N) return;
-  const int y = idx / k.nx, x = idx - y * k.nx;
+  const int i0 = bid * blockDim.x + threadIdx.x;  // interior node
+  if (i0 >= k.nint) return;
+  const int y = i0 / k.nx, x = i0 - y * k.nx;
+  const int idx = i0 + k.row0 * k.nx;              // its stored index
   const float* hs = hbuf + (size_t)parity * NH * N;
 
   // a2: stencils on phi
@@ -550,8 +562,9 @@ __global__ void k_stats_reset(DevStats* s) {
 // ------------------------------------------------------------------------------------
 template <bool HALF>
 __global__ void k_phi_now(KParams k, Pops pops, float* __restrict__ out) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= k.N) return;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i0 >= k.nint) return;
+  const int idx = i0 + k.row0 * k.nx;
   float s = 0.0f;
 #pragma unroll
   for (int i = 0; i < 9; ++i) s += ld_pop<HALF>(k, pops, 0, i, idx);
@@ -564,9 +577,10 @@ __global__ void k_fields(KParams k, const StepState* __restrict__ ss, Pops pops,
                          const float* __restrict__ hbuf, const float* __restrict__ hist,
                          const Ctl* ctl, unsigned mask, float* __restrict__ io) {
   const int N = k.N;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= N) return;
-  const int y = idx / k.nx, x = idx - y * k.nx;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i0 >= k.nint) return;
+  const int y = i0 / k.nx, x = i0 - y * k.nx;
+  const int idx = i0 + k.row0 * k.nx;
   const int parity = ld_cg(&ctl->parity);
   const float* hs = hbuf + (size_t)parity * NH * N;
   const StepState sa = *ss;
@@ -641,17 +655,17 @@ cudaError_t launch_init(const KParams& kp, const Buffers& b, int cur, bool have_
                         cudaStream_t st) {
   const Pops P = pops_copy(kp, b, cur);
   if (kp.half)
-    k_init<true><<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, b.ss + cur, b.io, have_p ? 1 : 0, P,
+    k_init<true><<<blocks_for(kp.nint, 256), 256, 0, st>>>(kp, b.ss + cur, b.io, have_p ? 1 : 0, P,
                                                        b.h, b.hist);
   else
-    k_init<false><<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, b.ss + cur, b.io, have_p ? 1 : 0,
+    k_init<false><<<blocks_for(kp.nint, 256), 256, 0, st>>>(kp, b.ss + cur, b.io, have_p ? 1 : 0,
                                                         P, b.h, b.hist);
   return cudaGetLastError();
 }
 
 cudaError_t launch_moments(const KParams& kp, const Buffers& b, int cur, double tol,
                            int min_iter, int max_iter, int fixed_iter, cudaStream_t st) {
-  const int nb = moments_blocks(kp.N);
+  const int nb = moments_blocks(kp.nint);
   const Pops P = pops_copy(kp, b, cur);
   if (kp.half)
     k_moments<true><<<nb, 256, 0, st>>>(kp, b.ss + cur, P, b.hist, b.phi, b.aq, b.partials,
@@ -665,10 +679,10 @@ cudaError_t launch_moments(const KParams& kp, const Buffers& b, int cur, double 
 cudaError_t launch_coupled(const KParams& kp, const Buffers& b, int cur, cudaStream_t st) {
   const Pops Pi = pops_copy(kp, b, cur), Po = pops_copy(kp, b, cur ^ 1);
   if (kp.half)
-    k_coupled<true><<<blocks_for(kp.N, 128), 128, 0, st>>>(kp, b.ss, cur, Pi, Po, b.phi, b.h,
+    k_coupled<true><<<blocks_for(kp.nint, 128), 128, 0, st>>>(kp, b.ss, cur, Pi, Po, b.phi, b.h,
                                                            b.hist, b.ctl, b.stats);
   else
-    k_coupled<false><<<blocks_for(kp.N, 128), 128, 0, st>>>(kp, b.ss, cur, Pi, Po, b.phi, b.h,
+    k_coupled<false><<<blocks_for(kp.nint, 128), 128, 0, st>>>(kp, b.ss, cur, Pi, Po, b.phi, b.h,
                                                             b.hist, b.ctl, b.stats);
   return cudaGetLastError();
 }
@@ -687,14 +701,36 @@ cudaError_t launch_fields(const KParams& kp, const Buffers& b, int cur, unsigned
                           cudaStream_t st) {
   const Pops P = pops_copy(kp, b, cur);
   if (kp.half) {
-    k_phi_now<true><<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, P, b.tmp);
-    k_fields<true><<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, b.ss + cur, P, b.tmp, b.phi, b.h,
+    k_phi_now<true><<<blocks_for(kp.nint, 256), 256, 0, st>>>(kp, P, b.tmp);
+    k_fields<true><<<blocks_for(kp.nint, 256), 256, 0, st>>>(kp, b.ss + cur, P, b.tmp, b.phi, b.h,
                                                           b.hist, b.ctl, mask, b.io);
   } else {
-    k_phi_now<false><<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, P, b.tmp);
-    k_fields<false><<<blocks_for(kp.N, 256), 256, 0, st>>>(kp, b.ss + cur, P, b.tmp, b.phi,
+    k_phi_now<false><<<blocks_for(kp.nint, 256), 256, 0, st>>>(kp, P, b.tmp);
+    k_fields<false><<<blocks_for(kp.nint, 256), 256, 0, st>>>(kp, b.ss + cur, P, b.tmp, b.phi,
                                                            b.h, b.hist, b.ctl, mask, b.io);
   }
+  return cudaGetLastError();
+}
+
+// The two halves of launch_fields, for slabs (whose phi ghost rows are exchanged in
+// between): phi of the current populations into tmp, then the requested fields into io.
+cudaError_t launch_phi_now(const KParams& kp, const Buffers& b, int cur, cudaStream_t st) {
+  const Pops P = pops_copy(kp, b, cur);
+  if (kp.half)
+    k_phi_now<true><<<blocks_for(kp.nint, 256), 256, 0, st>>>(kp, P, b.tmp);
+  else
+    k_phi_now<false><<<blocks_for(kp.nint, 256), 256, 0, st>>>(kp, P, b.tmp);
+  return cudaGetLastError();
+}
+cudaError_t launch_fields_from_phi(const KParams& kp, const Buffers& b, int cur, unsigned mask,
+                                   cudaStream_t st) {
+  const Pops P = pops_copy(kp, b, cur);
+  if (kp.half)
+    k_fields<true><<<blocks_for(kp.nint, 256), 256, 0, st>>>(kp, b.ss + cur, P, b.tmp, b.phi, b.h,
+                                                             b.hist, b.ctl, mask, b.io);
+  else
+    k_fields<false><<<blocks_for(kp.nint, 256), 256, 0, st>>>(kp, b.ss + cur, P, b.tmp, b.phi,
+                                                              b.h, b.hist, b.ctl, mask, b.io);
   return cudaGetLastError();
 }
 
@@ -714,7 +750,7 @@ cudaError_t add_moments_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t 
                   &fixed_iter};
   cudaKernelNodeParams p = {};
   p.func = kp.half ? (void*)k_moments<true> : (void*)k_moments<false>;
-  p.gridDim = dim3(moments_blocks(kp.N));
+  p.gridDim = dim3(moments_blocks(kp.nint));
   p.blockDim = dim3(256);
   p.kernelParams = args;
   return cudaGraphAddKernelNode(out, g, deps, nd, &p);
@@ -734,7 +770,7 @@ cudaError_t add_coupled_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t 
   void* args[] = {&k, &ss, &cur, &pin, &pout, &phi, &h, &hist, &ctl, &stats};
   cudaKernelNodeParams p = {};
   p.func = kp.half ? (void*)k_coupled<true> : (void*)k_coupled<false>;
-  p.gridDim = dim3(blocks_for(kp.N, 128));
+  p.gridDim = dim3(blocks_for(kp.nint, 128));
   p.blockDim = dim3(128);
   p.kernelParams = args;
   return cudaGraphAddKernelNode(out, g, deps, nd, &p);

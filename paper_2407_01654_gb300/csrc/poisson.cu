@@ -55,17 +55,19 @@ __global__ void __launch_bounds__(THREADS, 8) k_poisson(KParams k, float* __rest
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const float om = k.omega_h;
 
-  // phase 1: collide tile + ring
+  // phase 1: collide tile + ring (interior rows y0 - 1 .. y0 + TY; in a slab the rows
+  // beyond a cut are the stored ghost rows, -1 and ny)
   for (int t = threadIdx.x; t < RX * RY; t += THREADS) {
     const int ly = t / RX, lx = t - ly * RX;
     int gy = y0 + ly - 1;
-    if (k.walls) {
-      if (gy < 0 || gy >= ny) continue;  // outside a wall: never gathered
-    } else {
-      gy = wrap(gy, ny);
+    if (gy < 0 || gy >= ny) {
+      if (!(gy < 0 ? k.halo_lo : k.halo_hi)) {
+        if (k.walls) continue;  // outside a wall: never gathered
+        gy = wrap(gy, ny);
+      }
     }
     const int gx = wrap(x0 + lx - 1, nx);
-    const size_t idx = (size_t)gy * nx + gx;
+    const size_t idx = (size_t)(gy + k.row0) * nx + gx;
     float h[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) h[i] = __ldg(src + i * N + idx);
@@ -93,13 +95,13 @@ __global__ void __launch_bounds__(THREADS, 8) k_poisson(KParams k, float* __rest
     const int ly = t / TX, lx = t - ly * TX;
     const int gx = x0 + lx, gy = y0 + ly;
     if (gx >= nx || gy >= ny) continue;
-    const size_t idx = (size_t)gy * nx + gx;
+    const size_t idx = (size_t)(gy + k.row0) * nx + gx;
     float hn[8];
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
       const int sy = gy - cy(i);
       float v;
-      if (k.walls && (sy < 0 || sy >= ny)) {
+      if (k.walls && ((sy < 0 && !k.halo_lo) || (sy >= ny && !k.halo_hi))) {
         // anti-bounce-back at the wall the population came from
         v = h_wall(i, sm[opp(i) - 1][ly + 1][lx + 1], sy < 0 ? vw_b : vw_t);
       } else {
@@ -140,6 +142,8 @@ __global__ void __launch_bounds__(THREADS, 8) k_poisson(KParams k, float* __rest
   if (!s_last) return;
   __threadfence();
   __shared__ double s_red[THREADS][2];
+  // (in a slab this CTA only publishes the slab's sums; the decision combines every
+  // slab's, see k_slab_decide)
   double a = 0.0, b = 0.0;
   for (int j = threadIdx.x; j < nblocks; j += THREADS) {
     const double2 v = __ldcg(partials + j);
@@ -155,6 +159,13 @@ __global__ void __launch_bounds__(THREADS, 8) k_poisson(KParams k, float* __rest
       s_red[threadIdx.x][1] += s_red[threadIdx.x + o][1];
     }
     __syncthreads();
+  }
+  if (threadIdx.x == 0 && k.slab) {
+    ctl->slab_num = s_red[0][0];
+    ctl->slab_den = s_red[0][1];
+    ctl->ticket_p = 0u;
+    __threadfence();
+    return;
   }
   if (threadIdx.x == 0) {
     const double nm = s_red[0][0], dn = s_red[0][1];
@@ -188,10 +199,31 @@ __global__ void __launch_bounds__(THREADS, 8) k_poisson(KParams k, float* __rest
 
 cudaError_t launch_poisson(const KParams& kp, const Buffers& b, cudaStream_t st) {
   if (stream_tiles(kp.nx, kp.ny) > MAX_PARTIALS) return cudaErrorInvalidValue;
-  dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY);
+  dim3 grid((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY);  // interior rows
   k_poisson<<<grid, THREADS, 0, st>>>(kp, b.h, b.aq, b.partials, b.ctl,
                                       (cudaGraphConditionalHandle)0, 0);
   return cudaGetLastError();
+}
+
+// One sub-iteration as a graph node that leaves the loop's condition alone (slabs: the
+// kernel that combines the slabs' sums decides).
+cudaError_t add_poisson_node_nocond(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
+                                    cudaGraphNode_t* out, const KParams& kp, const Buffers& b) {
+  if (stream_tiles(kp.nx, kp.ny) > MAX_PARTIALS) return cudaErrorInvalidValue;
+  KParams k = kp;
+  float* h = b.h;
+  const float2* aq = b.aq;
+  double2* partials = b.partials;
+  Ctl* ctl = b.ctl;
+  cudaGraphConditionalHandle cond = 0;
+  int use = 0;
+  void* args[] = {&k, &h, &aq, &partials, &ctl, &cond, &use};
+  cudaKernelNodeParams p = {};
+  p.func = (void*)k_poisson;
+  p.gridDim = dim3((kp.nx + TX - 1) / TX, (kp.ny + TY - 1) / TY);
+  p.blockDim = dim3(THREADS);
+  p.kernelParams = args;
+  return cudaGraphAddKernelNode(out, g, deps, nd, &p);
 }
 
 cudaError_t add_poisson_node(cudaGraph_t g, cudaGraphNode_t* out, const KParams& kp,

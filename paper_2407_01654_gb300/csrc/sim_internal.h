@@ -41,6 +41,7 @@ struct ehd_sim {
   // one step graph per population copy (moments -> while{potential} -> coupled)
   bool graphs_tried = false;
   bool graphs_ok = false;
+  bool no_graphs = false;     // steps queued kernel by kernel from the host (ehd_use_graphs)
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   // resident (on-chip) potential loop, when the lattice fits

@@ -156,6 +156,17 @@ SIGNATURES = {
                                                    ctypes.POINTER(ctypes.c_int),
                                                    ctypes.POINTER(ctypes.c_double)]),
     "ehd_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(KernelTimes)]),
+    "ehd_diag_smem_bandwidth": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "ehd_use_graphs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "ehd_slabs_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_void_p)]),
+    "ehd_slabs_set_fields": (ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 5),
+    "ehd_slabs_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Stats)]),
+    "ehd_slabs_read_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint,
+                                             ctypes.POINTER(ctypes.c_void_p)]),
+    "ehd_slabs_exchange_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t),
+                                                ctypes.POINTER(ctypes.c_size_t)]),
+    "ehd_slabs_destroy": (None, [ctypes.c_void_p]),
 }
 
 
@@ -187,6 +198,14 @@ def _host(a):
 
 def _is_torch_cuda(a):
     return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def smem_bandwidth(stream=None):
+    """Shared-memory bandwidth of the current device in bytes per second (loads plus
+    stores, measured by ehd_diag_smem_bandwidth)."""
+    v = ctypes.c_double()
+    _check(lib().ehd_diag_smem_bandwidth(stream, ctypes.byref(v)), "ehd_diag_smem_bandwidth")
+    return v.value
 
 
 class Sim:
@@ -280,6 +299,11 @@ class Sim:
         out["status"] = code
         return out
 
+    def use_graphs(self, enable=True):
+        """enable=False: later steps queue their kernels one by one from the host instead of
+        launching one captured graph per step (same kernels, same states)."""
+        _check(lib().ehd_use_graphs(self._h, 1 if enable else 0), "ehd_use_graphs")
+
     def diag_expire_barrier(self):
         """Diagnostics: the next on-chip potential solve's grid barrier never completes, so
         its bounded waits run out and the call reports EHD_ERR_TIMEOUT (9)."""
@@ -348,8 +372,71 @@ class Sim:
         return buf.raw
 
     def load_state(self, blob):
+        """blob: bytes from save_state, or a host uint8 torch tensor holding them (e.g. in
+        pinned memory, passed to the library without a copy)."""
+        if hasattr(blob, "data_ptr"):
+            _check(lib().ehd_load_state(self._h, ctypes.c_void_p(blob.data_ptr()), blob.numel()),
+                   "ehd_load_state")
+            return
         buf = ctypes.create_string_buffer(blob, len(blob))
         _check(lib().ehd_load_state(self._h, buf, len(blob)), "ehd_load_state")
+
+
+class Slabs:
+    """One lattice computed by `nslabs` slabs of rows with their own buffers, exchanging
+    the rows that cross each cut (the ehd_slabs_* calls).  Host numpy I/O only."""
+
+    def __init__(self, params, nslabs, stream=None):
+        self.ny, self.nx = int(params["ny"]), int(params["nx"])
+        self._p = Params.from_dict(params)
+        h = ctypes.c_void_p()
+        _check(lib().ehd_slabs_create(ctypes.byref(self._p), int(nslabs), stream, ctypes.byref(h)),
+               "ehd_slabs_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ehd_slabs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_fields(self, phi, q, ux, uy, p=None):
+        arrs = [_host(a) for a in (phi, q, ux, uy)] + ([_host(p)] if p is not None else [])
+        ptrs = [a.ctypes.data for a in arrs] + ([None] if p is None else [])
+        code = lib().ehd_slabs_set_fields(self._h, *ptrs)
+        if code not in (EHD_OK, 4, 5):
+            _check(code, "ehd_slabs_set_fields")
+        return code
+
+    def step(self, nsteps=1):
+        st = Stats()
+        code = lib().ehd_slabs_step(self._h, int(nsteps), ctypes.byref(st))
+        if code not in (EHD_OK, 4, 5):
+            _check(code, "ehd_slabs_step")
+        out = st.as_dict()
+        out["status"] = code
+        return out
+
+    def read_fields(self, names=FIELDS):
+        mask = 0
+        for n in names:
+            mask |= 1 << FIELDS.index(n)
+        order = [n for n in FIELDS if mask & (1 << FIELDS.index(n))]
+        outs = [np.empty((self.ny, self.nx), dtype=np.float64) for _ in order]
+        arr = (ctypes.c_void_p * len(outs))(*[o.ctypes.data for o in outs])
+        _check(lib().ehd_slabs_read_fields(self._h, mask, arr), "ehd_slabs_read_fields")
+        return dict(zip(order, outs))
+
+    def exchange_bytes(self):
+        a, b = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(lib().ehd_slabs_exchange_bytes(self._h, ctypes.byref(a), ctypes.byref(b)),
+               "ehd_slabs_exchange_bytes")
+        return a.value, b.value
 
 
 class Batch:

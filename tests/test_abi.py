@@ -119,3 +119,19 @@ def test_size_validation_counts_streaming_tiles(L, nx, ny, ok):
         h = ctypes.c_void_p()
         assert L.ehd_create(ctypes.byref(p), None, 0, None, ctypes.byref(h)) == 1
         assert not h.value
+
+
+@pytest.mark.parametrize("change,nslabs", [
+    (dict(), 0),                    # at least one slab
+    (dict(), 65),                   # at most 64
+    (dict(ny=3), 4),                # at least one row per slab
+    (dict(precision=1), 2),         # FP32 storage only
+])
+def test_slabs_create_rejects_bad_arguments(L, change, nslabs):
+    """The slab decomposition refuses bad arguments on the host, before any device work."""
+    d = wl.make_params(nx=16, ny=16)
+    d.update(change)
+    p = ehd.Params.from_dict(d)
+    h = ctypes.c_void_p()
+    assert L.ehd_slabs_create(ctypes.byref(p), nslabs, None, ctypes.byref(h)) == 1
+    assert not h.value

@@ -42,4 +42,9 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    # the requested window, really timed, on the GPU arm's own config
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["steps"] == 1 and d["warmup"] == 3 and d["config"] == bench.CONFIG
+    assert abs(d["ms_per_step"] - 1e3 * bench.CONFIG["nodes"] / (d["value"] * 1e6)) < 1e-6 * d["ms_per_step"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"

@@ -6,7 +6,10 @@ state, 20 000 steps with the paper's stopping rule (tolerance 1e-5) on both side
 At the steady state the fluid is at rest (u is zero up to a decaying transient of about
 1e-8), so u is compared on an absolute scale: the RMS difference must stay below 1e-3 of
 the problem's electric velocity scale U_E = eps_l E^2 L / mu with E = delta varphi / L.
-The chemical potential uses the same bar scaled by the Laplacian's gain (test_gpu_parity).
+The pressure is compared without its mean: the flow model is gauge-free (only grad p
+enters), and the level of this steady pressure (rms about 2e-6) is a free constant whose
+FP32 drift over the run means nothing.  The chemical potential uses the same bar scaled by
+the Laplacian's gain (test_gpu_parity).
 """
 import numpy as np
 import pytest
@@ -63,13 +66,17 @@ def test_planar_layers_steady_fields_match_oracle(gpu, oracle_steady, loop):
     assert abs(sg["poisson_iters_total"] - sum(so.poisson_iters)) <= 0.05 * sum(so.poisson_iters)
     errs = {}
     for grp, ks in (("phi", ("phi",)), ("q", ("q",)), ("varphi", ("varphi",)),
-                    ("E", ("Ex", "Ey")), ("p", ("p",))):
+                    ("E", ("Ex", "Ey"))):
         errs[grp] = rel(np.stack([fg[k] for k in ks]), np.stack([fo[k] for k in ks]))
+    errs["p - mean"] = rel(fg["p"] - fg["p"].mean(), fo["p"] - fo["p"].mean())
     errs["mu"] = mu_error(o.P, fo, fg) / MU_GAIN
     L = p["ny"]
     E = p["varphi_bottom"] / L
     u_e = p["eps_l"] * E * E * L / p["mu_l"]
     du = np.sqrt(np.mean((fg["ux"] - fo["ux"]) ** 2 + (fg["uy"] - fo["uy"]) ** 2))
     errs["u/U_E"] = du / u_e
-    print("steady planar layers, loop", loop, {k: f"{v:.2e}" for k, v in errs.items()})
+    print("steady planar layers, loop", loop, {k: f"{v:.2e}" for k, v in errs.items()},
+          "sum phi gpu", float(fg["phi"].sum()), "oracle", float(fo["phi"].sum()),
+          "sum q gpu", float(fg["q"].sum()), "oracle", float(fo["q"].sum()),
+          "K total gpu", sg["poisson_iters_total"], "oracle", sum(so.poisson_iters))
     assert all(v <= TOL_STEADY for v in errs.values()), errs
