@@ -316,39 +316,52 @@ __global__ void __launch_bounds__(256) k_moments(KParams k, const StepState* __r
 // g (Eq. weq45), l (Eq. weq58) and f (Eq. weq38) and the push to the neighbours with
 // half-way bounce-back; history for the next step.
 // ------------------------------------------------------------------------------------
-// Block `bid` of blocks of 128 threads over one simulation.
+// Where the per-node kernel reads the node's post-stream populations, converged potential
+// populations and lagged quantities: device memory (GlobalSrc) or a shared-memory tile
+// staged by bulk copies (SmemSrc, k_coupled_staged).  The arithmetic is the same function
+// for both, so both compute the same bits.
 template <bool HALF>
-__device__ __forceinline__ void coupled_body(const KParams& k, StepState* ss, int cur,
-                                             const Pops& pin, const Pops& pout,
-                                             const float* __restrict__ phi_f,
-                                             const float* __restrict__ hbuf,
-                                             float* __restrict__ hist, const Ctl* ctl,
-                                             DevStats* stats, int bid) {
-  const int N = k.N;
-  const int parity = ld_cg(&ctl->parity);
-  const StepState sa = ss[cur];
-  if (bid == 0 && threadIdx.x == 0) {
-    // values of the next step, in the other slot (this step's slot is being read)
-    ss[cur ^ 1] = make_step(k, sa.n + 1, 0);
-    // the potential loop of this step has finished: record its statistics
-    const int it = ld_cg(&ctl->iter);
-    stats->iters_total += it;
-    stats->iters_min = min(stats->iters_min, it);
-    stats->iters_max = max(stats->iters_max, it);
-    stats->not_converged += ld_cg(&ctl->converged) ? 0 : 1;
-    stats->nonfinite |= ld_cg(&ctl->nonfinite);
-    stats->last_rel = ld_cg(&ctl->rel);
-    stats->sum_phi = ld_cg(&ctl->sum_phi);
-    stats->sum_q = ld_cg(&ctl->sum_q);
-    stats->barrier_error |= ld_cg(&ctl->bar_error);
-    stats->steps += 1;
+struct GlobalSrc {
+  const KParams& k;
+  const Pops& pin;
+  const float* __restrict__ hs;
+  const float* __restrict__ hist;
+  int idx;
+  __device__ __forceinline__ float pop(int field, int i) const {
+    return ld_pop<HALF>(k, pin, field, i, idx);
   }
-  const int i0 = bid * blockDim.x + threadIdx.x;  // interior node
-  if (i0 >= k.nint) return;
-  const int y = i0 / k.nx, x = i0 - y * k.nx;
-  const int idx = i0 + k.row0 * k.nx;              // its stored index
-  const float* hs = hbuf + (size_t)parity * NH * N;
+  __device__ __forceinline__ float h(int i) const { return __ldg(hs + i * (size_t)k.N + idx); }
+  __device__ __forceinline__ float hist_in(int j) const { return hist[j * (size_t)k.N + idx]; }
+};
 
+// The statistics and next-step values one thread of the pass records (the potential loop
+// of this step has finished).
+__device__ __forceinline__ void coupled_record(const KParams& k, StepState* ss, int cur,
+                                               const StepState& sa, const Ctl* ctl,
+                                               DevStats* stats) {
+  // values of the next step, in the other slot (this step's slot is being read)
+  ss[cur ^ 1] = make_step(k, sa.n + 1, 0);
+  const int it = ld_cg(&ctl->iter);
+  stats->iters_total += it;
+  stats->iters_min = min(stats->iters_min, it);
+  stats->iters_max = max(stats->iters_max, it);
+  stats->not_converged += ld_cg(&ctl->converged) ? 0 : 1;
+  stats->nonfinite |= ld_cg(&ctl->nonfinite);
+  stats->last_rel = ld_cg(&ctl->rel);
+  stats->sum_phi = ld_cg(&ctl->sum_phi);
+  stats->sum_q = ld_cg(&ctl->sum_q);
+  stats->barrier_error |= ld_cg(&ctl->bar_error);
+  stats->steps += 1;
+}
+
+// The coupled pass at interior node (x, y), stored index idx: everything after the loads.
+template <bool HALF, class Src>
+__device__ __forceinline__ void coupled_node(const KParams& k, const StepState& sa,
+                                             const Pops& pout, const float* __restrict__ phi_f,
+                                             const float* __restrict__ hs,
+                                             float* __restrict__ hist, const Ctl* ctl, int x,
+                                             int y, int idx, const Src& src) {
+  const int N = k.N;
   // a2: stencils on phi
   const Stencil st = load_stencil(k, sa, phi_f, x, y);
   float gphx, gphy, lap;
@@ -359,19 +372,19 @@ __device__ __forceinline__ void coupled_body(const KParams& k, StepState* ss, in
   float g[9], l[9], f[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    g[i] = ld_pop<HALF>(k, pin, 0, i, idx);
-    l[i] = ld_pop<HALF>(k, pin, 1, i, idx);
-    f[i] = ld_pop<HALF>(k, pin, 2, i, idx);
+    g[i] = src.pop(0, i);
+    l[i] = src.pop(1, i);
+    f[i] = src.pop(2, i);
   }
   float hv[8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) hv[i] = __ldg(hs + i * (size_t)N + idx);
-  const float s_prev_in = hist[idx];
-  const float jx_prev_in = hist[(size_t)N + idx];
-  const float jy_prev_in = hist[2 * (size_t)N + idx];
-  const float R_prev = hist[3 * (size_t)N + idx];
-  const float Fx_prev = hist[4 * (size_t)N + idx];
-  const float Fy_prev = hist[5 * (size_t)N + idx];
+  for (int i = 0; i < 8; ++i) hv[i] = src.h(i);
+  const float s_prev_in = src.hist_in(0);
+  const float jx_prev_in = src.hist_in(1);
+  const float jy_prev_in = src.hist_in(2);
+  const float R_prev = src.hist_in(3);
+  const float Fx_prev = src.hist_in(4);
+  const float Fy_prev = src.hist_in(5);
 
   // a1: moments and properties
   float lsum = 0.0f, mx = 0.0f, my = 0.0f, fsum_nr = 0.0f;
@@ -452,13 +465,26 @@ __device__ __forceinline__ void coupled_body(const KParams& k, StepState* ss, in
   const float djx = 3.0f * (Jx - jx_prev), djy = 3.0f * (Jy - jy_prev);
   const float grx = k.drho * gphx, gry = k.drho * gphy;
 
+  // The rest population carries phi, O(1), while a step changes it by far less than its
+  // FP32 spacing; relaxed on its own (g_0 - (g_0 - g_eq_0)/tau_g + ...) it would drop
+  // those increments systematically and phi would drift.  It takes instead the exact
+  // remainder of the collision's phi balance: sum_i g_i* = phi - (3 s - s_prev)/2 (sum_i
+  // g_eq_i = phi, sum_i w_i k_i = -1), so g_0* = phi - (sum_{i>0} g_i* + (3 s - s_prev)/2),
+  // the same value in exact arithmetic, with one unbiased rounding at the scale of phi.
+  float gmov = 0.0f;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
+  for (int i0 = 1; i0 < 10; ++i0) {
+    const int i = i0 == 9 ? 0 : i0;  // the moving populations first, the rest one last
     const float w = wgt(i);
     const float cu = cx(i) * ux + cy(i) * uy;
     // a6: Cahn-Hilliard, g_eq of Eq. weq46
-    const float geq = i == 0 ? phi - (1.0f - wgt(0)) * mu : w * mu;
-    const float gn = g[i] - om_g * (g[i] - geq) + w * ch_k(i) * gsrc;
+    float gn;
+    if (i == 0) {
+      gn = phi - (gmov + gsrc);
+    } else {
+      gn = g[i] - om_g * (g[i] - w * mu) + w * ch_k(i) * gsrc;
+      gmov += gn;
+    }
     // a7: Nernst-Planck, l_eq of Eq. weq61, S_i + T_i of Eqs. weq59, weq60
     const float leq = w * q * (1.0f + 3.0f * cu);
     const float ln = l[i] - om_l * (l[i] - leq) + pref_l * w * (R + cx(i) * djx + cy(i) * djy);
@@ -481,6 +507,195 @@ __device__ __forceinline__ void coupled_body(const KParams& k, StepState* ss, in
   hist[3 * (size_t)N + idx] = R;
   hist[4 * (size_t)N + idx] = Fx;
   hist[5 * (size_t)N + idx] = Fy;
+}
+
+// Block `bid` of blocks of 128 threads over one simulation, one node per thread, loads
+// straight from device memory.
+template <bool HALF>
+__device__ __forceinline__ void coupled_body(const KParams& k, StepState* ss, int cur,
+                                             const Pops& pin, const Pops& pout,
+                                             const float* __restrict__ phi_f,
+                                             const float* __restrict__ hbuf,
+                                             float* __restrict__ hist, const Ctl* ctl,
+                                             DevStats* stats, int bid) {
+  const int parity = ld_cg(&ctl->parity);
+  const StepState sa = ss[cur];
+  if (bid == 0 && threadIdx.x == 0) coupled_record(k, ss, cur, sa, ctl, stats);
+  const int i0 = bid * blockDim.x + threadIdx.x;  // interior node
+  if (i0 >= k.nint) return;
+  const int y = i0 / k.nx, x = i0 - y * k.nx;
+  const int idx = i0 + k.row0 * k.nx;              // its stored index
+  const float* hs = hbuf + (size_t)parity * NH * k.N;
+  const GlobalSrc<HALF> src{k, pin, hs, hist, idx};
+  coupled_node<HALF>(k, sa, pout, phi_f, hs, hist, ctl, x, y, idx, src);
+}
+
+// ------------------------------------------------------------------------------------
+// The coupled pass with its per-node inputs staged in shared memory by bulk copies (FP32
+// storage, one lattice, nodes a multiple of 4): persistent CTAs of CT_TL threads walk the
+// lattice in tiles of CT_TL consecutive nodes; each tile's 41 planes (27 populations, 8
+// potential populations, 6 lagged quantities) arrive by cp.async.bulk into one of two
+// stages, completing on that stage's mbarrier, while the CTA computes the previous tile.
+// The number of bytes in flight no longer depends on how many loaded values a thread can
+// hold in registers.  The arithmetic is coupled_node's, so the results are the bits of
+// k_coupled.
+// ------------------------------------------------------------------------------------
+constexpr int CT_TL = 256;
+constexpr int CT_PLANES = NPOP + NH + 6;
+constexpr int CT_STAGE_FLOATS = CT_PLANES * CT_TL;
+constexpr size_t CT_SMEM = 2 * sizeof(float) * CT_STAGE_FLOATS + 2 * sizeof(unsigned long long);
+constexpr unsigned long long CT_WAIT_NS = 2000000000ull;  // 2 s
+
+struct SmemSrc {
+  const float* s;  // the stage: [41][CT_TL]
+  int t;
+  __device__ __forceinline__ float pop(int field, int i) const {
+    return s[(field * 9 + i) * CT_TL + t];
+  }
+  __device__ __forceinline__ float h(int i) const { return s[(NPOP + i) * CT_TL + t]; }
+  __device__ __forceinline__ float hist_in(int j) const { return s[(NPOP + NH + j) * CT_TL + t]; }
+};
+
+__device__ __forceinline__ unsigned long long ct_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void ct_mbar_init(unsigned bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void ct_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void ct_bulk_load(unsigned dst, const float* src, unsigned bytes,
+                                             unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst), "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ bool ct_try_wait(unsigned bar, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+// Waits for a stage's copies, giving up after `limit_ns`.
+__device__ __forceinline__ bool ct_wait(unsigned bar, unsigned phase,
+                                        unsigned long long limit_ns) {
+  const unsigned long long t0 = ct_ns();
+  while (!ct_try_wait(bar, phase))
+    if (ct_ns() - t0 > limit_ns) return false;
+  return true;
+}
+
+__global__ void __launch_bounds__(CT_TL, 2)
+    k_coupled_staged(KParams k, StepState* ss, int cur, Pops pin, Pops pout,
+                     const float* __restrict__ phi_f, const float* __restrict__ hbuf,
+                     float* __restrict__ hist, const Ctl* ctl, DevStats* stats) {
+  extern __shared__ __align__(128) float ct_smem[];
+  __shared__ int s_ok;
+  const int N = k.N;
+  const int parity = ld_cg(&ctl->parity);
+  const StepState sa = ss[cur];
+  if (blockIdx.x == 0 && threadIdx.x == 0) coupled_record(k, ss, cur, sa, ctl, stats);
+  const float* hs = hbuf + (size_t)parity * NH * N;
+  const int ntiles = (N + CT_TL - 1) / CT_TL;
+  const unsigned sbase = (unsigned)__cvta_generic_to_shared(ct_smem);
+  const unsigned bar0 = sbase + 2u * sizeof(float) * CT_STAGE_FLOATS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    ct_mbar_init(bar0);
+    ct_mbar_init(bar0 + 8);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // warp 0 queues the 41 plane copies of a tile into a stage: N is a multiple of 4, so
+  // every source and size is a multiple of 16 bytes
+  auto issue = [&](int tile, int st) {
+    const int i0 = tile * CT_TL;
+    const int n = min(CT_TL, N - i0);
+    const unsigned bytes = (unsigned)n * 4u;
+    const unsigned bar = bar0 + 8u * st;
+    if (lane == 0) ct_expect_tx(bar, bytes * CT_PLANES);
+    __syncwarp();
+    for (int j = lane; j < CT_PLANES; j += 32) {
+      const float* src;
+      if (j < NPOP)
+        src = pin.p32 + (size_t)j * N;
+      else if (j < NPOP + NH)
+        src = hs + (size_t)(j - NPOP) * N;
+      else
+        src = hist + (size_t)(j - NPOP - NH) * N;
+      ct_bulk_load(sbase + (unsigned)(st * CT_STAGE_FLOATS + j * CT_TL) * 4u, src + i0, bytes, bar);
+    }
+  };
+  if (warp == 0) {
+    if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+    if ((int)(blockIdx.x + gridDim.x) < ntiles) issue(blockIdx.x + gridDim.x, 1);
+  }
+  int it = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    const int st = it & 1;
+    const unsigned phase = (unsigned)(it >> 1) & 1u;
+    // one thread waits (bounded) and tells the others, so a timeout is uniform
+    if (threadIdx.x == 0) s_ok = ct_wait(bar0 + 8u * st, phase, CT_WAIT_NS) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok) {
+      // a copy never completed: report it, let the other stage's copies land (bounded),
+      // and leave
+      if (threadIdx.x == 0) {
+        atomicOr(&stats->barrier_error, 1);
+        if (tile + (int)gridDim.x < ntiles)
+          ct_wait(bar0 + 8u * (st ^ 1), (unsigned)((it + 1) >> 1) & 1u, CT_WAIT_NS);
+      }
+      return;
+    }
+    ct_try_wait(bar0 + 8u * st, phase);  // every thread observes the completed phase
+    const int idx = tile * CT_TL + (int)threadIdx.x;
+    if (idx < N) {
+      const int y = idx / k.nx, x = idx - y * k.nx;
+      const SmemSrc src{ct_smem + st * CT_STAGE_FLOATS, (int)threadIdx.x};
+      coupled_node<false>(k, sa, pout, phi_f, hs, hist, ctl, x, y, idx, src);
+    }
+    __syncthreads();  // the stage has been read: it may be refilled
+    const int next = tile + 2 * (int)gridDim.x;
+    if (warp == 0 && next < ntiles) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(next, st);
+    }
+  }
+}
+
+// Whether a lattice takes the staged coupled pass, and its grid (persistent CTAs, as many
+// as fit on the device, at most one per tile).
+bool coupled_staged_ok(const KParams& kp) {
+  return !kp.half && !kp.slab && kp.N % 4 == 0 && kp.N == kp.nint;
+}
+int coupled_staged_grid(const KParams& kp) {
+  static int per_dev[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (!per_dev[dev]) {
+    int sms = 0, per_sm = 0;
+    if (cudaFuncSetAttribute(k_coupled_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)CT_SMEM) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coupled_staged, CT_TL,
+                                                      CT_SMEM) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      return 0;
+    }
+    per_dev[dev] = sms * per_sm;
+  }
+  const int ntiles = (kp.N + CT_TL - 1) / CT_TL;
+  return ntiles < per_dev[dev] ? ntiles : per_dev[dev];
 }
 
 // 128 threads.  The FP32 form (specialised below): at least 7 CTAs per SM (at most
@@ -678,6 +893,12 @@ cudaError_t launch_moments(const KParams& kp, const Buffers& b, int cur, double 
 
 cudaError_t launch_coupled(const KParams& kp, const Buffers& b, int cur, cudaStream_t st) {
   const Pops Pi = pops_copy(kp, b, cur), Po = pops_copy(kp, b, cur ^ 1);
+  const int sg = coupled_staged_ok(kp) ? coupled_staged_grid(kp) : 0;
+  if (sg > 0) {
+    k_coupled_staged<<<sg, CT_TL, CT_SMEM, st>>>(kp, b.ss, cur, Pi, Po, b.phi, b.h, b.hist,
+                                                 b.ctl, b.stats);
+    return cudaGetLastError();
+  }
   if (kp.half)
     k_coupled<true><<<blocks_for(kp.nint, 128), 128, 0, st>>>(kp, b.ss, cur, Pi, Po, b.phi, b.h,
                                                            b.hist, b.ctl, b.stats);
@@ -769,9 +990,17 @@ cudaError_t add_coupled_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t 
   DevStats* stats = b.stats;
   void* args[] = {&k, &ss, &cur, &pin, &pout, &phi, &h, &hist, &ctl, &stats};
   cudaKernelNodeParams p = {};
-  p.func = kp.half ? (void*)k_coupled<true> : (void*)k_coupled<false>;
-  p.gridDim = dim3(blocks_for(kp.nint, 128));
-  p.blockDim = dim3(128);
+  const int sg = coupled_staged_ok(kp) ? coupled_staged_grid(kp) : 0;
+  if (sg > 0) {
+    p.func = (void*)k_coupled_staged;
+    p.gridDim = dim3(sg);
+    p.blockDim = dim3(CT_TL);
+    p.sharedMemBytes = (unsigned)CT_SMEM;
+  } else {
+    p.func = kp.half ? (void*)k_coupled<true> : (void*)k_coupled<false>;
+    p.gridDim = dim3(blocks_for(kp.nint, 128));
+    p.blockDim = dim3(128);
+  }
   p.kernelParams = args;
   return cudaGraphAddKernelNode(out, g, deps, nd, &p);
 }
