@@ -57,10 +57,10 @@ Layout layout_for(const ehd_params& P, int fixed_ty = 0) {
   };
   L.ss = take(sizeof(StepState) * 2);
   if (P.precision == EHD_FP16DEV) {
-    L.pops = take(sizeof(float) * 2 * 3 * (size_t)N);
+    L.pops = take(sizeof(float) * 2 * NP32_HALF * (size_t)N);
     L.pops16 = take(sizeof(__half) * 2 * 24 * (size_t)N);
   } else {
-    L.pops = take(sizeof(float) * 2 * NPOP * (size_t)N);
+    L.pops = take(sizeof(float) * 2 * NP32 * (size_t)N);
     L.pops16 = take(256);
   }
   L.h = take(sizeof(float) * 2 * NH * (size_t)N);
@@ -811,8 +811,8 @@ struct StateHeader {
 };
 
 size_t pop_bytes(const KParams& k) {
-  return k.half ? (sizeof(float) * 3 + sizeof(__half) * 24) * (size_t)k.N
-                : sizeof(float) * NPOP * (size_t)k.N;
+  return k.half ? (sizeof(float) * NP32_HALF + sizeof(__half) * 24) * (size_t)k.N
+                : sizeof(float) * NP32 * (size_t)k.N;
 }
 
 int ehd_state_bytes(const ehd_sim* s, size_t* bytes) {
@@ -843,14 +843,15 @@ int ehd_save_state(ehd_sim* s, void* buf, size_t bytes) {
   const Pops pc = pops_copy(s->kp, s->b, s->cur);
   const float* h = s->b.h + (size_t)s->h_ctl->parity * NH * N;
   if (s->kp.half) {
-    EHD_CUDA(cudaMemcpyAsync(p, pc.p32, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, s->stream));
-    p += sizeof(float) * 3 * N;
+    EHD_CUDA(cudaMemcpyAsync(p, pc.p32, sizeof(float) * NP32_HALF * N, cudaMemcpyDeviceToHost,
+                             s->stream));
+    p += sizeof(float) * NP32_HALF * N;
     EHD_CUDA(cudaMemcpyAsync(p, pc.p16, sizeof(__half) * 24 * N, cudaMemcpyDeviceToHost, s->stream));
     p += sizeof(__half) * 24 * N;
   } else {
-    EHD_CUDA(cudaMemcpyAsync(p, pc.p32, sizeof(float) * NPOP * N, cudaMemcpyDeviceToHost,
+    EHD_CUDA(cudaMemcpyAsync(p, pc.p32, sizeof(float) * NP32 * N, cudaMemcpyDeviceToHost,
                              s->stream));
-    p += sizeof(float) * NPOP * N;
+    p += sizeof(float) * NP32 * N;
   }
   EHD_CUDA(cudaMemcpyAsync(p, h, sizeof(float) * NH * N, cudaMemcpyDeviceToHost, s->stream));
   p += sizeof(float) * NH * N;
@@ -884,14 +885,15 @@ int ehd_load_state(ehd_sim* s, const void* buf, size_t bytes) {
   }
   const Pops pc = pops_copy(s->kp, s->b, 0);
   if (s->kp.half) {
-    EHD_CUDA(cudaMemcpyAsync(pc.p32, p, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, s->stream));
-    p += sizeof(float) * 3 * N;
+    EHD_CUDA(cudaMemcpyAsync(pc.p32, p, sizeof(float) * NP32_HALF * N, cudaMemcpyHostToDevice,
+                             s->stream));
+    p += sizeof(float) * NP32_HALF * N;
     EHD_CUDA(cudaMemcpyAsync(pc.p16, p, sizeof(__half) * 24 * N, cudaMemcpyHostToDevice, s->stream));
     p += sizeof(__half) * 24 * N;
   } else {
-    EHD_CUDA(cudaMemcpyAsync(pc.p32, p, sizeof(float) * NPOP * N, cudaMemcpyHostToDevice,
+    EHD_CUDA(cudaMemcpyAsync(pc.p32, p, sizeof(float) * NP32 * N, cudaMemcpyHostToDevice,
                              s->stream));
-    p += sizeof(float) * NPOP * N;
+    p += sizeof(float) * NP32 * N;
   }
   EHD_CUDA(cudaMemcpyAsync(s->b.h, p, sizeof(float) * NH * N, cudaMemcpyHostToDevice, s->stream));
   p += sizeof(float) * NH * N;

@@ -61,10 +61,10 @@ __global__ void __launch_bounds__(STEADY_THREADS)
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   float a = 0.0f, b = 0.0f, c = 0.0f, d = 0.0f;
   if (idx < N) {
-    float phi = 0.0f, mx = 0.0f, my = 0.0f;
+    const float phi = phi_of<HALF>(k, pops, idx);
+    float mx = 0.0f, my = 0.0f;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-      phi += ld_pop<HALF>(k, pops, 0, i, idx);
       const float fi = ld_pop<HALF>(k, pops, 2, i, idx);
       mx += cx(i) * fi;
       my += cy(i) * fi;

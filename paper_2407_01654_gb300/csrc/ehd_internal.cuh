@@ -5,8 +5,11 @@
 // Weights 4/9, 1/9, 1/36; c_s^2 = 1/3.
 //
 // Device layout of one simulation (N = nx * ny nodes, x fastest):
-//   pops[2][27][N]  post-stream populations g (0..8), l (9..17), f (18..26), two copies
-//                   used alternately (ping-pong);
+//   pops[2][28][N]  post-stream populations g (0..8), l (9..17), f (18..26) and the low
+//                   part of g_0 (27), two copies used alternately (ping-pong).  g_0 (about
+//                   phi) is held as hi + lo so that the small per-step changes of a near
+//                   steady state survive the FP32 spacing of an O(1) value, and phi's
+//                   total is conserved to far below FP32 resolution;
 //   h[2][8][N]      post-stream potential populations h_1..h_8, two copies.  h_0 is not
 //                   stored: it never enters varphi (Eq. weq55), grad varphi (Eq. eqA.16)
 //                   or any other population, so it cannot influence any result;
@@ -30,6 +33,12 @@ namespace ehd {
 
 constexpr int Q9 = 9;
 constexpr int NPOP = 27;   // g, l, f
+// FP32 planes of one population copy: the 27 populations and the low part of g_0 (the
+// Cahn-Hilliard rest population is kept as an unevaluated sum hi + lo of two floats)
+constexpr int NP32 = NPOP + 1;
+// FP32 planes of one copy with FP16-deviation storage: the rest populations of g, l, f
+// and the low part of g_0
+constexpr int NP32_HALF = 4;
 constexpr int NH = 8;      // h_1..h_8
 constexpr int NHIST = 8;
 constexpr int NIO = 9;   // field staging slots: one per ehd_read_fields bit
@@ -108,8 +117,9 @@ struct KParams {
   float ipsc[3];            // 1 / S_f
 };
 
-// One copy of the g, l, f populations.  FP32: p32 = [27][N].  FP16: p32 = rest
-// populations [3][N], p16 = moving populations [24][N].
+// One copy of the g, l, f populations.  FP32: p32 = [28][N] (the 27 populations, then the
+// low part of g_0).  FP16: p32 = rest populations [3][N] and the low part of g_0, p16 =
+// moving populations [24][N].
 struct Pops {
   float* p32;
   __half* p16;
@@ -140,6 +150,49 @@ __device__ __forceinline__ void st_pop(const KParams& k, const Pops& P, int fiel
   } else {
     P.p16[(size_t)(field * 8 + i - 1) * N + idx] = __float2half_rn(v * (k.psc[field] * inv_wgt(i)));
   }
+}
+
+// The low part of the rest Cahn-Hilliard population g_0 = hi + lo (hi is population (0, 0)).
+template <bool HALF>
+__device__ __forceinline__ float ld_g0_lo(const KParams& k, const Pops& P, size_t idx) {
+  return __ldg(P.p32 + (size_t)(HALF ? 3 : NPOP) * k.N + idx);
+}
+template <bool HALF>
+__device__ __forceinline__ void st_g0_lo(const KParams& k, const Pops& P, size_t idx, float v) {
+  P.p32[(size_t)(HALF ? 3 : NPOP) * k.N + idx] = v;
+}
+// Stores a population and returns the value a later ld_pop of it reads (with FP16 storage
+// the rounded value).
+template <bool HALF>
+__device__ __forceinline__ float st_pop_read(const KParams& k, const Pops& P, int field, int i,
+                                             size_t idx, float v) {
+  const size_t N = (size_t)k.N;
+  if (!HALF || i == 0) {
+    st_pop<HALF>(k, P, field, i, idx, v);
+    return v;
+  }
+  const __half hv = __float2half_rn(v * (k.psc[field] * inv_wgt(i)));
+  P.p16[(size_t)(field * 8 + i - 1) * N + idx] = hv;
+  return __half2float(hv) * (k.ipsc[field] * wgt(i));
+}
+// phi = sum_i g_i of a node (Eq. weq49) with g_0 = hi + lo: the moving populations in
+// direction order, the low part, then the high part.  Every kernel forms phi this way.
+template <bool HALF>
+__device__ __forceinline__ float phi_of(const KParams& k, const Pops& P, size_t idx) {
+  float m = 0.0f;
+#pragma unroll
+  for (int i = 1; i < 9; ++i) m = __fadd_rn(m, ld_pop<HALF>(k, P, 0, i, idx));
+  return __fadd_rn(ld_pop<HALF>(k, P, 0, 0, idx), __fadd_rn(m, ld_g0_lo<HALF>(k, P, idx)));
+}
+// (hi, lo) + d as two floats again: Knuth's two-sum of hi and d (exact), the rounding
+// error folded into lo, then one fast two-sum to renormalise.
+__device__ __forceinline__ void two_float_add(float& hi, float& lo, float d) {
+  const float s = __fadd_rn(hi, d);
+  const float bp = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(d, bp));
+  const float l2 = __fadd_rn(lo, e);
+  hi = __fadd_rn(s, l2);
+  lo = __fsub_rn(l2, __fsub_rn(hi, s));
 }
 
 // Values that change from step to step, kept on the device so that a step needs no
@@ -353,7 +406,7 @@ __device__ __forceinline__ void h_change(float vnew, float vold, float& num, flo
 namespace ehd {
 struct Buffers {
   StepState* ss;     // [2]
-  float* pops;       // FP32: [2][27][N]; FP16: [2][3][N] rest populations
+  float* pops;       // FP32: [2][28][N]; FP16: [2][4][N] rest populations and g_0's low part
   __half* pops16;    // FP16: [2][24][N] moving populations
   float* h;          // [2][8][N]
   float* hist;       // [6][N]
@@ -371,10 +424,10 @@ struct Buffers {
 __host__ __device__ inline Pops pops_copy(const KParams& k, const Buffers& b, int c) {
   Pops P;
   if (k.half) {
-    P.p32 = b.pops + (size_t)c * 3 * k.N;
+    P.p32 = b.pops + (size_t)c * NP32_HALF * k.N;
     P.p16 = b.pops16 + (size_t)c * 24 * k.N;
   } else {
-    P.p32 = b.pops + (size_t)c * NPOP * k.N;
+    P.p32 = b.pops + (size_t)c * NP32 * k.N;
     P.p16 = nullptr;
   }
   return P;

@@ -176,6 +176,7 @@ __global__ void k_init(KParams k, const StepState* __restrict__ ss, const float*
     st_pop<HALF>(k, pops, 1, i, idx, wgt(i) * q * (1.0f + 3.0f * cu));
     st_pop<HALF>(k, pops, 2, i, idx, (i == 0 ? (wgt(0) - 1.0f) : wgt(i)) * 3.0f * p + rho * si);
   }
+  st_g0_lo<HALF>(k, pops, idx, 0.0f);
   // potential at equilibrium with the linear wall interpolation (0 when periodic); in a
   // slab, y and ny are those of the whole lattice
   float vlin = 0.0f;
@@ -211,12 +212,10 @@ __device__ __forceinline__ void moments_body(const KParams& k, const StepState* 
   const int off = k.row0 * k.nx;  // stored index of interior node 0
   for (int i0 = bid * blockDim.x + threadIdx.x; i0 < k.nint; i0 += nblk * blockDim.x) {
     const int idx = i0 + off;
-    float phi = 0.0f, q = 0.0f;
+    const float phi = phi_of<HALF>(k, pops, idx);
+    float q = 0.0f;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      phi += ld_pop<HALF>(k, pops, 0, i, idx);
-      q += ld_pop<HALF>(k, pops, 1, i, idx);
-    }
+    for (int i = 0; i < 9; ++i) q += ld_pop<HALF>(k, pops, 1, i, idx);
     q += 0.5f * __ldg(hist + 3 * (size_t)N + idx);
     phi_out[idx] = phi;
     aq[idx] = make_float2(potential_coef(k, phi), q);
@@ -224,56 +223,57 @@ __device__ __forceinline__ void moments_body(const KParams& k, const StepState* 
     phi_acc += phi;
     q_acc += q;
   }
-  // FP32 within a warp, FP64 across warps and CTAs.  Only warp 0 stays for the CTA's
-  // FP64 tail (the FP64 units are slow: the other warps leave at once).
+  // FP32 within a warp, FP64 across warps and CTAs.  Warp 0 forms the CTA's FP64 partial
+  // and takes a ticket; the CTA that takes the last one reduces every CTA's partial with
+  // all its threads (a fixed order: thread t adds partials t, t + 256, ..., then a fixed
+  // tree), the others leave.
   __shared__ float2 s_sum[8];
+  __shared__ double2 s_red[256];
+  __shared__ int s_last;
   const float wp = warp_sum(phi_acc), wq = warp_sum(q_acc);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) s_sum[warp] = make_float2(wp, wq);
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&ctl->nonfinite, 1);
   __syncthreads();
-  if (warp != 0) return;
-  const int nw = (int)(blockDim.x >> 5);
-  double a = 0.0, b = 0.0;
-  if (lane < nw) {
-    a = (double)s_sum[lane].x;
-    b = (double)s_sum[lane].y;
-  }
+  if (warp == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+    double a = 0.0, b = 0.0;
+    if (lane < nw) {
+      a = (double)s_sum[lane].x;
+      b = (double)s_sum[lane].y;
+    }
 #pragma unroll
-  for (int o = 4; o > 0; o >>= 1) {  // fixed tree over the (at most 8) warps
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-  }
-  unsigned t = 0;
-  if (lane == 0) {
-    partials[bid] = make_double2(a, b);
-    __threadfence();
-    t = atomicAdd(&ctl->ticket_m, 1u);
-  }
-  t = __shfl_sync(0xffffffffu, t, 0);
-  if (t != (unsigned)nblk - 1u) return;
-  __threadfence();
-  // last CTA, warp 0: fixed-order FP64 reduction of the per-CTA partials (four
-  // interleaved accumulators per lane, then a fixed shuffle tree)
-  double ra[4] = {0.0, 0.0, 0.0, 0.0}, rb[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int j = lane; j < nblk; j += 128) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (j + 32 * u < nblk) {
-        const double2 v = __ldcg(partials + j + 32 * u);
-        ra[u] += v.x;
-        rb[u] += v.y;
-      }
+    for (int o = 4; o > 0; o >>= 1) {  // fixed tree over the (at most 8) warps
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      partials[bid] = make_double2(a, b);
+      __threadfence();
+      s_last = atomicAdd(&ctl->ticket_m, 1u) == (unsigned)nblk - 1u;
     }
   }
-  double sa = (ra[0] + ra[1]) + (ra[2] + ra[3]);
-  double sb = (rb[0] + rb[1]) + (rb[2] + rb[3]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    sa += __shfl_xor_sync(0xffffffffu, sa, o);
-    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double ra = 0.0, rb = 0.0;
+  for (int j = threadIdx.x; j < nblk; j += blockDim.x) {
+    const double2 v = __ldcg(partials + j);
+    ra += v.x;
+    rb += v.y;
   }
-  if (lane == 0) {
+  s_red[threadIdx.x] = make_double2(ra, rb);
+  __syncthreads();
+  for (int o = (int)blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      const double2 u = s_red[threadIdx.x + o];
+      s_red[threadIdx.x].x += u.x;
+      s_red[threadIdx.x].y += u.y;
+    }
+    __syncthreads();
+  }
+  const double sa = s_red[0].x, sb = s_red[0].y;
+  if (threadIdx.x == 0) {
     // a non-finite phi or q (flagged by any CTA before its ticket) can never satisfy the
     // stopping rule: the solve then makes one sub-iteration and reports not converged,
     // and the call reports EHD_ERR_NONFINITE
@@ -317,9 +317,7 @@ __global__ void __launch_bounds__(256) k_moments(KParams k, const StepState* __r
 // half-way bounce-back; history for the next step.
 // ------------------------------------------------------------------------------------
 // Where the per-node kernel reads the node's post-stream populations, converged potential
-// populations and lagged quantities: device memory (GlobalSrc) or a shared-memory tile
-// staged by bulk copies (SmemSrc, k_coupled_staged).  The arithmetic is the same function
-// for both, so both compute the same bits.
+// populations and lagged quantities (device memory, one node per thread).
 template <bool HALF>
 struct GlobalSrc {
   const KParams& k;
@@ -330,6 +328,7 @@ struct GlobalSrc {
   __device__ __forceinline__ float pop(int field, int i) const {
     return ld_pop<HALF>(k, pin, field, i, idx);
   }
+  __device__ __forceinline__ float g0_lo() const { return ld_g0_lo<HALF>(k, pin, idx); }
   __device__ __forceinline__ float h(int i) const { return __ldg(hs + i * (size_t)k.N + idx); }
   __device__ __forceinline__ float hist_in(int j) const { return hist[j * (size_t)k.N + idx]; }
 };
@@ -465,39 +464,90 @@ __device__ __forceinline__ void coupled_node(const KParams& k, const StepState& 
   const float djx = 3.0f * (Jx - jx_prev), djy = 3.0f * (Jy - jy_prev);
   const float grx = k.drho * gphx, gry = k.drho * gphy;
 
-  // The rest population carries phi, O(1), while a step changes it by far less than its
-  // FP32 spacing; relaxed on its own (g_0 - (g_0 - g_eq_0)/tau_g + ...) it would drop
-  // those increments systematically and phi would drift.  It takes instead the exact
-  // remainder of the collision's phi balance: sum_i g_i* = phi - (3 s - s_prev)/2 (sum_i
-  // g_eq_i = phi, sum_i w_i k_i = -1), so g_0* = phi - (sum_{i>0} g_i* + (3 s - s_prev)/2),
-  // the same value in exact arithmetic, with one unbiased rounding at the scale of phi.
-  float gmov = 0.0f;
+  // The rest population g_0 carries phi, O(1), while a step near a steady state changes
+  // it by far less than its FP32 spacing; it is kept as hi + lo, and its change is the
+  // collision's phi balance: sum_i g_i* = sum_i g_i - (3 s - s_prev)/2 (sum_i g_eq_i =
+  // phi, sum_i w_i k_i = -1), so g_0* - g_0 = sum_{i>0} (g_i - g_i*) - (3 s - s_prev)/2,
+  // the value that relaxing g_0 by Eq. weq45 gives in exact arithmetic, added to hi + lo
+  // without rounding error.  The moving populations enter as stored (with FP16 storage,
+  // rounded), so phi's total over the lattice changes by the source alone.
+  // Per-node coefficients of the three collisions by lattice-weight class (axis, diagonal,
+  // rest), so that a direction costs a few fused multiply-adds:
+  //   g_i* = g_i + om_g (w_i mu - g_i) + w_i k_i gsrc                     (Eq. weq45)
+  //   l_i* = l_i + om_l (l_eq_i - l_i) + pref_l w_i (R + c_i.dJ),
+  //          l_eq_i = w_i q + 3 w_i q (c_i.u)                               (Eqs. weq58-61)
+  //   f_i* = f_i + om_f (f_eq_i - f_i) + 3 pref_f w_i (c_i.F + (c_i.u)(c_i.grad rho)),
+  //          f_eq_i = 3 w_i p + rho w_i ((c_i.u)(3 + 4.5 c_i.u) - 1.5 u.u),  (Eqs. weq38-40)
+  //          with w_0 - 1 in place of w_0 in the pressure term of f_eq_0
+  const float wa = wgt(1), wd = wgt(5), w0 = wgt(0);
+  const float wmu_a = __fmul_rn(wa, mu), wmu_d = __fmul_rn(wd, mu);
+  const float wks_a = __fmul_rn(wa * ch_k(1), gsrc), wks_d = __fmul_rn(wd * ch_k(5), gsrc);
+  const float wq_a = __fmul_rn(wa, q), wq_d = __fmul_rn(wd, q), wq_0 = __fmul_rn(w0, q);
+  const float wq3_a = __fmul_rn(3.0f, wq_a), wq3_d = __fmul_rn(3.0f, wq_d);
+  const float plw_a = __fmul_rn(pref_l, wa), plw_d = __fmul_rn(pref_l, wd);
+  const float plwR_a = __fmul_rn(plw_a, R), plwR_d = __fmul_rn(plw_d, R);
+  const float plwR_0 = __fmul_rn(__fmul_rn(pref_l, w0), R);
+  const float p3 = __fmul_rn(3.0f, p);
+  const float w3p_a = __fmul_rn(wa, p3), w3p_d = __fmul_rn(wd, p3), w3p_0 = __fmul_rn(w0 - 1.0f, p3);
+  const float rw_a = __fmul_rn(rho, wa), rw_d = __fmul_rn(rho, wd), rw_0 = __fmul_rn(rho, w0);
+  const float pf3 = __fmul_rn(3.0f, pref_f);
+  const float pf3w_a = __fmul_rn(pf3, wa), pf3w_d = __fmul_rn(pf3, wd);
+  const float m15uu = __fmul_rn(-1.5f, uu);
+  // c_i.v for the diagonal directions: v_x + v_y and v_x - v_y
+  const float upp = __fadd_rn(ux, uy), upm = __fsub_rn(ux, uy);
+  const float jpp = __fadd_rn(djx, djy), jpm = __fsub_rn(djx, djy);
+  const float Fpp = __fadd_rn(Fx, Fy), Fpm = __fsub_rn(Fx, Fy);
+  const float gpp = __fadd_rn(grx, gry), gpm = __fsub_rn(grx, gry);
+
+  // The rest population g_0 carries phi, O(1), while a step near a steady state changes
+  // it by far less than its FP32 spacing; it is kept as hi + lo, and its change is the
+  // collision's phi balance: sum_i g_i* = sum_i g_i - (3 s - s_prev)/2 (sum_i g_eq_i =
+  // phi, sum_i w_i k_i = -1), so g_0* - g_0 = sum_{i>0} (g_i - g_i*) - (3 s - s_prev)/2,
+  // the value that relaxing g_0 by Eq. weq45 gives in exact arithmetic, added to hi + lo
+  // without rounding error.  The moving populations enter as stored (with FP16 storage,
+  // rounded), so phi's total over the lattice changes by the source alone.
+  float gpre = 0.0f, gmov = 0.0f;
 #pragma unroll
   for (int i0 = 1; i0 < 10; ++i0) {
     const int i = i0 == 9 ? 0 : i0;  // the moving populations first, the rest one last
-    const float w = wgt(i);
-    const float cu = cx(i) * ux + cy(i) * uy;
-    // a6: Cahn-Hilliard, g_eq of Eq. weq46
-    float gn;
-    if (i == 0) {
-      gn = phi - (gmov + gsrc);
-    } else {
-      gn = g[i] - om_g * (g[i] - w * mu) + w * ch_k(i) * gsrc;
-      gmov += gn;
-    }
-    // a7: Nernst-Planck, l_eq of Eq. weq61, S_i + T_i of Eqs. weq59, weq60
-    const float leq = w * q * (1.0f + 3.0f * cu);
-    const float ln = l[i] - om_l * (l[i] - leq) + pref_l * w * (R + cx(i) * djx + cy(i) * djy);
-    // a8: hydrodynamics, f_eq of Eq. weq40, forcing of Eq. weq39 written as
-    // w_i [c_i.F + (c_i.u)(c_i.grad rho)] / c_s^2 (the u.grad rho terms cancel)
-    const float si = w * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
-    const float feq = (i == 0 ? (wgt(0) - 1.0f) : w) * 3.0f * p + rho * si;
-    const float cF = cx(i) * Fx + cy(i) * Fy;
-    const float cg = cx(i) * grx + cy(i) * gry;
-    const float fn = f[i] - om_f * (f[i] - feq) + pref_f * w * 3.0f * (cF + cu * cg);
+    const bool axis = i >= 1 && i <= 4;
+    // c_i.v of the direction (compile-time signs)
+    auto dot = [&](float vx, float vy, float vpp, float vpm) {
+      if (i == 0) return 0.0f;
+      if (axis) return cx(i) != 0 ? (cx(i) > 0 ? vx : -vx) : (cy(i) > 0 ? vy : -vy);
+      if (cx(i) == cy(i)) return cx(i) > 0 ? vpp : -vpp;
+      return cx(i) > 0 ? vpm : -vpm;
+    };
+    const float cu = dot(ux, uy, upp, upm);
     int dir;
     const int t = push_target(k, x, y, i, dir);
-    st_pop<HALF>(k, pout, 0, dir, t, gn);
+    // a6: Cahn-Hilliard, g_eq of Eq. weq46
+    if (i != 0) {
+      const float gn = __fadd_rn(__fmaf_rn(om_g, __fsub_rn(axis ? wmu_a : wmu_d, g[i]), g[i]),
+                                 axis ? wks_a : wks_d);
+      gpre = __fadd_rn(gpre, g[i]);
+      gmov = __fadd_rn(gmov, st_pop_read<HALF>(k, pout, 0, dir, t, gn));
+    } else {
+      float hi = g[0], lo = src.g0_lo();
+      two_float_add(hi, lo, __fsub_rn(__fsub_rn(gpre, gmov), gsrc));
+      st_pop<HALF>(k, pout, 0, 0, t, hi);
+      st_g0_lo<HALF>(k, pout, t, lo);
+    }
+    // a7: Nernst-Planck, l_eq of Eq. weq61, S_i + T_i of Eqs. weq59, weq60
+    const float leq = i == 0 ? wq_0 : __fmaf_rn(axis ? wq3_a : wq3_d, cu, axis ? wq_a : wq_d);
+    const float lsrc = i == 0 ? plwR_0
+                              : __fmaf_rn(axis ? plw_a : plw_d, dot(djx, djy, jpp, jpm),
+                                          axis ? plwR_a : plwR_d);
+    const float ln = __fadd_rn(__fmaf_rn(om_l, __fsub_rn(leq, l[i]), l[i]), lsrc);
+    // a8: hydrodynamics, f_eq of Eq. weq40, forcing of Eq. weq39 written as
+    // w_i [c_i.F + (c_i.u)(c_i.grad rho)] / c_s^2 (the u.grad rho terms cancel)
+    const float core = i == 0 ? m15uu : __fmaf_rn(cu, __fmaf_rn(4.5f, cu, 3.0f), m15uu);
+    const float feq = __fmaf_rn(i == 0 ? rw_0 : (axis ? rw_a : rw_d), core,
+                                i == 0 ? w3p_0 : (axis ? w3p_a : w3p_d));
+    float fn = __fmaf_rn(om_f, __fsub_rn(feq, f[i]), f[i]);
+    if (i != 0)
+      fn = __fmaf_rn(axis ? pf3w_a : pf3w_d,
+                     __fmaf_rn(cu, dot(grx, gry, gpp, gpm), dot(Fx, Fy, Fpp, Fpm)), fn);
     st_pop<HALF>(k, pout, 1, dir, t, ln);
     st_pop<HALF>(k, pout, 2, dir, t, fn);
   }
@@ -528,174 +578,6 @@ __device__ __forceinline__ void coupled_body(const KParams& k, StepState* ss, in
   const float* hs = hbuf + (size_t)parity * NH * k.N;
   const GlobalSrc<HALF> src{k, pin, hs, hist, idx};
   coupled_node<HALF>(k, sa, pout, phi_f, hs, hist, ctl, x, y, idx, src);
-}
-
-// ------------------------------------------------------------------------------------
-// The coupled pass with its per-node inputs staged in shared memory by bulk copies (FP32
-// storage, one lattice, nodes a multiple of 4): persistent CTAs of CT_TL threads walk the
-// lattice in tiles of CT_TL consecutive nodes; each tile's 41 planes (27 populations, 8
-// potential populations, 6 lagged quantities) arrive by cp.async.bulk into one of two
-// stages, completing on that stage's mbarrier, while the CTA computes the previous tile.
-// The number of bytes in flight no longer depends on how many loaded values a thread can
-// hold in registers.  The arithmetic is coupled_node's, so the results are the bits of
-// k_coupled.
-// ------------------------------------------------------------------------------------
-constexpr int CT_TL = 256;
-constexpr int CT_PLANES = NPOP + NH + 6;
-constexpr int CT_STAGE_FLOATS = CT_PLANES * CT_TL;
-constexpr size_t CT_SMEM = 2 * sizeof(float) * CT_STAGE_FLOATS + 2 * sizeof(unsigned long long);
-constexpr unsigned long long CT_WAIT_NS = 2000000000ull;  // 2 s
-
-struct SmemSrc {
-  const float* s;  // the stage: [41][CT_TL]
-  int t;
-  __device__ __forceinline__ float pop(int field, int i) const {
-    return s[(field * 9 + i) * CT_TL + t];
-  }
-  __device__ __forceinline__ float h(int i) const { return s[(NPOP + i) * CT_TL + t]; }
-  __device__ __forceinline__ float hist_in(int j) const { return s[(NPOP + NH + j) * CT_TL + t]; }
-};
-
-__device__ __forceinline__ unsigned long long ct_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void ct_mbar_init(unsigned bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void ct_expect_tx(unsigned bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void ct_bulk_load(unsigned dst, const float* src, unsigned bytes,
-                                             unsigned bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(dst), "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-__device__ __forceinline__ bool ct_try_wait(unsigned bar, unsigned phase) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(bar), "r"(phase)
-      : "memory");
-  return ok != 0;
-}
-// Waits for a stage's copies, giving up after `limit_ns`.
-__device__ __forceinline__ bool ct_wait(unsigned bar, unsigned phase,
-                                        unsigned long long limit_ns) {
-  const unsigned long long t0 = ct_ns();
-  while (!ct_try_wait(bar, phase))
-    if (ct_ns() - t0 > limit_ns) return false;
-  return true;
-}
-
-__global__ void __launch_bounds__(CT_TL, 2)
-    k_coupled_staged(KParams k, StepState* ss, int cur, Pops pin, Pops pout,
-                     const float* __restrict__ phi_f, const float* __restrict__ hbuf,
-                     float* __restrict__ hist, const Ctl* ctl, DevStats* stats) {
-  extern __shared__ __align__(128) float ct_smem[];
-  __shared__ int s_ok;
-  const int N = k.N;
-  const int parity = ld_cg(&ctl->parity);
-  const StepState sa = ss[cur];
-  if (blockIdx.x == 0 && threadIdx.x == 0) coupled_record(k, ss, cur, sa, ctl, stats);
-  const float* hs = hbuf + (size_t)parity * NH * N;
-  const int ntiles = (N + CT_TL - 1) / CT_TL;
-  const unsigned sbase = (unsigned)__cvta_generic_to_shared(ct_smem);
-  const unsigned bar0 = sbase + 2u * sizeof(float) * CT_STAGE_FLOATS;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) {
-    ct_mbar_init(bar0);
-    ct_mbar_init(bar0 + 8);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  // warp 0 queues the 41 plane copies of a tile into a stage: N is a multiple of 4, so
-  // every source and size is a multiple of 16 bytes
-  auto issue = [&](int tile, int st) {
-    const int i0 = tile * CT_TL;
-    const int n = min(CT_TL, N - i0);
-    const unsigned bytes = (unsigned)n * 4u;
-    const unsigned bar = bar0 + 8u * st;
-    if (lane == 0) ct_expect_tx(bar, bytes * CT_PLANES);
-    __syncwarp();
-    for (int j = lane; j < CT_PLANES; j += 32) {
-      const float* src;
-      if (j < NPOP)
-        src = pin.p32 + (size_t)j * N;
-      else if (j < NPOP + NH)
-        src = hs + (size_t)(j - NPOP) * N;
-      else
-        src = hist + (size_t)(j - NPOP - NH) * N;
-      ct_bulk_load(sbase + (unsigned)(st * CT_STAGE_FLOATS + j * CT_TL) * 4u, src + i0, bytes, bar);
-    }
-  };
-  if (warp == 0) {
-    if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
-    if ((int)(blockIdx.x + gridDim.x) < ntiles) issue(blockIdx.x + gridDim.x, 1);
-  }
-  int it = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-    const int st = it & 1;
-    const unsigned phase = (unsigned)(it >> 1) & 1u;
-    // one thread waits (bounded) and tells the others, so a timeout is uniform
-    if (threadIdx.x == 0) s_ok = ct_wait(bar0 + 8u * st, phase, CT_WAIT_NS) ? 1 : 0;
-    __syncthreads();
-    if (!s_ok) {
-      // a copy never completed: report it, let the other stage's copies land (bounded),
-      // and leave
-      if (threadIdx.x == 0) {
-        atomicOr(&stats->barrier_error, 1);
-        if (tile + (int)gridDim.x < ntiles)
-          ct_wait(bar0 + 8u * (st ^ 1), (unsigned)((it + 1) >> 1) & 1u, CT_WAIT_NS);
-      }
-      return;
-    }
-    ct_try_wait(bar0 + 8u * st, phase);  // every thread observes the completed phase
-    const int idx = tile * CT_TL + (int)threadIdx.x;
-    if (idx < N) {
-      const int y = idx / k.nx, x = idx - y * k.nx;
-      const SmemSrc src{ct_smem + st * CT_STAGE_FLOATS, (int)threadIdx.x};
-      coupled_node<false>(k, sa, pout, phi_f, hs, hist, ctl, x, y, idx, src);
-    }
-    __syncthreads();  // the stage has been read: it may be refilled
-    const int next = tile + 2 * (int)gridDim.x;
-    if (warp == 0 && next < ntiles) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(next, st);
-    }
-  }
-}
-
-// Whether a lattice takes the staged coupled pass, and its grid (persistent CTAs, as many
-// as fit on the device, at most one per tile).
-bool coupled_staged_ok(const KParams& kp) {
-  return !kp.half && !kp.slab && kp.N % 4 == 0 && kp.N == kp.nint;
-}
-int coupled_staged_grid(const KParams& kp) {
-  static int per_dev[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
-  if (!per_dev[dev]) {
-    int sms = 0, per_sm = 0;
-    if (cudaFuncSetAttribute(k_coupled_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)CT_SMEM) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coupled_staged, CT_TL,
-                                                      CT_SMEM) != cudaSuccess ||
-        per_sm < 1) {
-      cudaGetLastError();
-      return 0;
-    }
-    per_dev[dev] = sms * per_sm;
-  }
-  const int ntiles = (kp.N + CT_TL - 1) / CT_TL;
-  return ntiles < per_dev[dev] ? ntiles : per_dev[dev];
 }
 
 // 128 threads.  The FP32 form (specialised below): at least 7 CTAs per SM (at most
@@ -780,10 +662,7 @@ __global__ void k_phi_now(KParams k, Pops pops, float* __restrict__ out) {
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (i0 >= k.nint) return;
   const int idx = i0 + k.row0 * k.nx;
-  float s = 0.0f;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) s += ld_pop<HALF>(k, pops, 0, i, idx);
-  out[idx] = s;
+  out[idx] = phi_of<HALF>(k, pops, idx);
 }
 
 template <bool HALF>
@@ -893,12 +772,6 @@ cudaError_t launch_moments(const KParams& kp, const Buffers& b, int cur, double 
 
 cudaError_t launch_coupled(const KParams& kp, const Buffers& b, int cur, cudaStream_t st) {
   const Pops Pi = pops_copy(kp, b, cur), Po = pops_copy(kp, b, cur ^ 1);
-  const int sg = coupled_staged_ok(kp) ? coupled_staged_grid(kp) : 0;
-  if (sg > 0) {
-    k_coupled_staged<<<sg, CT_TL, CT_SMEM, st>>>(kp, b.ss, cur, Pi, Po, b.phi, b.h, b.hist,
-                                                 b.ctl, b.stats);
-    return cudaGetLastError();
-  }
   if (kp.half)
     k_coupled<true><<<blocks_for(kp.nint, 128), 128, 0, st>>>(kp, b.ss, cur, Pi, Po, b.phi, b.h,
                                                            b.hist, b.ctl, b.stats);
@@ -990,17 +863,9 @@ cudaError_t add_coupled_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t 
   DevStats* stats = b.stats;
   void* args[] = {&k, &ss, &cur, &pin, &pout, &phi, &h, &hist, &ctl, &stats};
   cudaKernelNodeParams p = {};
-  const int sg = coupled_staged_ok(kp) ? coupled_staged_grid(kp) : 0;
-  if (sg > 0) {
-    p.func = (void*)k_coupled_staged;
-    p.gridDim = dim3(sg);
-    p.blockDim = dim3(CT_TL);
-    p.sharedMemBytes = (unsigned)CT_SMEM;
-  } else {
-    p.func = kp.half ? (void*)k_coupled<true> : (void*)k_coupled<false>;
-    p.gridDim = dim3(blocks_for(kp.nint, 128));
-    p.blockDim = dim3(128);
-  }
+  p.func = kp.half ? (void*)k_coupled<true> : (void*)k_coupled<false>;
+  p.gridDim = dim3(blocks_for(kp.nint, 128));
+  p.blockDim = dim3(128);
   p.kernelParams = args;
   return cudaGraphAddKernelNode(out, g, deps, nd, &p);
 }

@@ -74,7 +74,9 @@ def test_slabs_equal_single_lattice_bitwise(gpu, case, n):
     assert s2["status"] == 0 and s2["poisson_iters_total"] == s1["poisson_iters_total"]
     for k in ALL_FIELDS:
         assert np.array_equal(a[k], b[k]), k
-    assert s2["sum_phi"] == pytest.approx(s1["sum_phi"], rel=1e-12)
+    # the FP64 phase-mass sum is formed from FP32 per-thread partials, which the slabs
+    # partition differently: equal to FP32 rounding
+    assert s2["sum_phi"] == pytest.approx(s1["sum_phi"], rel=1e-6)
 
 
 def test_slabs_neutralised_source_within_rounding(gpu):
