@@ -286,7 +286,7 @@ def run_gpu(args, rank, world):
     resident = loop_kind in (2, 3, 4)
     rkernel = {3: "k_poisson_resident2", 4: "k_poisson_resident3"}.get(loop_kind, "k_poisson_resident")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    spin = sim.step(SPINUP_STEPS)
+    spin = sim.step(args.spinup)
     sim.step(args.warmup)
     # the state the timed steps start from: the per-kernel profile, the fixed-count
     # comparison and the end-to-end run below start from it too
@@ -436,11 +436,12 @@ def run_gpu(args, rank, world):
         "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": dict(CONFIG),
+        "config": dict(CONFIG, start=f"step 10000 of a 20000-step ramp, then {args.spinup} "
+                                    f"untimed steps"),
         "poisson_iters_mean": kbar,
         "run": {"parallelism": f"replicas x{world}", "contact_angle_deg": round(info["theta"], 2),
                 "storage": "fp32 SoA populations",
-                "spinup_poisson_iters_mean": spin["poisson_iters_total"] / max(SPINUP_STEPS, 1),
+                "spinup_poisson_iters_mean": spin["poisson_iters_total"] / max(args.spinup, 1),
                 "potential_loop": {1: "streaming (one launch per sub-iteration, graph WHILE node)",
                                    2: "on chip (one cooperative launch per step)",
                                    3: "on chip, two sub-iterations per halo exchange (one "
@@ -558,6 +559,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--spinup", type=int, default=SPINUP_STEPS,
+                    help="untimed steps before the warm-up (the workload's start state); "
+                         "profiling captures use fewer to keep the launches before them few")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -593,8 +593,11 @@ __global__ void __launch_bounds__(128) k_coupled(KParams k, StepState* ss, int c
                                                  DevStats* stats) {
   coupled_body<HALF>(k, ss, cur, pin, pout, phi_f, hbuf, hist, ctl, stats, blockIdx.x);
 }
+#ifndef EHD_COUPLED_MIN_CTAS
+#define EHD_COUPLED_MIN_CTAS 7
+#endif
 template <>
-__global__ void __launch_bounds__(128, 7) k_coupled<false>(KParams k, StepState* ss, int cur,
+__global__ void __launch_bounds__(128, EHD_COUPLED_MIN_CTAS) k_coupled<false>(KParams k, StepState* ss, int cur,
                                                            Pops pin, Pops pout,
                                                            const float* __restrict__ phi_f,
                                                            const float* __restrict__ hbuf,
