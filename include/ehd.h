@@ -308,7 +308,8 @@ void ehd_destroy(ehd_sim* sim);
  * all slots share ONE cooperative launch (a tile work-list across slots); each slot keeps
  * its own stopping rule and reaches exactly the state it would reach alone.  After the
  * steps, each slot's relative L2 change of phi and of u since the previous run call is
- * measured; a slot is steady when both are below steady_tol.  Requests that arrive while
+ * measured; a slot is steady when both are below steady_tol, or when phi's is and the
+ * flow is at rest (RMS speed below 1e-6 lattice units).  Requests that arrive while
  * others run are admitted between run calls as slots and memory free up (continuous
  * batching); the scheduling policy is the caller's.
  * --------------------------------------------------------------------------------------- */

@@ -517,10 +517,12 @@ int ehd_batch_run(ehd_batch* b, int nsteps) {
       for (int c = 0; c < 4; ++c) t[c] += parts[i][(size_t)j * 4 + c];
     if (sl.have_snap) {
       sl.rel_phi = t[1] > 0 ? std::sqrt(t[0] / t[1]) : (t[0] > 0 ? INFINITY : 0.0);
-      // velocities below 1e-6 (lattice units) count as rest in the denominator
+      // velocities below 1e-6 (lattice units) count as rest in the denominator, and a flow
+      // whose RMS speed is below that is at rest (steady in u whatever its change)
       const double u_floor2 = 1e-12 * (double)s->kp.N;
       sl.rel_u = std::sqrt(t[2] / std::fmax(t[3], u_floor2));
-      sl.steady = (sl.rel_phi < b->steady_tol && sl.rel_u < b->steady_tol) ? 1 : 0;
+      const bool at_rest = t[3] < u_floor2;
+      sl.steady = (sl.rel_phi < b->steady_tol && (sl.rel_u < b->steady_tol || at_rest)) ? 1 : 0;
     }
     sl.have_snap = 1;
     ehd_stats es;

@@ -197,6 +197,12 @@ __global__ void k_step_set(KParams k, StepState* ss, long long n, int first) {
 // (Eq. weq62 with the lagged R of Algorithm 1).  Writes phi and the per-node potential
 // coefficients; FP64 sums of phi and q; the last CTA resets the potential loop.
 // ------------------------------------------------------------------------------------
+__device__ __forceinline__ void moments_tail(const KParams& k, const StepState* __restrict__ ss,
+                                             double2* __restrict__ partials, Ctl* ctl,
+                                             double tol, int min_iter, int max_iter,
+                                             int fixed_iter, int bid, int nblk, float phi_acc,
+                                             float q_acc, int bad);
+
 // Block `bid` of `nblk` blocks of 256 threads over one simulation.
 template <bool HALF>
 __device__ __forceinline__ void moments_body(const KParams& k, const StepState* __restrict__ ss,
@@ -223,6 +229,16 @@ __device__ __forceinline__ void moments_body(const KParams& k, const StepState* 
     phi_acc += phi;
     q_acc += q;
   }
+  moments_tail(k, ss, partials, ctl, tol, min_iter, max_iter, fixed_iter, bid, nblk, phi_acc,
+               q_acc, bad);
+}
+
+// The reduction of the moments pass: FP32 within a warp, FP64 across warps and CTAs.
+__device__ __forceinline__ void moments_tail(const KParams& k, const StepState* __restrict__ ss,
+                                             double2* __restrict__ partials, Ctl* ctl,
+                                             double tol, int min_iter, int max_iter,
+                                             int fixed_iter, int bid, int nblk, float phi_acc,
+                                             float q_acc, int bad) {
   // FP32 within a warp, FP64 across warps and CTAs.  Warp 0 forms the CTA's FP64 partial
   // and takes a ticket; the CTA that takes the last one reduces every CTA's partial with
   // all its threads (a fixed order: thread t adds partials t, t + 256, ..., then a fixed
@@ -309,6 +325,65 @@ __global__ void __launch_bounds__(256) k_moments(KParams k, const StepState* __r
   moments_body<HALF>(k, ss, pops, hist, phi_out, aq, partials, ctl, tol, min_iter, max_iter,
                      fixed_iter, blockIdx.x, gridDim.x);
 }
+
+// The moments pass for FP32 storage with N a multiple of 4: four consecutive nodes per
+// thread with 16-byte loads, so a thread has its 20 loads in flight at once (the scalar
+// form's grid-stride loop waited on one node's loads before the next).  Per node the
+// arithmetic is moments_body's, in the same order; only the FP32 partial sums group the
+// nodes differently.
+__global__ void __launch_bounds__(256) k_moments4(KParams k, const StepState* __restrict__ ss,
+                                                  Pops pops, const float* __restrict__ hist,
+                                                  float* __restrict__ phi_out,
+                                                  float2* __restrict__ aq,
+                                                  double2* __restrict__ partials, Ctl* ctl,
+                                                  double tol, int min_iter, int max_iter,
+                                                  int fixed_iter) {
+  const size_t N4 = (size_t)k.N / 4;
+  const size_t q4 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float phi_acc = 0.0f, q_acc = 0.0f;
+  int bad = 0;
+  if (q4 < N4) {
+    const float4* P = reinterpret_cast<const float4*>(pops.p32) + q4;
+    float4 g[9], l[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      g[i] = __ldg(P + i * N4);
+      l[i] = __ldg(P + (9 + i) * N4);
+    }
+    const float4 lo = __ldg(P + NPOP * N4);
+    const float4 R = __ldg(reinterpret_cast<const float4*>(hist + 3 * (size_t)k.N) + q4);
+    float ph[4], qq[4];
+    const float* gf = reinterpret_cast<const float*>(g);
+    const float* lf = reinterpret_cast<const float*>(l);
+    const float lov[4] = {lo.x, lo.y, lo.z, lo.w}, Rv[4] = {R.x, R.y, R.z, R.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float m = 0.0f;
+#pragma unroll
+      for (int i = 1; i < 9; ++i) m = __fadd_rn(m, gf[4 * i + c]);
+      ph[c] = __fadd_rn(gf[c], __fadd_rn(m, lov[c]));
+      float q = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) q += lf[4 * i + c];
+      q += 0.5f * Rv[c];
+      qq[c] = q;
+      bad |= !(isfinite(ph[c]) && isfinite(q));
+      phi_acc += ph[c];
+      q_acc += q;
+    }
+    reinterpret_cast<float4*>(phi_out)[q4] = make_float4(ph[0], ph[1], ph[2], ph[3]);
+    float4* a4 = reinterpret_cast<float4*>(aq) + 2 * q4;
+    a4[0] = make_float4(potential_coef(k, ph[0]), qq[0], potential_coef(k, ph[1]), qq[1]);
+    a4[1] = make_float4(potential_coef(k, ph[2]), qq[2], potential_coef(k, ph[3]), qq[3]);
+  }
+  moments_tail(k, ss, partials, ctl, tol, min_iter, max_iter, fixed_iter, blockIdx.x,
+               gridDim.x, phi_acc, q_acc, bad);
+}
+// Whether a lattice takes k_moments4, and its grid.
+static inline bool moments4_ok(const KParams& kp) {
+  return !kp.half && !kp.slab && kp.N % 4 == 0 && kp.N == kp.nint;
+}
+static inline int moments4_blocks(const KParams& kp) { return (kp.N / 4 + 255) / 256; }
 
 // ------------------------------------------------------------------------------------
 // The fused coupled pass (a1, a2, a4-a9): stencils on phi, field from the converged
@@ -764,6 +839,12 @@ cudaError_t launch_moments(const KParams& kp, const Buffers& b, int cur, double 
                            int min_iter, int max_iter, int fixed_iter, cudaStream_t st) {
   const int nb = moments_blocks(kp.nint);
   const Pops P = pops_copy(kp, b, cur);
+  if (moments4_ok(kp)) {
+    k_moments4<<<moments4_blocks(kp), 256, 0, st>>>(kp, b.ss + cur, P, b.hist, b.phi, b.aq,
+                                                    b.partials, b.ctl, tol, min_iter, max_iter,
+                                                    fixed_iter);
+    return cudaGetLastError();
+  }
   if (kp.half)
     k_moments<true><<<nb, 256, 0, st>>>(kp, b.ss + cur, P, b.hist, b.phi, b.aq, b.partials,
                                         b.ctl, tol, min_iter, max_iter, fixed_iter);
@@ -846,8 +927,9 @@ cudaError_t add_moments_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t 
   void* args[] = {&k, &ss, &pops, &hist, &phi, &aq, &partials, &ctl, &tol, &min_iter, &max_iter,
                   &fixed_iter};
   cudaKernelNodeParams p = {};
-  p.func = kp.half ? (void*)k_moments<true> : (void*)k_moments<false>;
-  p.gridDim = dim3(moments_blocks(kp.nint));
+  p.func = moments4_ok(kp) ? (void*)k_moments4
+                           : (kp.half ? (void*)k_moments<true> : (void*)k_moments<false>);
+  p.gridDim = dim3(moments4_ok(kp) ? moments4_blocks(kp) : moments_blocks(kp.nint));
   p.blockDim = dim3(256);
   p.kernelParams = args;
   return cudaGraphAddKernelNode(out, g, deps, nd, &p);

@@ -188,6 +188,7 @@ class OneAtATime:
         self.steps = 0
         self.prev = None
         self.rel = (math.inf, math.inf)
+        self.at_rest = False
 
     def admit(self, params, fields, rid):
         if self.sim is not None:
@@ -205,6 +206,7 @@ class OneAtATime:
         self.iters = 0
         self.prev = None
         self.rel = (math.inf, math.inf)
+        self.at_rest = False
         return 0
 
     def _snap(self):
@@ -226,12 +228,15 @@ class OneAtATime:
             self.rel = (float(np.linalg.norm(phi - p0) / max(np.linalg.norm(phi), 1e-300)),
                         float(np.linalg.norm(u - u0) / max(np.linalg.norm(u), u_floor)))
         self.prev = (phi, u)
+        self.at_rest = bool(np.sqrt(np.mean(np.sum(u * u, axis=0))) < 1e-6)
         return 0
 
     def poll(self):
         if self.sim is None:
             return []
-        steady = self.rel[0] < self.tol and self.rel[1] < self.tol
+        # the batch's rule: phi's relative change below the tolerance, and u's too unless
+        # the flow is at rest (RMS speed below 1e-6 lattice units)
+        steady = self.rel[0] < self.tol and (self.rel[1] < self.tol or self.at_rest)
         return [dict(slot=0, live=1, request_id=self.rid, steps=self.steps, poisson_iters=self.iters,
                      steady=int(steady), capped=int(self.steps >= self.cap), status=0,
                      rel_change_phi=self.rel[0], rel_change_u=self.rel[1])]
