@@ -730,33 +730,38 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
   auto valid = [&](int s) { return ly0 + s * T::ROWS < nrows; };
   auto bw = [&](int s) { return k.walls && ty0 + ly0 + s * T::ROWS == 0; };
   auto tw_ = [&](int s) { return k.walls && ty0 + ly0 + s * T::ROWS == ny - 1; };
+  // every load of the thread's four nodes is issued before any is used (a node outside the
+  // lattice loads node 0 and then starts from zero), so the prologue waits for one round
+  // trip to memory instead of four
+  float2 c[NPT];
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
-    const int ly = ly0 + s * T::ROWS;
-    float v[8];
-    float a = 0.0f, q = 0.0f;
-    if (valid(s)) {
-      const int g = (ty0 + ly) * nx + tx0 + lx;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = hsrc[i * N + g];
-      const float2 c = aq[g];
-      a = c.x;
-      q = __fsub_rn(c.y, qshift);
-      if (CONV) q = __fmul_rn(q, k.inv_chi);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = 0.0f;
-    }
-    if (valid(s)) {  // a node outside the lattice may sit on a ring node's cell
-      ca[at0 + s * T::ROWS * PXF] = a;
-      cq[at0 + s * T::ROWS * PXF] = q;
-    }
+    const int g = valid(s) ? (ty0 + ly0 + s * T::ROWS) * nx + tx0 + lx : 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
+      const float v = hsrc[i * N + g];
       if (s & 1)
-        h[s >> 1][i].y = v[i];
+        h[s >> 1][i].y = v;
       else
-        h[s >> 1][i].x = v[i];
+        h[s >> 1][i].x = v;
+    }
+    c[s] = aq[g];
+  }
+#pragma unroll
+  for (int s = 0; s < NPT; ++s) {
+    if (valid(s)) {  // a node outside the lattice may sit on a ring node's cell
+      float q = __fsub_rn(c[s].y, qshift);
+      if (CONV) q = __fmul_rn(q, k.inv_chi);
+      ca[at0 + s * T::ROWS * PXF] = c[s].x;
+      cq[at0 + s * T::ROWS * PXF] = q;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (s & 1)
+          h[s >> 1][i].y = 0.0f;
+        else
+          h[s >> 1][i].x = 0.0f;
+      }
     }
   }
   __syncthreads();
