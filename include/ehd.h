@@ -160,10 +160,13 @@ typedef struct ehd_stats {
   int64_t kernel_launches;      /* CUDA kernel launches the call queued                  */
 } ehd_stats;
 
-/* Device time per kernel kind, from CUDA events recorded around each launch on the
- * simulation's stream while profiling is on.  Kinds: 0 moments, 1 potential
- * sub-iteration, 2 potential launches queued after the loop had finished (they return at
- * once), 3 coupled collide-and-push. */
+/* Device time per kernel kind while profiling is on.  Steps launched as graphs use a
+ * profiling form of the step graph with event-record nodes around the moments pass, the
+ * potential loop and the coupled pass (one "launch" per part and step, the loop counted
+ * whole); steps queued from the host (ehd_use_graphs(0)) record CUDA events around every
+ * launch on the simulation's stream.  Kinds: 0 moments, 1 potential loop, 2 potential
+ * launches queued after the loop had finished (they return at once; host-queued streaming
+ * loop only), 3 coupled collide-and-push. */
 typedef struct ehd_kernel_times {
   double ms[4];
   int64_t launches[4];
@@ -245,9 +248,10 @@ int ehd_state_bytes(const ehd_sim* sim, size_t* bytes);
 int ehd_save_state(ehd_sim* sim, void* buf, size_t bytes);
 int ehd_load_state(ehd_sim* sim, const void* buf, size_t bytes);
 
-/* Per-launch event timing: ehd_profile(sim, 1) clears the totals and starts recording,
- * ehd_profile(sim, 0) stops; ehd_profile_read synchronises the stream and returns the
- * totals since profiling was turned on. */
+/* Kernel timing (ehd_kernel_times): ehd_profile(sim, 1) clears the totals and starts
+ * recording, ehd_profile(sim, 0) stops; ehd_profile_read synchronises the stream and
+ * returns the totals since profiling was turned on.  Profiled graph steps synchronise the
+ * stream after each step. */
 int ehd_profile(ehd_sim* sim, int enable);
 int ehd_profile_read(ehd_sim* sim, ehd_kernel_times* out);
 

@@ -308,10 +308,45 @@ void destroy_graphs(ehd_sim* s) {
   for (int c = 0; c < 2; ++c) {
     if (s->exec[c]) cudaGraphExecDestroy(s->exec[c]);
     if (s->graph[c]) cudaGraphDestroy(s->graph[c]);
+    if (s->pexec[c]) cudaGraphExecDestroy(s->pexec[c]);
     s->exec[c] = nullptr;
     s->graph[c] = nullptr;
+    s->pexec[c] = nullptr;
   }
   s->graphs_ok = false;
+  s->pgraphs_ok = false;
+  s->pgraphs_tried = false;
+}
+
+// The profiling form of the step graphs: event-record nodes before the moments pass and
+// after each part, so the per-kernel times come from the graph's own execution.
+void ensure_prof_graphs(ehd_sim* s) {
+  if (s->pgraphs_tried) return;
+  s->pgraphs_tried = true;
+  const ehd_params& P = s->P;
+  for (int j = 0; j < 4; ++j)
+    if (!s->pev[j] && cudaEventCreate(&s->pev[j]) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+  for (int c = 0; c < 2; ++c) {
+    cudaGraph_t g = nullptr;
+    const bool ok =
+        build_step_graph(s->kp, s->b, c, P.poisson_tol, P.poisson_min_iter, P.poisson_max_iter,
+                         P.poisson_fixed_iter, s->resident_ok ? &s->rg : nullptr, s->rthreads,
+                         s->rsmem, &g, s->pev) == cudaSuccess &&
+        cudaGraphInstantiate(&s->pexec[c], g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+      cudaGetLastError();
+      for (int d = 0; d < 2; ++d) {
+        if (s->pexec[d]) cudaGraphExecDestroy(s->pexec[d]);
+        s->pexec[d] = nullptr;
+      }
+      return;
+    }
+  }
+  s->pgraphs_ok = true;
 }
 
 // Builds the two step graphs once.  If the driver refuses (e.g. no conditional nodes),
@@ -605,6 +640,8 @@ void ehd_destroy(ehd_sim* s) {
   cudaStreamSynchronize(s->stream);
   destroy_graphs(s);
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : s->pev)
+    if (e) cudaEventDestroy(e);
   if (s->own_ws && s->ws) cudaFree(s->ws);
   if (s->h_ctl) cudaFreeHost(s->h_ctl);
   if (s->h_stats) cudaFreeHost(s->h_stats);
@@ -704,11 +741,25 @@ int ehd_step(ehd_sim* s, int nsteps, ehd_stats* out) {
     if (reset_stats(s) != EHD_OK) return EHD_ERR_CUDA;
     s->stats_live = true;
   }
-  if (!s->profiling && !s->no_graphs) ensure_graphs(s);
+  if (!s->no_graphs) ensure_graphs(s);
+  if (s->profiling && s->graphs_ok && !s->no_graphs) ensure_prof_graphs(s);
   for (int k = 0; k < nsteps; ++k) {
     // an armed diagnostic runs its step from the host (the graph has no slot for it)
-    const bool use_graphs = s->graphs_ok && !s->profiling && !s->expire_barrier && !s->no_graphs;
-    if (use_graphs) {
+    const bool use_graphs = s->graphs_ok && !s->expire_barrier && !s->no_graphs &&
+                            (!s->profiling || s->pgraphs_ok);
+    if (use_graphs && s->profiling) {
+      // the profiling graph: the step's three parts timed by its own event nodes
+      EHD_CUDA(cudaGraphLaunch(s->pexec[s->cur], s->stream));
+      EHD_CUDA(cudaEventSynchronize(s->pev[3]));
+      const int kinds[3] = {0, 1, 3};
+      for (int j = 0; j < 3; ++j) {
+        float ms = 0.0f;
+        EHD_CUDA(cudaEventElapsedTime(&ms, s->pev[j], s->pev[j + 1]));
+        s->prof_ms[kinds[j]] += ms;
+        s->prof_n[kinds[j]] += 1;
+      }
+      s->graph_steps += 1;
+    } else if (use_graphs) {
       // the whole step, potential loop included, without returning to the host
       EHD_CUDA(cudaGraphLaunch(s->exec[s->cur], s->stream));
       s->graph_steps += 1;

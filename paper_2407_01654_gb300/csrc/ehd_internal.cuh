@@ -514,7 +514,10 @@ cudaError_t add_coupled_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t 
 // graph is launched unchanged every step.
 // With `rg` non-null the potential loop is the single resident cooperative kernel instead
 // of the WHILE node.
+// With `ev` (4 events) the graph records ev[0] before the moments pass, ev[1] after it,
+// ev[2] after the potential loop and ev[3] after the coupled pass (per-kernel timing).
 cudaError_t build_step_graph(const KParams& kp, const Buffers& b, int cur, double tol,
                              int min_iter, int max_iter, int fixed_iter, const ResidentGeom* rg,
-                             int rthreads, size_t rsmem, cudaGraph_t* out);
+                             int rthreads, size_t rsmem, cudaGraph_t* out,
+                             const cudaEvent_t* ev = nullptr);
 }  // namespace ehd

@@ -984,44 +984,67 @@ cudaError_t add_poisson_node(cudaGraph_t g, cudaGraphNode_t* out, const KParams&
 
 cudaError_t build_step_graph(const KParams& kp, const Buffers& b, int cur, double tol,
                              int min_iter, int max_iter, int fixed_iter, const ResidentGeom* rg,
-                             int rthreads, size_t rsmem, cudaGraph_t* out) {
+                             int rthreads, size_t rsmem, cudaGraph_t* out,
+                             const cudaEvent_t* ev) {
   cudaGraph_t g;
   cudaError_t e = cudaGraphCreate(&g, 0);
   if (e != cudaSuccess) return e;
-  cudaGraphNode_t mn, wn, pn, cn;
-  if (rg) {
-    if ((e = add_moments_node(g, nullptr, 0, &mn, kp, b, cur, tol, min_iter, max_iter,
-                              fixed_iter)) != cudaSuccess ||
-        (e = add_poisson_resident_node(g, &mn, 1, &pn, kp, *rg, rthreads, rsmem, b)) !=
-            cudaSuccess ||
-        (e = add_coupled_node(g, &pn, 1, &cn, kp, b, cur)) != cudaSuccess) {
+  // the nodes in order, each depending on the previous one; with events, a record node
+  // before the moments pass and after each of the three parts of the step
+  cudaGraphNode_t last = nullptr;
+  bool have = false;
+  auto record = [&](int j) -> cudaError_t {
+    if (!ev) return cudaSuccess;
+    cudaGraphNode_t n;
+    const cudaError_t r = cudaGraphAddEventRecordNode(&n, g, have ? &last : nullptr, have ? 1 : 0,
+                                                      ev[j]);
+    if (r == cudaSuccess) {
+      last = n;
+      have = true;
+    }
+    return r;
+  };
+  auto done = [&](cudaError_t r) {
+    if (r != cudaSuccess) {
       cudaGraphDestroy(g);
-      return e;
+      return r;
     }
     *out = g;
     return cudaSuccess;
+  };
+  cudaGraphNode_t mn, wn, pn, cn;
+  if ((e = record(0)) != cudaSuccess ||
+      (e = add_moments_node(g, have ? &last : nullptr, have ? 1 : 0, &mn, kp, b, cur, tol,
+                            min_iter, max_iter, fixed_iter)) != cudaSuccess)
+    return done(e);
+  last = mn;
+  have = true;
+  if ((e = record(1)) != cudaSuccess) return done(e);
+  if (rg) {
+    if ((e = add_poisson_resident_node(g, &last, 1, &pn, kp, *rg, rthreads, rsmem, b)) !=
+        cudaSuccess)
+      return done(e);
+    last = pn;
+  } else {
+    cudaGraphConditionalHandle h;
+    if ((e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault)) !=
+        cudaSuccess)
+      return done(e);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&wn, g, &last, nullptr, 1, &cp)) != cudaSuccess ||
+        (e = add_poisson_node(cp.conditional.phGraph_out[0], &pn, kp, b, h)) != cudaSuccess)
+      return done(e);
+    last = wn;
   }
-  cudaGraphConditionalHandle h;
-  if ((e = add_moments_node(g, nullptr, 0, &mn, kp, b, cur, tol, min_iter, max_iter,
-                            fixed_iter)) != cudaSuccess ||
-      (e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault)) !=
-          cudaSuccess) {
-    cudaGraphDestroy(g);
-    return e;
-  }
-  cudaGraphNodeParams cp = {};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = h;
-  cp.conditional.type = cudaGraphCondTypeWhile;
-  cp.conditional.size = 1;
-  if ((e = cudaGraphAddNode(&wn, g, &mn, nullptr, 1, &cp)) != cudaSuccess ||
-      (e = add_poisson_node(cp.conditional.phGraph_out[0], &pn, kp, b, h)) != cudaSuccess ||
-      (e = add_coupled_node(g, &wn, 1, &cn, kp, b, cur)) != cudaSuccess) {
-    cudaGraphDestroy(g);
-    return e;
-  }
-  *out = g;
-  return cudaSuccess;
+  if ((e = record(2)) != cudaSuccess ||
+      (e = add_coupled_node(g, &last, 1, &cn, kp, b, cur)) != cudaSuccess)
+    return done(e);
+  last = cn;
+  return done(record(3));
 }
 
 }  // namespace ehd

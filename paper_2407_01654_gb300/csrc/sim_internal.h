@@ -44,6 +44,11 @@ struct ehd_sim {
   bool no_graphs = false;     // steps queued kernel by kernel from the host (ehd_use_graphs)
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  // the same step graphs with event-record nodes around the three parts, for profiling
+  bool pgraphs_tried = false;
+  bool pgraphs_ok = false;
+  cudaGraphExec_t pexec[2] = {nullptr, nullptr};
+  cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
   // resident (on-chip) potential loop, when the lattice fits
   bool resident_ok = false;
   ResidentGeom rg{};

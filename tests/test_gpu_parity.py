@@ -257,27 +257,36 @@ def test_deterministic(gpu):
     assert out[0][1]["sum_q"] == out[1][1]["sum_q"]
 
 
-def test_graph_and_host_loop_agree(gpu):
-    """The step graph (WHILE node around the potential kernel) and the host-driven loop
-    used while profiling run the same kernels: bitwise equal results and equal K."""
-    p, f = droplet_box(64, 48, 10.0, seed=11)
+@pytest.mark.parametrize("loop", [pytest.param(1, id="stream"), pytest.param(3, id="resident2")])
+def test_graph_and_host_loop_agree(gpu, loop):
+    """The step graph (WHILE node around the streaming potential kernel, or the on-chip
+    loop's one launch), its profiling form (event-record nodes around the three parts)
+    and the host-driven loop (ehd_use_graphs(0), CUDA events around every launch) run the
+    same kernels: bitwise equal results and equal K; the profiles count one potential part
+    per step in the graphs and one launch per sub-iteration on the host."""
+    p, f = droplet_box(64, 48, 10.0, seed=11, poisson_loop=loop)
     a = gpu.Sim(p)
     a.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
     sa = a.step(25)
-    b = gpu.Sim(p)
-    b.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
-    b.profile(True)
-    sb = b.step(25)
-    prof = b.profile_read()
-    assert sa["poisson_iters_total"] == sb["poisson_iters_total"]
-    if b.uses_resident_loop():
-        assert prof["potential"]["launches"] == 25
-    else:
-        assert prof["potential"]["launches"] == sb["poisson_iters_total"]
-    assert prof["coupled"]["launches"] == 25
-    fa, fb = a.read_fields(), b.read_fields()
-    for k in ALL_FIELDS:
-        assert np.array_equal(fa[k], fb[k]), k
+    fa = a.read_fields()
+    for host in (False, True):
+        b = gpu.Sim(p)
+        b.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
+        if host:
+            b.use_graphs(False)
+        b.profile(True)
+        sb = b.step(25)
+        prof = b.profile_read()
+        assert sa["poisson_iters_total"] == sb["poisson_iters_total"]
+        if host and not b.uses_resident_loop():
+            assert prof["potential"]["launches"] == sb["poisson_iters_total"]
+        else:
+            assert prof["potential"]["launches"] == 25
+        assert prof["coupled"]["launches"] == 25 and prof["moments"]["launches"] == 25
+        assert all(prof[k]["ms"] > 0 for k in ("moments", "potential", "coupled"))
+        fb = b.read_fields()
+        for k in ALL_FIELDS:
+            assert np.array_equal(fa[k], fb[k]), k
 
 
 @pytest.mark.parametrize("fixed", [7, 8, 9])
