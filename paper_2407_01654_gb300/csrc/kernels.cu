@@ -25,6 +25,21 @@ __device__ __forceinline__ float ghost(float v, float a_cos) { return v + a_cos 
 __device__ __forceinline__ Stencil load_stencil(const KParams& k, const StepState& sa,
                                                 const float* __restrict__ phi, int x, int y) {
   const int nx = k.nx, ny = k.ny;
+  if (x > 0 && x + 1 < nx && y > 0 && y + 1 < ny) {
+    // away from every edge: the 3 x 3 neighbourhood at fixed offsets
+    const float* r = phi + (size_t)(y + k.row0) * nx + x;
+    Stencil s;
+    s.c = __ldg(r);
+    s.e = __ldg(r + 1);
+    s.w = __ldg(r - 1);
+    s.n = __ldg(r + nx);
+    s.ne = __ldg(r + nx + 1);
+    s.nw = __ldg(r + nx - 1);
+    s.s = __ldg(r - nx);
+    s.se = __ldg(r - nx + 1);
+    s.sw = __ldg(r - nx - 1);
+    return s;
+  }
   const int xm = x == 0 ? nx - 1 : x - 1;
   const int xp = x + 1 == nx ? 0 : x + 1;
   Stencil s;
@@ -582,6 +597,7 @@ __device__ __forceinline__ void coupled_node(const KParams& k, const StepState& 
   // without rounding error.  The moving populations enter as stored (with FP16 storage,
   // rounded), so phi's total over the lattice changes by the source alone.
   float gpre = 0.0f, gmov = 0.0f;
+  const bool inner = x > 0 && x + 1 < k.nx && y > 0 && y + 1 < k.ny;
 #pragma unroll
   for (int i0 = 1; i0 < 10; ++i0) {
     const int i = i0 == 9 ? 0 : i0;  // the moving populations first, the rest one last
@@ -594,8 +610,10 @@ __device__ __forceinline__ void coupled_node(const KParams& k, const StepState& 
       return cx(i) > 0 ? vpm : -vpm;
     };
     const float cu = dot(ux, uy, upp, upm);
-    int dir;
-    const int t = push_target(k, x, y, i, dir);
+    // away from every edge a population lands at a fixed offset; at an edge the wrap, wall
+    // or cut rule of push_target applies
+    int dir = i;
+    const int t = inner ? idx + cx(i) + cy(i) * k.nx : push_target(k, x, y, i, dir);
     // a6: Cahn-Hilliard, g_eq of Eq. weq46
     if (i != 0) {
       const float gn = __fadd_rn(__fmaf_rn(om_g, __fsub_rn(axis ? wmu_a : wmu_d, g[i]), g[i]),
