@@ -51,8 +51,8 @@ K_COMPARE = 5
 # The workload as both arms name it (identical in the GPU and the reference line).
 CONFIG = {"workload": WORKLOAD, "nodes": 512 * 1024,
           "start": f"step 10000 of a 20000-step ramp, then {SPINUP_STEPS} untimed steps",
-          "l2": "inputs (about 175 MB of populations and fields) larger than L2; L2 also "
-                "flushed between timed steps by a 512 MiB device write outside the events"}
+          "l2": "inputs larger than L2: the simulation state is about 175 MB and a step "
+                "touches about 150 MB (L2 129 MB); steps run back to back, L2 not flushed"}
 # algorithmic bytes per node (FP32 populations read once and written once per pass):
 # coupled pass: 27 populations read + written (216 B) + 6 lagged quantities read + written
 # (48 B) + the 8 converged potential populations its local field needs (32 B) + phi for
@@ -69,7 +69,6 @@ FLOPS_POTENTIAL = 96
 # and export band traffic on top of it is overhead, not counted
 SMEM_BYTES_POTENTIAL = 64
 SM_MAX_MHZ = 2070.0
-L2_FLUSH_BYTES = 512 << 20
 
 
 def workload(seed=0):
@@ -285,7 +284,6 @@ def run_gpu(args, rank, world):
     loop_kind = sim.loop_kind()
     resident = loop_kind in (2, 3, 4)
     rkernel = {3: "k_poisson_resident2", 4: "k_poisson_resident3"}.get(loop_kind, "k_poisson_resident")
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     spin = sim.step(args.spinup)
     sim.step(args.warmup)
     # the state the timed steps start from: the per-kernel profile, the fixed-count
@@ -293,17 +291,16 @@ def run_gpu(args, rank, world):
     start_state = sim.save_state()
 
     def timed_steps(s, n):
-        """n steps as step graphs, L2 flushed before each, CUDA events around each step on
-        the stream the library uses; returns the summed step time in ms."""
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
-        for j in range(n):
-            flush.fill_(j & 0xff)
-            starts[j].record(stream)
-            s.step(1, stats=False)
-            ends[j].record(stream)
+        """n steps as step graphs, back to back, between two CUDA events on the stream the
+        library uses (synchronised on both sides); returns the time in ms."""
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+        t0.record(stream)
+        s.step(n, stats=False)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1)
 
     if world > 1:
         torch.distributed.barrier()
