@@ -656,7 +656,7 @@ int ehd_solve_potential(ehd_sim* s, double tol, int max_iter, int* iters, double
   const int mx = max_iter > 0 ? max_iter : P.poisson_max_iter;
   const int fixed = (tol > 0 || max_iter > 0) ? 0 : P.poisson_fixed_iter;
   EHD_LAUNCH(s, 0, launch_moments(s->kp, s->b, s->cur, t, P.poisson_min_iter, mx, fixed,
-                                   s->stream));
+                                   s->stream, s->resident_ok));
   int st = run_potential_loop(s, fixed, mx);
   if (st == EHD_ERR_CUDA) return st;
   EHD_CUDA(cudaMemcpyAsync(s->h_ctl, s->b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s->stream));
@@ -765,7 +765,8 @@ int ehd_step(ehd_sim* s, int nsteps, ehd_stats* out) {
       s->graph_steps += 1;
     } else {
       EHD_LAUNCH(s, 0, launch_moments(s->kp, s->b, s->cur, P.poisson_tol, P.poisson_min_iter,
-                                       P.poisson_max_iter, P.poisson_fixed_iter, s->stream));
+                                       P.poisson_max_iter, P.poisson_fixed_iter, s->stream,
+                                       s->resident_ok));
       const int st = run_potential_loop(s, P.poisson_fixed_iter, P.poisson_max_iter);
       if (st == EHD_ERR_CUDA || st == EHD_ERR_TIMEOUT) return st;
       if (st != EHD_OK) status = st;

@@ -251,6 +251,9 @@ struct Ctl {
                             // the current solve (reset with the loop control)
   int bar_error;            // a barrier wait timed out (sticky)
   double slab_num, slab_den;// one slab's stopping sums of its last sub-iteration
+  int mpart_n;              // > 0: the moments pass left its FP64 sums as this many
+                            // per-CTA partials, reduced by the coupled pass
+  int pad2;
 };
 
 // Tiling of the resident potential loop: ntx x nty tiles of TX x TY nodes (the last
@@ -488,8 +491,11 @@ cudaError_t launch_step_set(const KParams& kp, const Buffers& b, int slot, long 
                             int first, cudaStream_t st);
 cudaError_t launch_init(const KParams& kp, const Buffers& b, int cur, bool have_p,
                         cudaStream_t st);
+// sums_in_coupled: the potential loop that follows runs on chip, so (without a neutralised
+// source) the moments pass may leave its FP64 sums as per-CTA partials for the coupled pass.
 cudaError_t launch_moments(const KParams& kp, const Buffers& b, int cur, double tol,
-                           int min_iter, int max_iter, int fixed_iter, cudaStream_t st);
+                           int min_iter, int max_iter, int fixed_iter, cudaStream_t st,
+                           bool sums_in_coupled = false);
 cudaError_t launch_poisson(const KParams& kp, const Buffers& b, cudaStream_t st);
 cudaError_t launch_coupled(const KParams& kp, const Buffers& b, int cur, cudaStream_t st);
 cudaError_t launch_stats_reset(const Buffers& b, cudaStream_t st);
@@ -505,7 +511,8 @@ cudaError_t add_poisson_node_nocond(cudaGraph_t g, const cudaGraphNode_t* deps, 
 // Graph nodes of the per-step kernels (argument values are copied into the node).
 cudaError_t add_moments_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
                              cudaGraphNode_t* out, const KParams& kp, const Buffers& b, int cur,
-                             double tol, int min_iter, int max_iter, int fixed_iter);
+                             double tol, int min_iter, int max_iter, int fixed_iter,
+                             bool sums_in_coupled = false);
 cudaError_t add_coupled_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
                              cudaGraphNode_t* out, const KParams& kp, const Buffers& b, int cur);
 

@@ -324,7 +324,54 @@ __device__ __forceinline__ void moments_tail(const KParams& k, const StepState* 
     ctl->vw_t = ss->vw_t;
     ctl->ticket_m = 0u;
     ctl->bar_count = 0u;
+    ctl->mpart_n = 0;
     __threadfence();
+  }
+}
+
+// The moments pass without the cross-CTA reduction (an on-chip potential loop without a
+// neutralised source needs neither the mean charge nor the sums before it runs): each CTA
+// leaves its FP64 partial, the coupled pass reduces them for the statistics, and block 0
+// sets the loop control.  (A non-finite flag is applied by the loop itself.)
+__device__ __forceinline__ void moments_partial_only(const KParams& k,
+                                                     const StepState* __restrict__ ss,
+                                                     double2* __restrict__ partials, Ctl* ctl,
+                                                     double tol, int min_iter, int max_iter,
+                                                     int fixed_iter, int bid, int nblk,
+                                                     float phi_acc, float q_acc, int bad) {
+  __shared__ float2 s_sum[8];
+  const float wp = warp_sum(phi_acc), wq = warp_sum(q_acc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) s_sum[warp] = make_float2(wp, wq);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&ctl->nonfinite, 1);
+  __syncthreads();
+  if (warp != 0) return;
+  const int nw = (int)(blockDim.x >> 5);
+  double a = 0.0, b = 0.0;
+  if (lane < nw) {
+    a = (double)s_sum[lane].x;
+    b = (double)s_sum[lane].y;
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {  // the same fixed tree as moments_tail
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) partials[bid] = make_double2(a, b);
+  if (bid == 0 && lane == 0) {
+    ctl->iter = 0;
+    ctl->done = 0;
+    ctl->converged = 0;
+    ctl->rel = 0.0;
+    ctl->tol = tol;
+    ctl->min_iter = min_iter;
+    ctl->max_iter = max_iter;
+    ctl->fixed_iter = fixed_iter;
+    ctl->vw_b = ss->vw_b;
+    ctl->vw_t = ss->vw_t;
+    ctl->ticket_m = 0u;
+    ctl->bar_count = 0u;
+    ctl->mpart_n = nblk;
   }
 }
 
@@ -346,6 +393,7 @@ __global__ void __launch_bounds__(256) k_moments(KParams k, const StepState* __r
 // form's grid-stride loop waited on one node's loads before the next).  Per node the
 // arithmetic is moments_body's, in the same order; only the FP32 partial sums group the
 // nodes differently.
+template <bool TAIL>
 __global__ void __launch_bounds__(256) k_moments4(KParams k, const StepState* __restrict__ ss,
                                                   Pops pops, const float* __restrict__ hist,
                                                   float* __restrict__ phi_out,
@@ -391,8 +439,12 @@ __global__ void __launch_bounds__(256) k_moments4(KParams k, const StepState* __
     a4[0] = make_float4(potential_coef(k, ph[0]), qq[0], potential_coef(k, ph[1]), qq[1]);
     a4[1] = make_float4(potential_coef(k, ph[2]), qq[2], potential_coef(k, ph[3]), qq[3]);
   }
-  moments_tail(k, ss, partials, ctl, tol, min_iter, max_iter, fixed_iter, blockIdx.x,
-               gridDim.x, phi_acc, q_acc, bad);
+  if (TAIL)
+    moments_tail(k, ss, partials, ctl, tol, min_iter, max_iter, fixed_iter, blockIdx.x,
+                 gridDim.x, phi_acc, q_acc, bad);
+  else
+    moments_partial_only(k, ss, partials, ctl, tol, min_iter, max_iter, fixed_iter, blockIdx.x,
+                         gridDim.x, phi_acc, q_acc, bad);
 }
 // Whether a lattice takes k_moments4, and its grid.
 static inline bool moments4_ok(const KParams& kp) {
@@ -652,6 +704,38 @@ __device__ __forceinline__ void coupled_node(const KParams& k, const StepState& 
   hist[5 * (size_t)N + idx] = Fy;
 }
 
+// The FP64 sums of phi and q of this step's moments pass from its np per-CTA partials (the
+// whole block, a fixed order: thread t adds partials t, t + blockDim, ..., then a fixed
+// tree), for the statistics and the loop control.
+__device__ __forceinline__ void coupled_reduce_moments(const KParams& k,
+                                                       const double2* __restrict__ partials,
+                                                       int np, Ctl* ctl) {
+  __shared__ double2 s_red[128];
+  double a = 0.0, b = 0.0;
+  for (int j = threadIdx.x; j < np; j += blockDim.x) {
+    const double2 v = __ldcg(partials + j);
+    a += v.x;
+    b += v.y;
+  }
+  s_red[threadIdx.x] = make_double2(a, b);
+  __syncthreads();
+  for (int o = (int)blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      const double2 u = s_red[threadIdx.x + o];
+      s_red[threadIdx.x].x += u.x;
+      s_red[threadIdx.x].y += u.y;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    ctl->sum_phi = s_red[0].x;
+    ctl->sum_q = s_red[0].y;
+    ctl->mean_q = (float)(s_red[0].y / (double)k.nint);
+    ctl->mpart_n = 0;
+  }
+  __syncthreads();
+}
+
 // Block `bid` of blocks of 128 threads over one simulation, one node per thread, loads
 // straight from device memory.
 template <bool HALF>
@@ -659,11 +743,16 @@ __device__ __forceinline__ void coupled_body(const KParams& k, StepState* ss, in
                                              const Pops& pin, const Pops& pout,
                                              const float* __restrict__ phi_f,
                                              const float* __restrict__ hbuf,
-                                             float* __restrict__ hist, const Ctl* ctl,
+                                             float* __restrict__ hist, Ctl* ctl,
+                                             const double2* __restrict__ partials,
                                              DevStats* stats, int bid) {
   const int parity = ld_cg(&ctl->parity);
   const StepState sa = ss[cur];
-  if (bid == 0 && threadIdx.x == 0) coupled_record(k, ss, cur, sa, ctl, stats);
+  if (bid == 0) {
+    const int np = ld_cg(&ctl->mpart_n);
+    if (np > 0) coupled_reduce_moments(k, partials, np, ctl);
+    if (threadIdx.x == 0) coupled_record(k, ss, cur, sa, ctl, stats);
+  }
   const int i0 = bid * blockDim.x + threadIdx.x;  // interior node
   if (i0 >= k.nint) return;
   const int y = i0 / k.nx, x = i0 - y * k.nx;
@@ -682,9 +771,10 @@ __global__ void __launch_bounds__(128) k_coupled(KParams k, StepState* ss, int c
                                                  Pops pout,
                                                  const float* __restrict__ phi_f,
                                                  const float* __restrict__ hbuf,
-                                                 float* __restrict__ hist, const Ctl* ctl,
+                                                 float* __restrict__ hist, Ctl* ctl,
+                                                 const double2* __restrict__ partials,
                                                  DevStats* stats) {
-  coupled_body<HALF>(k, ss, cur, pin, pout, phi_f, hbuf, hist, ctl, stats, blockIdx.x);
+  coupled_body<HALF>(k, ss, cur, pin, pout, phi_f, hbuf, hist, ctl, partials, stats, blockIdx.x);
 }
 #ifndef EHD_COUPLED_MIN_CTAS
 #define EHD_COUPLED_MIN_CTAS 7
@@ -695,8 +785,10 @@ __global__ void __launch_bounds__(128, EHD_COUPLED_MIN_CTAS) k_coupled<false>(KP
                                                            const float* __restrict__ phi_f,
                                                            const float* __restrict__ hbuf,
                                                            float* __restrict__ hist,
-                                                           const Ctl* ctl, DevStats* stats) {
-  coupled_body<false>(k, ss, cur, pin, pout, phi_f, hbuf, hist, ctl, stats, blockIdx.x);
+                                                           Ctl* ctl,
+                                                           const double2* __restrict__ partials,
+                                                           DevStats* stats) {
+  coupled_body<false>(k, ss, cur, pin, pout, phi_f, hbuf, hist, ctl, partials, stats, blockIdx.x);
 }
 
 // ------------------------------------------------------------------------------------
@@ -723,11 +815,11 @@ __global__ void __launch_bounds__(128) k_coupled_batch(const StepSlot* __restric
   const StepSlot& S = slots[w.x];
   const Pops Pi = pops_copy(S.k, S.b, cur), Po = pops_copy(S.k, S.b, cur ^ 1);
   if (S.k.half)
-    coupled_body<true>(S.k, S.b.ss, cur, Pi, Po, S.b.phi, S.b.h, S.b.hist, S.b.ctl, S.b.stats,
-                       w.y);
+    coupled_body<true>(S.k, S.b.ss, cur, Pi, Po, S.b.phi, S.b.h, S.b.hist, S.b.ctl,
+                       S.b.partials, S.b.stats, w.y);
   else
-    coupled_body<false>(S.k, S.b.ss, cur, Pi, Po, S.b.phi, S.b.h, S.b.hist, S.b.ctl, S.b.stats,
-                        w.y);
+    coupled_body<false>(S.k, S.b.ss, cur, Pi, Po, S.b.phi, S.b.h, S.b.hist, S.b.ctl,
+                        S.b.partials, S.b.stats, w.y);
 }
 
 // Diagnostics: puts the grid barrier's arrival count half the counter range behind every
@@ -854,13 +946,19 @@ cudaError_t launch_init(const KParams& kp, const Buffers& b, int cur, bool have_
 }
 
 cudaError_t launch_moments(const KParams& kp, const Buffers& b, int cur, double tol,
-                           int min_iter, int max_iter, int fixed_iter, cudaStream_t st) {
+                           int min_iter, int max_iter, int fixed_iter, cudaStream_t st,
+                           bool sums_in_coupled) {
   const int nb = moments_blocks(kp.nint);
   const Pops P = pops_copy(kp, b, cur);
   if (moments4_ok(kp)) {
-    k_moments4<<<moments4_blocks(kp), 256, 0, st>>>(kp, b.ss + cur, P, b.hist, b.phi, b.aq,
-                                                    b.partials, b.ctl, tol, min_iter, max_iter,
-                                                    fixed_iter);
+    if (sums_in_coupled && !kp.neutralize)
+      k_moments4<false><<<moments4_blocks(kp), 256, 0, st>>>(kp, b.ss + cur, P, b.hist, b.phi,
+                                                             b.aq, b.partials, b.ctl, tol,
+                                                             min_iter, max_iter, fixed_iter);
+    else
+      k_moments4<true><<<moments4_blocks(kp), 256, 0, st>>>(kp, b.ss + cur, P, b.hist, b.phi,
+                                                            b.aq, b.partials, b.ctl, tol,
+                                                            min_iter, max_iter, fixed_iter);
     return cudaGetLastError();
   }
   if (kp.half)
@@ -876,10 +974,10 @@ cudaError_t launch_coupled(const KParams& kp, const Buffers& b, int cur, cudaStr
   const Pops Pi = pops_copy(kp, b, cur), Po = pops_copy(kp, b, cur ^ 1);
   if (kp.half)
     k_coupled<true><<<blocks_for(kp.nint, 128), 128, 0, st>>>(kp, b.ss, cur, Pi, Po, b.phi, b.h,
-                                                           b.hist, b.ctl, b.stats);
+                                                           b.hist, b.ctl, b.partials, b.stats);
   else
     k_coupled<false><<<blocks_for(kp.nint, 128), 128, 0, st>>>(kp, b.ss, cur, Pi, Po, b.phi, b.h,
-                                                            b.hist, b.ctl, b.stats);
+                                                            b.hist, b.ctl, b.partials, b.stats);
   return cudaGetLastError();
 }
 
@@ -933,7 +1031,8 @@ cudaError_t launch_fields_from_phi(const KParams& kp, const Buffers& b, int cur,
 // Graph nodes (the argument values are copied by cudaGraphAddKernelNode).
 cudaError_t add_moments_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
                              cudaGraphNode_t* out, const KParams& kp, const Buffers& b, int cur,
-                             double tol, int min_iter, int max_iter, int fixed_iter) {
+                             double tol, int min_iter, int max_iter, int fixed_iter,
+                             bool sums_in_coupled) {
   KParams k = kp;
   const StepState* ss = b.ss + cur;
   Pops pops = pops_copy(kp, b, cur);
@@ -945,8 +1044,10 @@ cudaError_t add_moments_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t 
   void* args[] = {&k, &ss, &pops, &hist, &phi, &aq, &partials, &ctl, &tol, &min_iter, &max_iter,
                   &fixed_iter};
   cudaKernelNodeParams p = {};
-  p.func = moments4_ok(kp) ? (void*)k_moments4
-                           : (kp.half ? (void*)k_moments<true> : (void*)k_moments<false>);
+  p.func = moments4_ok(kp)
+               ? ((sums_in_coupled && !kp.neutralize) ? (void*)k_moments4<false>
+                                                      : (void*)k_moments4<true>)
+               : (kp.half ? (void*)k_moments<true> : (void*)k_moments<false>);
   p.gridDim = dim3(moments4_ok(kp) ? moments4_blocks(kp) : moments_blocks(kp.nint));
   p.blockDim = dim3(256);
   p.kernelParams = args;
@@ -962,9 +1063,10 @@ cudaError_t add_coupled_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t 
   const float* phi = b.phi;
   const float* h = b.h;
   float* hist = b.hist;
-  const Ctl* ctl = b.ctl;
+  Ctl* ctl = b.ctl;
+  const double2* partials = b.partials;
   DevStats* stats = b.stats;
-  void* args[] = {&k, &ss, &cur, &pin, &pout, &phi, &h, &hist, &ctl, &stats};
+  void* args[] = {&k, &ss, &cur, &pin, &pout, &phi, &h, &hist, &ctl, &partials, &stats};
   cudaKernelNodeParams p = {};
   p.func = kp.half ? (void*)k_coupled<true> : (void*)k_coupled<false>;
   p.gridDim = dim3(blocks_for(kp.nint, 128));
@@ -1033,7 +1135,7 @@ cudaError_t build_step_graph(const KParams& kp, const Buffers& b, int cur, doubl
   cudaGraphNode_t mn, wn, pn, cn;
   if ((e = record(0)) != cudaSuccess ||
       (e = add_moments_node(g, have ? &last : nullptr, have ? 1 : 0, &mn, kp, b, cur, tol,
-                            min_iter, max_iter, fixed_iter)) != cudaSuccess)
+                            min_iter, max_iter, fixed_iter, rg != nullptr)) != cudaSuccess)
     return done(e);
   last = mn;
   have = true;

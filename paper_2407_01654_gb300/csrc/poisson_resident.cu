@@ -120,7 +120,11 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
   const float qshift = k.neutralize ? ld_cg(&ctl->mean_q) : 0.0f;
   const float vw_b = ld_cg(&ctl->vw_b), vw_t = ld_cg(&ctl->vw_t);
   const double tol = ctl->tol;
-  const int min_iter = ctl->min_iter, max_iter = ctl->max_iter, fixed = ctl->fixed_iter;
+  // a non-finite phi or q (flagged by the moments pass) stops the loop after one
+  // sub-iteration, not converged
+  const bool bad_state = ld_cg(&ctl->nonfinite) != 0;
+  const int min_iter = bad_state ? 1 : ctl->min_iter, max_iter = bad_state ? 1 : ctl->max_iter,
+            fixed = bad_state ? 0 : ctl->fixed_iter;
   const float om = k.omega_h;
   constexpr int pstride = 8 * T::PMAX;
   // this thread's nodes: column lx, rows ly0 + s ROWS
@@ -640,7 +644,11 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
   const float qshift = k.neutralize ? ld_cg(&ctl->mean_q) : 0.0f;
   const float vw_b = ld_cg(&ctl->vw_b), vw_t = ld_cg(&ctl->vw_t);
   const double tol = ctl->tol;
-  const int min_iter = ctl->min_iter, max_iter = ctl->max_iter, fixed = ctl->fixed_iter;
+  // a non-finite phi or q (flagged by the moments pass) stops the loop after one
+  // sub-iteration, not converged
+  const bool bad_state = ld_cg(&ctl->nonfinite) != 0;
+  const int min_iter = bad_state ? 1 : ctl->min_iter, max_iter = bad_state ? 1 : ctl->max_iter,
+            fixed = bad_state ? 0 : ctl->fixed_iter;
   const float om = k.omega_h;
   constexpr int pstride = 8 * T::PMAX;
   const int warp = threadIdx.x >> 5;
@@ -1251,7 +1259,11 @@ __device__ __forceinline__ void resident_loopD(const KParams& k, const ResidentG
   const float qshift = k.neutralize ? ld_cg(&ctl->mean_q) : 0.0f;
   const float vw_b = ld_cg(&ctl->vw_b), vw_t = ld_cg(&ctl->vw_t);
   const double tol = ctl->tol;
-  const int min_iter = ctl->min_iter, max_iter = ctl->max_iter, fixed = ctl->fixed_iter;
+  // a non-finite phi or q (flagged by the moments pass) stops the loop after one
+  // sub-iteration, not converged
+  const bool bad_state = ld_cg(&ctl->nonfinite) != 0;
+  const int min_iter = bad_state ? 1 : ctl->min_iter, max_iter = bad_state ? 1 : ctl->max_iter,
+            fixed = bad_state ? 0 : ctl->fixed_iter;
   const float om = k.omega_h;
   constexpr int pstride = 8 * T::PMAX;
   const int warp = threadIdx.x >> 5;
