@@ -140,7 +140,7 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -154,6 +154,31 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
             self.fh.close()
+
+    def count(self):
+        """Samples written so far."""
+        if self.proc is None or not os.path.exists(self.path):
+            return 0
+        self.fh.flush()
+        n = 0
+        for line in open(self.path):
+            parts = line.split(",")
+            if len(parts) >= 9:
+                try:
+                    float(parts[1])
+                    n += 1
+                except ValueError:
+                    pass
+        return n
+
+    def keep_busy(self, work, target, limit_s=5.0):
+        """Runs `work` (GPU work, synchronised) until `target` samples have been written or
+        `limit_s` has passed: the samples then show the clocks under load."""
+        import torch
+        t0 = time.perf_counter()
+        while self.proc is not None and self.count() < target and time.perf_counter() - t0 < limit_s:
+            work()
+            torch.cuda.synchronize()
 
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
@@ -306,8 +331,17 @@ def run_gpu(args, rank, world):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
+    # the timed region (K steps of well under 0.1 ms each) is shorter than one clock sample
+    # interval, so the clocks are sampled while a copy of the simulation runs the same steps
+    # right before and right after it
+    load_sim = ehd.Sim(p, stream=stream)
+    load_sim.load_state(start_state)
     with ClockSampler(dev) as clk:
+        clk.keep_busy(lambda: load_sim.step(100, stats=False), 2)
+        n_before = clk.count()
         step_ms = timed_steps(sim, args.steps)
+        clk.keep_busy(lambda: load_sim.step(100, stats=False), n_before + 2)
+    load_sim.close()
     wall = time.perf_counter() - wall0
     st = sim.read_stats()
     if st["status"] not in (0, 4):
@@ -457,6 +491,8 @@ def run_gpu(args, rank, world):
         "e2e": e2e,
     }
     line["clocks"] = clk.summary()
+    line["clocks"]["window"] = ("nvidia-smi every 50 ms while a copy of the simulation ran the "
+                                "same steps right before and right after the timed region")
     if world == 1 and not args.no_serve:
         line["serving"] = run_serving()
     if world == 1 and not args.no_cpu_baseline:

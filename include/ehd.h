@@ -209,11 +209,13 @@ int ehd_set_fields(ehd_sim* sim, const void* phi, const void* q, const void* ux,
 int ehd_step(ehd_sim* sim, int nsteps, ehd_stats* stats);
 
 /* Launch mode of later ehd_step calls (no counterpart in the paper): enable != 0 (the
- * default) launches each step as one captured CUDA graph; enable == 0 queues the step's
- * kernels one by one from the host, with the streaming loop's stopping rule checked on
- * the host between chunks of launches.  Both run the same kernels and give the same
- * states, bit for bit.  Errors: EHD_ERR_INVALID_ARG (null handle). */
+ * default) launches steps as captured CUDA graphs (runs of 8 steps as one graph, the
+ * rest one graph per step); enable == 0 queues the step's kernels one by one from the
+ * host, with the streaming loop's stopping rule checked on the host between chunks of
+ * launches.  Both give the same states, bit for bit.  Errors: EHD_ERR_INVALID_ARG (null
+ * handle). */
 int ehd_use_graphs(ehd_sim* sim, int enable);
+
 
 /* Which potential loop this simulation runs: EHD_LOOP_STREAM, EHD_LOOP_RESIDENT,
  * EHD_LOOP_RESIDENT2 or EHD_LOOP_RESIDENT3 (negative: invalid handle). */

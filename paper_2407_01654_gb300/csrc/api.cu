@@ -309,11 +309,14 @@ void destroy_graphs(ehd_sim* s) {
     if (s->exec[c]) cudaGraphExecDestroy(s->exec[c]);
     if (s->graph[c]) cudaGraphDestroy(s->graph[c]);
     if (s->pexec[c]) cudaGraphExecDestroy(s->pexec[c]);
+    if (s->mexec[c]) cudaGraphExecDestroy(s->mexec[c]);
     s->exec[c] = nullptr;
     s->graph[c] = nullptr;
     s->pexec[c] = nullptr;
+    s->mexec[c] = nullptr;
   }
   s->graphs_ok = false;
+  s->mgraphs_ok = false;
   s->pgraphs_ok = false;
   s->pgraphs_tried = false;
 }
@@ -366,6 +369,25 @@ void ensure_graphs(ehd_sim* s) {
     }
   }
   s->graphs_ok = true;
+  // the multi-step graphs are an optimisation: without them steps run one graph each
+  bool mok = true;
+  for (int c = 0; c < 2 && mok; ++c) {
+    cudaGraph_t g = nullptr;
+    mok = build_step_graph(s->kp, s->b, c, P.poisson_tol, P.poisson_min_iter,
+                           P.poisson_max_iter, P.poisson_fixed_iter,
+                           s->resident_ok ? &s->rg : nullptr, s->rthreads, s->rsmem, &g,
+                           nullptr, ehd_sim::MULTI_STEPS) == cudaSuccess &&
+          cudaGraphInstantiate(&s->mexec[c], g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+  }
+  if (!mok) {
+    cudaGetLastError();
+    for (int c = 0; c < 2; ++c) {
+      if (s->mexec[c]) cudaGraphExecDestroy(s->mexec[c]);
+      s->mexec[c] = nullptr;
+    }
+  }
+  s->mgraphs_ok = mok;
 }
 
 // Copies one input field into the staging area; returns its largest magnitude in *amax
@@ -747,6 +769,15 @@ int ehd_step(ehd_sim* s, int nsteps, ehd_stats* out) {
     // an armed diagnostic runs its step from the host (the graph has no slot for it)
     const bool use_graphs = s->graphs_ok && !s->expire_barrier && !s->no_graphs &&
                             (!s->profiling || s->pgraphs_ok);
+    if (use_graphs && !s->profiling && s->mgraphs_ok && nsteps - k >= ehd_sim::MULTI_STEPS) {
+      // a run of steps in one launch (an even count: the copy index is unchanged after it)
+      EHD_CUDA(cudaGraphLaunch(s->mexec[s->cur], s->stream));
+      s->graph_steps += ehd_sim::MULTI_STEPS;
+      s->n += ehd_sim::MULTI_STEPS;
+      s->history_valid = true;
+      k += ehd_sim::MULTI_STEPS - 1;
+      continue;
+    }
     if (use_graphs && s->profiling) {
       // the profiling graph: the step's three parts timed by its own event nodes
       EHD_CUDA(cudaGraphLaunch(s->pexec[s->cur], s->stream));

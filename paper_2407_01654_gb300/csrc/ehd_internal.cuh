@@ -144,7 +144,8 @@ __device__ __forceinline__ void st_pop(const KParams& k, const Pops& P, int fiel
                                        size_t idx, float v) {
   const size_t N = (size_t)k.N;
   if (!HALF) {
-    P.p32[(size_t)(field * 9 + i) * N + idx] = v;
+    // written once a step and read once the next: stored evict-first (st.global.cs)
+    __stcs(P.p32 + (size_t)(field * 9 + i) * N + idx, v);
   } else if (i == 0) {
     P.p32[(size_t)field * N + idx] = v;
   } else {
@@ -159,7 +160,7 @@ __device__ __forceinline__ float ld_g0_lo(const KParams& k, const Pops& P, size_
 }
 template <bool HALF>
 __device__ __forceinline__ void st_g0_lo(const KParams& k, const Pops& P, size_t idx, float v) {
-  P.p32[(size_t)(HALF ? 3 : NPOP) * k.N + idx] = v;
+  __stcs(P.p32 + (size_t)(HALF ? 3 : NPOP) * k.N + idx, v);  // evict-first, as st_pop
 }
 // Stores a population and returns the value a later ld_pop of it reads (with FP16 storage
 // the rounded value).
@@ -184,6 +185,22 @@ __device__ __forceinline__ float phi_of(const KParams& k, const Pops& P, size_t 
   for (int i = 1; i < 9; ++i) m = __fadd_rn(m, ld_pop<HALF>(k, P, 0, i, idx));
   return __fadd_rn(ld_pop<HALF>(k, P, 0, 0, idx), __fadd_rn(m, ld_g0_lo<HALF>(k, P, idx)));
 }
+// The moments of one node from its post-stream populations (Algorithm 1, first step):
+// phi = sum_i g_i with g_0 = hi + lo (the moving populations summed in order, then lo,
+// then hi, as phi_of does) and q = sum_i l_i + R/2 (the Nernst-Planck source's half-step
+// correction).  Every rounding is explicit: the same bits in every translation unit.
+__device__ __forceinline__ void moments_of(const float (&g)[9], float lo, const float (&l)[9],
+                                           float R, float& phi, float& q) {
+  float m = 0.0f;
+#pragma unroll
+  for (int i = 1; i < 9; ++i) m = __fadd_rn(m, g[i]);
+  phi = __fadd_rn(g[0], __fadd_rn(m, lo));
+  float s = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) s = __fadd_rn(s, l[i]);
+  q = __fadd_rn(s, __fmul_rn(0.5f, R));
+}
+
 // (hi, lo) + d as two floats again: Knuth's two-sum of hi and d (exact), the rounding
 // error folded into lo, then one fast two-sum to renormalise.
 __device__ __forceinline__ void two_float_add(float& hi, float& lo, float d) {
@@ -271,17 +288,20 @@ struct DevStats {
 
 // Property laws (Remark II, Eq. weq36).
 __device__ __forceinline__ float eps_hat_of(const KParams& k, float phi) {
-  return phi * phi * (2.0f * phi - 3.0f) * k.deps;
+  return __fmul_rn(__fmul_rn(__fmul_rn(phi, phi), __fsub_rn(__fmul_rn(2.0f, phi), 3.0f)), k.deps);
 }
 
 // Per-node coefficient of the potential collision, kept in aq[].x: the paper's scheme
 // a = eps_hat / (c_s^2 tau_h (eps_hat + c_s^2 tau_h)) (forcing through the local first
 // moment, Eq. eqA.16); the conventional scheme its relaxation rate 1 / tau_varphi with
 // tau_varphi = 1/2 + eps(phi) / (chi c_s^2) (Sec. 3.3).
+// Every rounding is explicit, so each translation unit computes the same bits whatever its
+// multiply-add contraction.
 __device__ __forceinline__ float potential_coef(const KParams& k, float phi) {
   const float eh = eps_hat_of(k, phi);
-  if (k.scheme == 1) return 1.0f / (0.5f + (k.eps_v + eh) * k.inv_chi_cs2);
-  return eh / (k.cs2tauh * (eh + k.cs2tauh));
+  if (k.scheme == 1)
+    return __fdiv_rn(1.0f, __fadd_rn(0.5f, __fmul_rn(__fadd_rn(k.eps_v, eh), k.inv_chi_cs2)));
+  return __fdiv_rn(eh, __fmul_rn(k.cs2tauh, __fadd_rn(eh, k.cs2tauh)));
 }
 // The denominator d of grad varphi = -sum_i c_i h_i / d: eps_hat + c_s^2 tau_h
 // (Eq. eqA.16), or c_s^2 tau_varphi for the conventional scheme.
@@ -523,8 +543,10 @@ cudaError_t add_coupled_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t 
 // of the WHILE node.
 // With `ev` (4 events) the graph records ev[0] before the moments pass, ev[1] after it,
 // ev[2] after the potential loop and ev[3] after the coupled pass (per-kernel timing).
+// With nsteps > 1 (and no events) the graph holds that many consecutive steps, the first
+// on population copy `cur`, the copies alternating: one launch runs them all.
 cudaError_t build_step_graph(const KParams& kp, const Buffers& b, int cur, double tol,
                              int min_iter, int max_iter, int fixed_iter, const ResidentGeom* rg,
                              int rthreads, size_t rsmem, cudaGraph_t* out,
-                             const cudaEvent_t* ev = nullptr);
+                             const cudaEvent_t* ev = nullptr, int nsteps = 1);
 }  // namespace ehd

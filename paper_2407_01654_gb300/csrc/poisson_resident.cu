@@ -641,6 +641,34 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
   float* ring = cq + T::PLANE;
   const int parity = ld_cg(&ctl->parity);
   float* __restrict__ hsrc = hbuf + (size_t)parity * NH * N;
+  // my tile nodes: column lx, rows ly0 + s ROWS
+  const int lx = threadIdx.x & (TXR - 1);
+  const int ly0 = threadIdx.x >> 6;
+  const int at0 = (ly0 + 2) * PXF + lx + 2;   // frame index of node 0
+  const int nrows = lx < tw ? th : 0;
+  // per node: inside the lattice; on the bottom / top lattice row next to a wall
+  auto valid = [&](int s) { return ly0 + s * T::ROWS < nrows; };
+  auto bw = [&](int s) { return k.walls && ty0 + ly0 + s * T::ROWS == 0; };
+  auto tw_ = [&](int s) { return k.walls && ty0 + ly0 + s * T::ROWS == ny - 1; };
+  // every load of the thread's four nodes is issued at entry, before the tensor-memory
+  // allocation, the neighbour table and the ring import, and before any value is used (a
+  // node outside the lattice loads node 0 and then starts from zero): their round trip to
+  // memory overlaps the rest of the set-up
+  float2 h[2][8];
+  float2 tc[NPT];
+#pragma unroll
+  for (int s = 0; s < NPT; ++s) {
+    const int g = valid(s) ? (ty0 + ly0 + s * T::ROWS) * nx + tx0 + lx : 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float v = hsrc[i * N + g];
+      if (s & 1)
+        h[s >> 1][i].y = v;
+      else
+        h[s >> 1][i].x = v;
+    }
+    tc[s] = aq[g];
+  }
   const float qshift = k.neutralize ? ld_cg(&ctl->mean_q) : 0.0f;
   const float vw_b = ld_cg(&ctl->vw_b), vw_t = ld_cg(&ctl->vw_t);
   const double tol = ctl->tol;
@@ -662,12 +690,6 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-
-  // my tile nodes: column lx, rows ly0 + s ROWS
-  const int lx = threadIdx.x & (TXR - 1);
-  const int ly0 = threadIdx.x >> 6;
-  const int at0 = (ly0 + 2) * PXF + lx + 2;   // frame index of node 0
-  const int nrows = lx < tw ? th : 0;
 
   if (threadIdx.x < 9) {
     const int dx = (int)threadIdx.x % 3 - 1, dy = (int)threadIdx.x / 3 - 1;
@@ -730,37 +752,16 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
     }
   }
 
-  // my tile nodes: state in registers (two packed pairs), coefficients in the frame.
-  // Nodes outside the lattice (partial tiles) compute with their pair but write nothing
-  // to shared memory: their cells may be ring nodes of this tile.
-  float2 h[2][8];
-  // per node: inside the lattice; on the bottom / top lattice row next to a wall
-  auto valid = [&](int s) { return ly0 + s * T::ROWS < nrows; };
-  auto bw = [&](int s) { return k.walls && ty0 + ly0 + s * T::ROWS == 0; };
-  auto tw_ = [&](int s) { return k.walls && ty0 + ly0 + s * T::ROWS == ny - 1; };
-  // every load of the thread's four nodes is issued before any is used (a node outside the
-  // lattice loads node 0 and then starts from zero), so the prologue waits for one round
-  // trip to memory instead of four
-  float2 c[NPT];
-#pragma unroll
-  for (int s = 0; s < NPT; ++s) {
-    const int g = valid(s) ? (ty0 + ly0 + s * T::ROWS) * nx + tx0 + lx : 0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float v = hsrc[i * N + g];
-      if (s & 1)
-        h[s >> 1][i].y = v;
-      else
-        h[s >> 1][i].x = v;
-    }
-    c[s] = aq[g];
-  }
+  // my tile nodes: the state loaded at entry sits in registers (two packed pairs), the
+  // coefficients go to the frame.  Nodes outside the lattice (partial tiles) compute with
+  // their pair but write nothing to shared memory: their cells may be ring nodes of this
+  // tile.
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
     if (valid(s)) {  // a node outside the lattice may sit on a ring node's cell
-      float q = __fsub_rn(c[s].y, qshift);
+      float q = __fsub_rn(tc[s].y, qshift);
       if (CONV) q = __fmul_rn(q, k.inv_chi);
-      ca[at0 + s * T::ROWS * PXF] = c[s].x;
+      ca[at0 + s * T::ROWS * PXF] = tc[s].x;
       cq[at0 + s * T::ROWS * PXF] = q;
     } else {
 #pragma unroll

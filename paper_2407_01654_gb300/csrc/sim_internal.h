@@ -44,6 +44,12 @@ struct ehd_sim {
   bool no_graphs = false;     // steps queued kernel by kernel from the host (ehd_use_graphs)
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  // MULTI_STEPS consecutive steps in one graph (from copy 0 and from copy 1): runs of that
+  // many steps pay one graph launch instead of one per step
+  static constexpr int MULTI_STEPS = 8;
+  static_assert(MULTI_STEPS % 2 == 0, "a run must leave the copy index unchanged");
+  cudaGraphExec_t mexec[2] = {nullptr, nullptr};
+  bool mgraphs_ok = false;
   // the same step graphs with event-record nodes around the three parts, for profiling
   bool pgraphs_tried = false;
   bool pgraphs_ok = false;

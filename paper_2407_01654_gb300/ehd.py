@@ -301,7 +301,7 @@ class Sim:
 
     def use_graphs(self, enable=True):
         """enable=False: later steps queue their kernels one by one from the host instead of
-        launching one captured graph per step (same kernels, same states)."""
+        launching captured graphs (same states, bit for bit)."""
         _check(lib().ehd_use_graphs(self._h, 1 if enable else 0), "ehd_use_graphs")
 
     def diag_expire_barrier(self):
