@@ -48,6 +48,10 @@ SPINUP_STEPS = 300
 # not on the state): the reference arm runs the oracle at this count, the GPU line reports
 # its own throughput at this count next to the rule-driven value.
 K_COMPARE = 5
+# A second fixed count: the step's time at K_COMPARE and at K_HIGH sub-iterations gives the
+# marginal cost of one sub-iteration and, with the profiled solve time, the solve's fixed
+# cost (launch, loading the state, writing it back)
+K_HIGH = 25
 # The workload as both arms name it (identical in the GPU and the reference line).
 CONFIG = {"workload": WORKLOAD, "nodes": 512 * 1024,
           "start": f"step 10000 of a 20000-step ramp, then {SPINUP_STEPS} untimed steps",
@@ -378,6 +382,15 @@ def run_gpu(args, rank, world):
                "value": nodes * args.steps / (fixed_ms / 1e3) / 1e6, "unit": UNIT,
                "ms_per_step": fixed_ms / args.steps,
                "sub_iterations": stk["poisson_iters_total"]}
+    simh = ehd.Sim(dict(p, poisson_fixed_iter=K_HIGH), stream=stream)
+    simh.load_state(start_state)
+    simh.step(2)
+    simh.load_state(start_state)
+    torch.cuda.synchronize()
+    high_ms = timed_steps(simh, args.steps)
+    simh.close()
+    # marginal cost of one sub-iteration inside the step (us)
+    marginal_us = (high_ms - fixed_ms) / args.steps / (K_HIGH - K_COMPARE) * 1e3
     # e2e through the C ABI with host buffers, the same window: the start state loaded
     # from pinned host memory (ehd_load_state), the steps, all fields read back to host
     # arrays (ehd_read_fields, float32 copies converted to double)
@@ -452,6 +465,17 @@ def run_gpu(args, rank, world):
                              "TFLOPs": FLOPS_POTENTIAL * nodes_f / t_it / 1e12,
                              "frac_of_derived_peak": FLOPS_POTENTIAL * nodes_f / t_it / 1e12 /
                              fp32_peak}}
+        # per launch at the window's K the solve's fixed part (launch, loading h and the
+        # coefficients, writing h back) weighs heavily; the marginal sub-iteration is the
+        # loop's own rate
+        mb = SMEM_BYTES_POTENTIAL * nodes_f / (marginal_us * 1e-6) / 1e9
+        roof_pot["marginal"] = {
+            "what": f"(step time at K={K_HIGH} - at K={K_COMPARE}) / {K_HIGH - K_COMPARE}, "
+                    "fixed sub-iteration counts, the same state",
+            "sub_iteration_us": marginal_us, "achieved": mb, "frac": mb / smem_peak,
+            "hbm_streamed_equivalent_frac":
+                BYTES_POTENTIAL * nodes_f / (marginal_us * 1e-6) / 1e9 / peak,
+            "solve_fixed_us": kinds["potential"]["us_per_launch"] - kbar * marginal_us}
     else:
         roof_pot = {"bound": "hbm", "kernel": "k_poisson", "achieved": BYTES_POTENTIAL * nodes_f / t_it / 1e9,
                     "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)", "unit": "GB/s",

@@ -144,8 +144,12 @@ __device__ __forceinline__ void st_pop(const KParams& k, const Pops& P, int fiel
                                        size_t idx, float v) {
   const size_t N = (size_t)k.N;
   if (!HALF) {
-    // written once a step and read once the next: stored evict-first (st.global.cs)
-    __stcs(P.p32 + (size_t)(field * 9 + i) * N + idx, v);
+    // the hydrodynamic populations are read only by the next coupled pass: stored
+    // evict-first (st.global.cs); g and l stay in L2 for the next moments pass
+    if (field == 2)
+      __stcs(P.p32 + (size_t)(field * 9 + i) * N + idx, v);
+    else
+      P.p32[(size_t)(field * 9 + i) * N + idx] = v;
   } else if (i == 0) {
     P.p32[(size_t)field * N + idx] = v;
   } else {
@@ -160,7 +164,7 @@ __device__ __forceinline__ float ld_g0_lo(const KParams& k, const Pops& P, size_
 }
 template <bool HALF>
 __device__ __forceinline__ void st_g0_lo(const KParams& k, const Pops& P, size_t idx, float v) {
-  __stcs(P.p32 + (size_t)(HALF ? 3 : NPOP) * k.N + idx, v);  // evict-first, as st_pop
+  P.p32[(size_t)(HALF ? 3 : NPOP) * k.N + idx] = v;
 }
 // Stores a population and returns the value a later ld_pop of it reads (with FP16 storage
 // the rounded value).
