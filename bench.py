@@ -101,12 +101,13 @@ KERNEL_FILES = {
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # of the bench workload (summaries under profiles/, named for the kernel and workload)
 RECORDED_TRAFFIC = {
-    # one potential solve of the two-step loop (280 sub-iterations on the captured step):
-    # 21.030 MB read, 0.076 MB written
-    "k_poisson_resident2": (21106176, "419d0b415696813c"),
-    # one coupled pass: 88.137 MB read, 20.969 MB written back during the launch (the
-    # rest of its writes leave L2 later)
-    "k_coupled": (109106688, "3bcd59efcd78de5f"),
+    # one potential solve of the two-step loop (about 380 sub-iterations on the captured
+    # spin-up step; the solve's DRAM traffic does not grow with them): 21.022 MB read,
+    # 0.035 MB written
+    "k_poisson_resident2": (21057280, "f9f13bd821681553"),
+    # one coupled pass, caches flushed before the launch: 90.249 MB read, 15.439 MB written
+    # back during the launch (the rest of its writes leave L2 later)
+    "k_coupled": (105688064, "61ffe24fb0d5ff29"),
 }
 
 
