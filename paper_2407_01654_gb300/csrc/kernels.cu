@@ -756,7 +756,7 @@ __device__ __forceinline__ void coupled_body(const KParams& k, StepState* ss, in
                                              float* __restrict__ hist, Ctl* ctl,
                                              const double2* __restrict__ partials,
                                              DevStats* stats, int bid) {
-  const int parity = ld_cg(&ctl->parity);
+  const int parity = __ldg(&ctl->parity);  // not written in this pass: one request per SM
   const StepState sa = ss[cur];
   if (bid == 0) {
     const int np = ld_cg(&ctl->mpart_n);
@@ -873,7 +873,7 @@ __global__ void k_fields(KParams k, const StepState* __restrict__ ss, Pops pops,
   if (i0 >= k.nint) return;
   const int y = i0 / k.nx, x = i0 - y * k.nx;
   const int idx = i0 + k.row0 * k.nx;
-  const int parity = ld_cg(&ctl->parity);
+  const int parity = __ldg(&ctl->parity);  // not written in this pass: one request per SM
   const float* hs = hbuf + (size_t)parity * NH * N;
   const StepState sa = *ss;
   const Stencil st = load_stencil(k, sa, phi_now, x, y);

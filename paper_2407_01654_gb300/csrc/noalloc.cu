@@ -112,10 +112,12 @@ __global__ void __launch_bounds__(NA_THREADS) k_poisson_noalloc(
   __shared__ double s_w[NA_THREADS / 32][2];
   __shared__ int s_last;
   Ctl* ctl = &sc->ctl;
-  if (ld_cg(&ctl->done)) return;
-  const int parity = ld_cg(&ctl->parity);
-  const float qshift = k.neutralize ? ld_cg(&ctl->mean_q) : 0.0f;
-  const float vw_b = ld_cg(&ctl->vw_b), vw_t = ld_cg(&ctl->vw_t);
+  // the same control words for every thread, written only by a launch's last CTA after
+  // every CTA has read them: the read-only path merges them per SM
+  if (__ldg(&ctl->done)) return;
+  const int parity = __ldg(&ctl->parity);
+  const float qshift = k.neutralize ? __ldg(&ctl->mean_q) : 0.0f;
+  const float vw_b = __ldg(&ctl->vw_b), vw_t = __ldg(&ctl->vw_t);
   const int nx = k.nx, ny = k.ny;
   const size_t N = (size_t)k.N;
   const float* __restrict__ src = parity ? h1 : h0;

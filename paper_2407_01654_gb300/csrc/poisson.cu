@@ -44,10 +44,13 @@ __global__ void __launch_bounds__(THREADS, 8) k_poisson(KParams k, float* __rest
   __shared__ double s_w[THREADS / 32][2];
   __shared__ int s_last;
 
-  if (ld_cg(&ctl->done)) return;
-  const int parity = ld_cg(&ctl->parity);
-  const float qshift = k.neutralize ? ld_cg(&ctl->mean_q) : 0.0f;
-  const float vw_b = ld_cg(&ctl->vw_b), vw_t = ld_cg(&ctl->vw_t);
+  // every thread reads the same few words of the loop control, which only the last CTA
+  // of a launch writes (after every CTA has read them): through the read-only path, so
+  // L1 merges them per SM instead of one L2 slice serving every warp
+  if (__ldg(&ctl->done)) return;
+  const int parity = __ldg(&ctl->parity);
+  const float qshift = k.neutralize ? __ldg(&ctl->mean_q) : 0.0f;
+  const float vw_b = __ldg(&ctl->vw_b), vw_t = __ldg(&ctl->vw_t);
   const int nx = k.nx, ny = k.ny;
   const size_t N = (size_t)k.N;
   const float* __restrict__ src = hbuf + (size_t)parity * NH * N;

@@ -115,14 +115,17 @@ __device__ __forceinline__ void resident_loop(const KParams& k, const ResidentGe
   const int tw = min(TXR, nx - tx0), th = min(TY, ny - ty0);
   float* ca = sm + 8 * T::PLANE;
   float* cq = ca + TY * TXR;
-  const int parity = ld_cg(&ctl->parity);
+  // the loop control's fields this solve reads but no CTA of it writes come through the
+  // read-only path: every warp of every CTA asks for the same few words at once, which
+  // L1 merges per SM instead of sending each request to one L2 slice
+  const int parity = __ldg(&ctl->parity);
   float* __restrict__ hsrc = hbuf + (size_t)parity * NH * N;
-  const float qshift = k.neutralize ? ld_cg(&ctl->mean_q) : 0.0f;
-  const float vw_b = ld_cg(&ctl->vw_b), vw_t = ld_cg(&ctl->vw_t);
+  const float qshift = k.neutralize ? __ldg(&ctl->mean_q) : 0.0f;
+  const float vw_b = __ldg(&ctl->vw_b), vw_t = __ldg(&ctl->vw_t);
   const double tol = ctl->tol;
   // a non-finite phi or q (flagged by the moments pass) stops the loop after one
   // sub-iteration, not converged
-  const bool bad_state = ld_cg(&ctl->nonfinite) != 0;
+  const bool bad_state = __ldg(&ctl->nonfinite) != 0;
   const int min_iter = bad_state ? 1 : ctl->min_iter, max_iter = bad_state ? 1 : ctl->max_iter,
             fixed = bad_state ? 0 : ctl->fixed_iter;
   const float om = k.omega_h;
@@ -639,7 +642,10 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
   float* ca = sm + 8 * T::PLANE;
   float* cq = ca + T::PLANE;
   float* ring = cq + T::PLANE;
-  const int parity = ld_cg(&ctl->parity);
+  // the loop control's fields this solve reads but no CTA of it writes come through the
+  // read-only path: every warp of every CTA asks for the same few words at once, which
+  // L1 merges per SM instead of sending each request to one L2 slice
+  const int parity = __ldg(&ctl->parity);
   float* __restrict__ hsrc = hbuf + (size_t)parity * NH * N;
   // my tile nodes: column lx, rows ly0 + s ROWS
   const int lx = threadIdx.x & (TXR - 1);
@@ -669,12 +675,12 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
     }
     tc[s] = aq[g];
   }
-  const float qshift = k.neutralize ? ld_cg(&ctl->mean_q) : 0.0f;
-  const float vw_b = ld_cg(&ctl->vw_b), vw_t = ld_cg(&ctl->vw_t);
+  const float qshift = k.neutralize ? __ldg(&ctl->mean_q) : 0.0f;
+  const float vw_b = __ldg(&ctl->vw_b), vw_t = __ldg(&ctl->vw_t);
   const double tol = ctl->tol;
   // a non-finite phi or q (flagged by the moments pass) stops the loop after one
   // sub-iteration, not converged
-  const bool bad_state = ld_cg(&ctl->nonfinite) != 0;
+  const bool bad_state = __ldg(&ctl->nonfinite) != 0;
   const int min_iter = bad_state ? 1 : ctl->min_iter, max_iter = bad_state ? 1 : ctl->max_iter,
             fixed = bad_state ? 0 : ctl->fixed_iter;
   const float om = k.omega_h;
@@ -1255,14 +1261,17 @@ __device__ __forceinline__ void resident_loopD(const KParams& k, const ResidentG
   float* ca = sm + 8 * T::PLANE;
   float* cq = ca + T::PLANE;
   float* ring = cq + T::PLANE;
-  const int parity = ld_cg(&ctl->parity);
+  // the loop control's fields this solve reads but no CTA of it writes come through the
+  // read-only path: every warp of every CTA asks for the same few words at once, which
+  // L1 merges per SM instead of sending each request to one L2 slice
+  const int parity = __ldg(&ctl->parity);
   float* __restrict__ hsrc = hbuf + (size_t)parity * NH * N;
-  const float qshift = k.neutralize ? ld_cg(&ctl->mean_q) : 0.0f;
-  const float vw_b = ld_cg(&ctl->vw_b), vw_t = ld_cg(&ctl->vw_t);
+  const float qshift = k.neutralize ? __ldg(&ctl->mean_q) : 0.0f;
+  const float vw_b = __ldg(&ctl->vw_b), vw_t = __ldg(&ctl->vw_t);
   const double tol = ctl->tol;
   // a non-finite phi or q (flagged by the moments pass) stops the loop after one
   // sub-iteration, not converged
-  const bool bad_state = ld_cg(&ctl->nonfinite) != 0;
+  const bool bad_state = __ldg(&ctl->nonfinite) != 0;
   const int min_iter = bad_state ? 1 : ctl->min_iter, max_iter = bad_state ? 1 : ctl->max_iter,
             fixed = bad_state ? 0 : ctl->fixed_iter;
   const float om = k.omega_h;
