@@ -253,7 +253,8 @@ int rebuild(ehd_batch* b) {
     q.min_iter = s->P.poisson_min_iter;
     q.max_iter = s->P.poisson_max_iter;
     q.fixed_iter = s->P.poisson_fixed_iter;
-    q.mblocks = moments_blocks(s->kp.N);
+    q.quad = moments4_ok(s->kp) ? 1 : 0;
+    q.mblocks = q.quad ? (s->kp.N / 4 + 255) / 256 : moments_blocks(s->kp.N);
     for (int t = 0; t < q.mblocks; ++t) mwork.push_back(make_int2((int)j, t));
     const int cb = (s->kp.N + 127) / 128;
     for (int t = 0; t < cb; ++t) cwork.push_back(make_int2((int)j, t));

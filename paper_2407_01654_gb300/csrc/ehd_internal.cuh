@@ -482,8 +482,15 @@ struct StepSlot {
   Buffers b;
   double tol;
   int min_iter, max_iter, fixed_iter;
-  int mblocks;       // moments blocks of this simulation (moments_blocks(N))
+  int mblocks;       // moments blocks of this simulation (its own moments launch's grid)
+  int quad;          // 1: moments four nodes per thread, as k_moments4 (moments4_ok)
 };
+
+// Whether a lattice's moments pass takes four nodes per thread with 16-byte loads
+// (k_moments4): FP32 populations, no slab, N a multiple of 4.
+__host__ __device__ inline bool moments4_ok(const KParams& kp) {
+  return !kp.half && !kp.slab && kp.N % 4 == 0 && kp.N == kp.nint;
+}
 
 // Batched moments / coupled passes: one launch over work[] = (slot, block of that slot).
 cudaError_t add_moments_batch_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,

@@ -394,15 +394,15 @@ __global__ void __launch_bounds__(256) k_moments(KParams k, const StepState* __r
 // arithmetic is moments_body's, in the same order; only the FP32 partial sums group the
 // nodes differently.
 template <bool TAIL>
-__global__ void __launch_bounds__(256) k_moments4(KParams k, const StepState* __restrict__ ss,
-                                                  Pops pops, const float* __restrict__ hist,
-                                                  float* __restrict__ phi_out,
-                                                  float2* __restrict__ aq,
-                                                  double2* __restrict__ partials, Ctl* ctl,
-                                                  double tol, int min_iter, int max_iter,
-                                                  int fixed_iter) {
+__device__ __forceinline__ void moments4_body(const KParams& k, const StepState* __restrict__ ss,
+                                              const Pops& pops, const float* __restrict__ hist,
+                                              float* __restrict__ phi_out,
+                                              float2* __restrict__ aq,
+                                              double2* __restrict__ partials, Ctl* ctl,
+                                              double tol, int min_iter, int max_iter,
+                                              int fixed_iter, int bid, int nblk) {
   const size_t N4 = (size_t)k.N / 4;
-  const size_t q4 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t q4 = (size_t)bid * blockDim.x + threadIdx.x;
   float phi_acc = 0.0f, q_acc = 0.0f;
   int bad = 0;
   if (q4 < N4) {
@@ -438,16 +438,24 @@ __global__ void __launch_bounds__(256) k_moments4(KParams k, const StepState* __
     a4[1] = make_float4(potential_coef(k, ph[2]), qq[2], potential_coef(k, ph[3]), qq[3]);
   }
   if (TAIL)
-    moments_tail(k, ss, partials, ctl, tol, min_iter, max_iter, fixed_iter, blockIdx.x,
-                 gridDim.x, phi_acc, q_acc, bad);
+    moments_tail(k, ss, partials, ctl, tol, min_iter, max_iter, fixed_iter, bid, nblk, phi_acc,
+                 q_acc, bad);
   else
-    moments_partial_only(k, ss, partials, ctl, tol, min_iter, max_iter, fixed_iter, blockIdx.x,
-                         gridDim.x, phi_acc, q_acc, bad);
+    moments_partial_only(k, ss, partials, ctl, tol, min_iter, max_iter, fixed_iter, bid, nblk,
+                         phi_acc, q_acc, bad);
 }
-// Whether a lattice takes k_moments4, and its grid.
-static inline bool moments4_ok(const KParams& kp) {
-  return !kp.half && !kp.slab && kp.N % 4 == 0 && kp.N == kp.nint;
+template <bool TAIL>
+__global__ void __launch_bounds__(256) k_moments4(KParams k, const StepState* __restrict__ ss,
+                                                  Pops pops, const float* __restrict__ hist,
+                                                  float* __restrict__ phi_out,
+                                                  float2* __restrict__ aq,
+                                                  double2* __restrict__ partials, Ctl* ctl,
+                                                  double tol, int min_iter, int max_iter,
+                                                  int fixed_iter) {
+  moments4_body<TAIL>(k, ss, pops, hist, phi_out, aq, partials, ctl, tol, min_iter, max_iter,
+                      fixed_iter, blockIdx.x, gridDim.x);
 }
+// Whether a lattice takes k_moments4 (moments4_ok, in the header), and its grid.
 static inline int moments4_blocks(const KParams& kp) { return (kp.N / 4 + 255) / 256; }
 
 // ------------------------------------------------------------------------------------
@@ -557,7 +565,7 @@ __device__ __forceinline__ void coupled_node(const KParams& k, const StepState& 
   const float eh = eps_hat_of(k, phi);
   float Ex, Ey;
   if (k.field_fd) {
-    const Stencil sv = load_varphi_stencil(k, hs, x, y, ld_cg(&ctl->vw_b), ld_cg(&ctl->vw_t));
+    const Stencil sv = load_varphi_stencil(k, hs, x, y, __ldg(&ctl->vw_b), __ldg(&ctl->vw_t));
     float gvx, gvy, lv;
     grad_lap(sv, gvx, gvy, lv);
     Ex = -gvx;
@@ -756,8 +764,21 @@ __device__ __forceinline__ void coupled_body(const KParams& k, StepState* ss, in
                                              float* __restrict__ hist, Ctl* ctl,
                                              const double2* __restrict__ partials,
                                              DevStats* stats, int bid) {
-  const int parity = __ldg(&ctl->parity);  // not written in this pass: one request per SM
-  const StepState sa = ss[cur];
+  // the control words and this step's state are read by every thread and written by no
+  // CTA of the pass (it writes the other state slot): the read-only path, one request
+  // per SM
+  const int parity = __ldg(&ctl->parity);
+  StepState sa;
+  {
+    const StepState* p = ss + cur;
+    sa.n = __ldg(&p->n);
+    sa.first = __ldg(&p->first);
+    sa.pad = 0;
+    sa.cos_b = __ldg(&p->cos_b);
+    sa.cos_t = __ldg(&p->cos_t);
+    sa.vw_b = __ldg(&p->vw_b);
+    sa.vw_t = __ldg(&p->vw_t);
+  }
   if (bid == 0) {
     const int np = ld_cg(&ctl->mpart_n);
     if (np > 0) coupled_reduce_moments(k, partials, np, ctl);
@@ -811,7 +832,10 @@ __global__ void __launch_bounds__(256) k_moments_batch(const StepSlot* __restric
   const int2 w = work[blockIdx.x];
   const StepSlot& S = slots[w.x];
   const Pops P = pops_copy(S.k, S.b, cur);
-  if (S.k.half)
+  if (S.quad)  // the blocks and arithmetic of the slot's own k_moments4<true> launch
+    moments4_body<true>(S.k, S.b.ss + cur, P, S.b.hist, S.b.phi, S.b.aq, S.b.partials, S.b.ctl,
+                        S.tol, S.min_iter, S.max_iter, S.fixed_iter, w.y, S.mblocks);
+  else if (S.k.half)
     moments_body<true>(S.k, S.b.ss + cur, P, S.b.hist, S.b.phi, S.b.aq, S.b.partials, S.b.ctl,
                        S.tol, S.min_iter, S.max_iter, S.fixed_iter, w.y, S.mblocks);
   else
@@ -906,7 +930,7 @@ __global__ void k_fields(KParams k, const StepState* __restrict__ ss, Pops pops,
   const float varphi = hsum * (9.0f / 5.0f);
   float Ex, Ey;
   if (k.field_fd) {
-    const Stencil sv = load_varphi_stencil(k, hs, x, y, ld_cg(&ctl->vw_b), ld_cg(&ctl->vw_t));
+    const Stencil sv = load_varphi_stencil(k, hs, x, y, __ldg(&ctl->vw_b), __ldg(&ctl->vw_t));
     float gvx, gvy, lv;
     grad_lap(sv, gvx, gvy, lv);
     Ex = -gvx;
