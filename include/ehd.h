@@ -242,6 +242,18 @@ int ehd_solve_potential(ehd_sim* sim, double tol, int max_iter, int* iters,
  * Errors: EHD_ERR_INVALID_ARG (null pointer, a bit beyond EHD_F_MU, bad mem). */
 int ehd_read_fields(ehd_sim* sim, unsigned mask, void* const* out, int mem);
 
+/* The contact line of a drop sitting on the bottom wall, from the current populations
+ * (the normalised contact-radius histories of Sec. 7.2, Fig. 11, are radius / its initial
+ * value): on each of the first two lattice rows the crossings of phi = level are placed
+ * by linear interpolation between the outermost nodes with phi >= level and their outside
+ * neighbours, and extrapolated linearly to the wall at y = -1/2.  out[0] = left and
+ * out[1] = right (x in lattice units, node i at x = i), out[2] = radius = (right - left)/2,
+ * all NaN when a row has no node with phi >= level or the drop crosses the periodic seam
+ * (the span reaches x = 0 or x = nx - 1).  Host array of 3 doubles; synchronises the
+ * stream.  Errors: EHD_ERR_INVALID_ARG (null pointer, a lattice without walls in y or
+ * with fewer than 2 rows, a slab, level outside (0, 1)). */
+int ehd_contact_line(ehd_sim* sim, double level, double* out);
+
 /* Complete state (populations, potential distribution, lagged quantities, step counter)
  * as an opaque host blob: ehd_state_bytes gives its size; ehd_save_state fills `buf`;
  * ehd_load_state restores it into a simulation with the same parameters, after which the

@@ -68,7 +68,8 @@ def build(verbose=False, ptxas_info=False, force=False):
         for o in outs:
             print(o)
     tmp = LIB + ".tmp"
-    _run([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs], verbose)
+    # -ldl: the header-only NVTX ranges look their tool up with dlopen
+    _run([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-ldl"], verbose)
     os.replace(tmp, LIB)
     return LIB
 

@@ -671,7 +671,22 @@ void ehd_destroy(ehd_sim* s) {
   delete s;
 }
 
+int ehd_contact_line(ehd_sim* s, double level, double* out) {
+  if (!s || !out || !s->kp.walls || s->kp.ny < 2 || s->kp.slab || !(level > 0.0) ||
+      !(level < 1.0))
+    return EHD_ERR_INVALID_ARG;
+  EHD_CUDA(launch_contact_line(s->kp, s->b, s->cur, (float)level, s->stream));
+  double2 r[2];
+  EHD_CUDA(cudaMemcpyAsync(r, s->b.partials, sizeof(r), cudaMemcpyDeviceToHost, s->stream));
+  EHD_CUDA(cudaStreamSynchronize(s->stream));
+  out[0] = r[0].x;
+  out[1] = r[0].y;
+  out[2] = r[1].x;
+  return EHD_OK;
+}
+
 int ehd_solve_potential(ehd_sim* s, double tol, int max_iter, int* iters, double* rel_change) {
+  NvtxRange range("ehd_solve_potential");
   if (!s) return EHD_ERR_INVALID_ARG;
   const ehd_params& P = s->P;
   const double t = tol > 0 ? tol : P.poisson_tol;
@@ -693,6 +708,7 @@ int ehd_set_fields(ehd_sim* s, const void* phi, const void* q, const void* ux, c
                    const void* p, int mem) {
   if (!s || !phi || !q || !ux || !uy || (mem != EHD_HOST && mem != EHD_DEVICE))
     return EHD_ERR_INVALID_ARG;
+  NvtxRange range("ehd_set_fields");
   int st;
   double m_phi, m_q, m_ux, m_uy, m_p;
   if ((st = stage_in(s, phi, 0, mem, &m_phi)) != EHD_OK) return st;
@@ -757,6 +773,7 @@ static int reset_stats(ehd_sim* s) {
 
 int ehd_step(ehd_sim* s, int nsteps, ehd_stats* out) {
   if (!s || nsteps < 0) return EHD_ERR_INVALID_ARG;
+  NvtxRange range("ehd_step");
   const ehd_params& P = s->P;
   int status = EHD_OK;
   if (out || !s->stats_live) {
@@ -795,13 +812,21 @@ int ehd_step(ehd_sim* s, int nsteps, ehd_stats* out) {
       EHD_CUDA(cudaGraphLaunch(s->exec[s->cur], s->stream));
       s->graph_steps += 1;
     } else {
-      EHD_LAUNCH(s, 0, launch_moments(s->kp, s->b, s->cur, P.poisson_tol, P.poisson_min_iter,
-                                       P.poisson_max_iter, P.poisson_fixed_iter, s->stream,
-                                       s->resident_ok));
-      const int st = run_potential_loop(s, P.poisson_fixed_iter, P.poisson_max_iter);
+      {
+        NvtxRange r("moments");
+        EHD_LAUNCH(s, 0, launch_moments(s->kp, s->b, s->cur, P.poisson_tol,
+                                         P.poisson_min_iter, P.poisson_max_iter,
+                                         P.poisson_fixed_iter, s->stream, s->resident_ok));
+      }
+      int st;
+      {
+        NvtxRange r("potential loop");
+        st = run_potential_loop(s, P.poisson_fixed_iter, P.poisson_max_iter);
+      }
       if (st == EHD_ERR_CUDA || st == EHD_ERR_TIMEOUT) return st;
       if (st != EHD_OK) status = st;
       if (!s->resident_ok) s->host_iters += s->h_ctl->iter;
+      NvtxRange r("coupled");
       EHD_LAUNCH(s, 3, launch_coupled(s->kp, s->b, s->cur, s->stream));
     }
     s->cur ^= 1;
@@ -849,6 +874,7 @@ int ehd_read_stats(ehd_sim* s, ehd_stats* out) {
 }
 
 int ehd_read_fields(ehd_sim* s, unsigned mask, void* const* out, int mem) {
+  NvtxRange range("ehd_read_fields");
   if (!s || !out || (mem != EHD_HOST && mem != EHD_DEVICE) || (mask & ~((1u << EHD_NUM_FIELDS) - 1u)))
     return EHD_ERR_INVALID_ARG;
   if (!mask) return EHD_OK;

@@ -454,6 +454,7 @@ int ehd_batch_admit(ehd_batch* b, const ehd_params* params, const double* phi, c
 }
 
 int ehd_batch_run(ehd_batch* b, int nsteps) {
+  NvtxRange range("ehd_batch_run");
   if (!b || nsteps < 1) return EHD_ERR_INVALID_ARG;
   if (b->dirty) {
     const int st = rebuild(b);

@@ -534,6 +534,9 @@ cudaError_t launch_expire_barrier(const Buffers& b, cudaStream_t st);
 cudaError_t launch_fields(const KParams& kp, const Buffers& b, int cur, unsigned mask,
                           cudaStream_t st);
 cudaError_t launch_phi_now(const KParams& kp, const Buffers& b, int cur, cudaStream_t st);
+// The contact line on the bottom wall into b.partials[0..1] (see k_contact_line).
+cudaError_t launch_contact_line(const KParams& kp, const Buffers& b, int cur, float level,
+                                cudaStream_t st);
 cudaError_t launch_fields_from_phi(const KParams& kp, const Buffers& b, int cur, unsigned mask,
                                    cudaStream_t st);
 cudaError_t add_poisson_node_nocond(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,

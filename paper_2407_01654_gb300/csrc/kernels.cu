@@ -879,6 +879,67 @@ __global__ void k_stats_reset(DevStats* s) {
 // Output fields.  k_phi_now: phi of the current populations; k_fields: the requested
 // fields (order of the mask bits) into io[slot][N].
 // ------------------------------------------------------------------------------------
+// The contact line of a drop sitting on the bottom wall (the contact-radius histories of
+// Sec. 7.2, Fig. 11): on each of the first two lattice rows, the nodes with phi >= level
+// (current populations, phi as every pass forms it) span [a, b]; the crossings are placed
+// by linear interpolation with the outside neighbours, a - (phi_a - level) / (phi_a -
+// phi_{a-1}) and b + (phi_b - level) / (phi_b - phi_{b+1}), and each is extrapolated
+// linearly from rows 0 and 1 to the wall at y = -1/2.  One CTA; out[0] = (left, right),
+// out[1] = (radius = (right - left) / 2, 1), or NaNs and 0 when a row has no such node or
+// the span reaches an end of the row (a drop across the periodic seam).
+template <bool HALF>
+__global__ void __launch_bounds__(256) k_contact_line(KParams k, Pops pops, float level,
+                                                      double2* __restrict__ out) {
+  __shared__ int s_lo[2], s_hi[2];
+  if (threadIdx.x < 2) {
+    s_lo[threadIdx.x] = 0x7fffffff;
+    s_hi[threadIdx.x] = -1;
+  }
+  __syncthreads();
+  for (int r = 0; r < 2; ++r)
+    for (int x = threadIdx.x; x < k.nx; x += blockDim.x)
+      if (phi_of<HALF>(k, pops, (size_t)r * k.nx + x) >= level) {
+        atomicMin(&s_lo[r], x);
+        atomicMax(&s_hi[r], x);
+      }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  double left[2], right[2];
+  bool ok = true;
+  for (int r = 0; r < 2 && ok; ++r) {
+    const int a = s_lo[r], b = s_hi[r];
+    if (b < 0 || a == 0 || b == k.nx - 1) {
+      ok = false;
+      break;
+    }
+    const size_t row = (size_t)r * k.nx;
+    const double pa = phi_of<HALF>(k, pops, row + a), pam = phi_of<HALF>(k, pops, row + a - 1);
+    const double pb = phi_of<HALF>(k, pops, row + b), pbp = phi_of<HALF>(k, pops, row + b + 1);
+    left[r] = (double)a - (pa - (double)level) / (pa - pam);
+    right[r] = (double)b + (pb - (double)level) / (pb - pbp);
+  }
+  if (!ok) {
+    out[0] = make_double2(nan, nan);
+    out[1] = make_double2(nan, 0.0);
+    return;
+  }
+  const double l = left[0] + 0.5 * (left[0] - left[1]);
+  const double rr = right[0] + 0.5 * (right[0] - right[1]);
+  out[0] = make_double2(l, rr);
+  out[1] = make_double2(0.5 * (rr - l), 1.0);
+}
+
+cudaError_t launch_contact_line(const KParams& kp, const Buffers& b, int cur, float level,
+                                cudaStream_t st) {
+  const Pops P = pops_copy(kp, b, cur);
+  if (kp.half)
+    k_contact_line<true><<<1, 256, 0, st>>>(kp, P, level, b.partials);
+  else
+    k_contact_line<false><<<1, 256, 0, st>>>(kp, P, level, b.partials);
+  return cudaGetLastError();
+}
+
 template <bool HALF>
 __global__ void k_phi_now(KParams k, Pops pops, float* __restrict__ out) {
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;

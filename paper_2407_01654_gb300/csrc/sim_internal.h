@@ -1,10 +1,23 @@
 // The simulation object behind the C ABI's ehd_sim handle, shared by api.cu and batch.cu.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <vector>
 
 #include "../../include/ehd.h"
 #include "ehd_internal.cuh"
+
+// A named NVTX range over a scope: the host-side phases of the library (each API call,
+// and the moments pass, potential loop and coupled pass of steps queued from the host) on
+// an Nsight timeline.  Header-only NVTX: without a tool attached each push / pop is a
+// check of one pointer.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 struct ehd_sim {
   using KParams = ehd::KParams;

@@ -126,6 +126,8 @@ SIGNATURES = {
                                            ctypes.POINTER(ctypes.c_double)]),
     "ehd_read_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint,
                                        ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
+    "ehd_contact_line": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double,
+                                        ctypes.POINTER(ctypes.c_double)]),
     "ehd_state_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "ehd_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "ehd_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
@@ -355,6 +357,13 @@ class Sim:
         arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
         _check(lib().ehd_read_fields(self._h, mask, arr, mem), "ehd_read_fields")
         return dict(zip(order, outs))
+
+    def contact_line(self, level=0.5):
+        """Contact line of a drop on the bottom wall: dict left, right, radius (lattice
+        units; NaN when there is none or it crosses the periodic seam)."""
+        out = (ctypes.c_double * 3)()
+        _check(lib().ehd_contact_line(self._h, float(level), out), "ehd_contact_line")
+        return {"left": out[0], "right": out[1], "radius": out[2]}
 
     def profile(self, enable=True):
         _check(lib().ehd_profile(self._h, 1 if enable else 0), "ehd_profile")

@@ -138,3 +138,24 @@ def cap_contact_angle(phi, wall_row=0, level=0.5):
     w1 = width_at(1)
     base = w0 + 0.5 * (w0 - w1)
     return math.degrees(2.0 * math.atan(2.0 * h / base))
+
+
+def cap_contact_line(phi, level=0.5):
+    """Contact line of a drop on the bottom wall (at y = -1/2) from a [ny, nx] phi field:
+    on rows 0 and 1, the crossings of phi = level interpolated linearly between the
+    outermost nodes with phi >= level and their outside neighbours, each extrapolated
+    linearly to the wall.  Returns (left, right, radius); NaNs when a row has no such node
+    or the span reaches an end of the row."""
+    ends = []
+    for r in (0, 1):
+        row = np.asarray(phi[r], dtype=np.float64)
+        inside = np.where(row >= level)[0]
+        if inside.size == 0 or inside.min() == 0 or inside.max() == row.size - 1:
+            return (math.nan, math.nan, math.nan)
+        a, b = int(inside.min()), int(inside.max())
+        left = a - (row[a] - level) / (row[a] - row[a - 1])
+        right = b + (row[b] - level) / (row[b] - row[b + 1])
+        ends.append((left, right))
+    left = ends[0][0] + 0.5 * (ends[0][0] - ends[1][0])
+    right = ends[0][1] + 0.5 * (ends[0][1] - ends[1][1])
+    return (left, right, 0.5 * (right - left))

@@ -129,3 +129,33 @@ def test_electrowetting_young_lippmann(gpu):
         assert np.abs(c - (cy + e)).max() < 0.02
         fits.append(np.array([p[1] for p in pts]))
     assert np.abs(fits[0] - fits[1]).max() < 0.5
+
+
+def test_contact_line_tracking(gpu):
+    """ehd_contact_line (the contact-radius histories of Sec. 7.2, Fig. 11) on the device
+    equals the numpy extraction of the same phi read back, at set-up and along a run of
+    the reversed-electrowetting sessile drop (ramped potential, 128 x 64, r = 20); the
+    set-up radius is the cap's closed form to 0.05; a wall without drop gives NaN."""
+    p, f, _ = wl.sessile_drop(seed=2, nx=128, ny=64, r=20.0, ramp_steps=2000)
+    g = gpu.Sim(p)
+    g.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
+    r0 = None
+    for k in range(4):
+        if k:
+            g.step(100)
+        got = g.contact_line()
+        ref = an.cap_contact_line(g.read_fields(("phi",))["phi"])
+        assert got["left"] == pytest.approx(ref[0], abs=1e-9)
+        assert got["right"] == pytest.approx(ref[1], abs=1e-9)
+        assert got["radius"] == pytest.approx(ref[2], abs=1e-9)
+        if r0 is None:
+            r0 = got["radius"]
+            # the set-up is a half-disc of radius 20 centred on the wall
+            assert abs(r0 - 20.0) < 0.05
+        assert 0.5 * r0 < got["radius"] < 1.5 * r0
+    g.close()
+    z = np.zeros((64, 128))
+    e = gpu.Sim(p)
+    e.set_fields(z, z, z, z)
+    assert all(math.isnan(v) for v in e.contact_line().values())
+    e.close()
