@@ -365,6 +365,19 @@ class Sim:
         _check(lib().ehd_contact_line(self._h, float(level), out), "ehd_contact_line")
         return {"left": out[0], "right": out[1], "radius": out[2]}
 
+    def contact_radius_history(self, total_steps, every, level=0.5):
+        """Runs total_steps steps and returns [(steps run, radius)] of the contact line on
+        the bottom wall, at the start and after every `every` steps (the histories of Sec.
+        7.2, Fig. 11, normalise radius by its first value)."""
+        out = [(0, self.contact_line(level)["radius"])]
+        done = 0
+        while done < total_steps:
+            n = min(every, total_steps - done)
+            self.step(n, stats=False)
+            done += n
+            out.append((done, self.contact_line(level)["radius"]))
+        return out
+
     def profile(self, enable=True):
         _check(lib().ehd_profile(self._h, 1 if enable else 0), "ehd_profile")
 
