@@ -104,10 +104,10 @@ RECORDED_TRAFFIC = {
     # one potential solve of the two-step loop (about 380 sub-iterations on the captured
     # spin-up step; the solve's DRAM traffic does not grow with them): 21.022 MB read,
     # 0.035 MB written
-    "k_poisson_resident2": (21057280, "f9f13bd821681553"),
-    # one coupled pass, caches flushed before the launch: 90.249 MB read, 15.439 MB written
+    "k_poisson_resident2": (21056768, "8adaa3938685046a"),
+    # one coupled pass, caches flushed before the launch: 90.245 MB read, 15.035 MB written
     # back during the launch (the rest of its writes leave L2 later)
-    "k_coupled": (105688064, "61ffe24fb0d5ff29"),
+    "k_coupled": (105280256, "4c3f74e1ec68f400"),
 }
 
 
