@@ -175,8 +175,8 @@ struct BatchLaunch {
   int2* work;
   StepSlot* step;
   int2* mwork;
-  int2* cwork;
-  int nm, nc;
+  int2* cwork;       // the FP32 slots' coupled blocks, then the FP16 slots'
+  int nm, nc, nc16;  // nc16 of the nc items are of FP16 slots
 };
 
 // Appends one batch step from copy `cur` after `dep` (null: no dependency); its last node
@@ -201,7 +201,17 @@ cudaError_t add_batch_step(cudaGraph_t g, const BatchLaunch& L, int cur,
   if ((e = cudaGraphKernelNodeSetAttribute(rn, cudaLaunchAttributeCooperative, &v)) !=
       cudaSuccess)
     return e;
-  return add_coupled_batch_node(g, &rn, 1, last, L.step, L.cwork, L.nc, cur);
+  // the coupled pass in one launch per storage precision present (the two touch
+  // disjoint slots)
+  const int n32 = L.nc - L.nc16;
+  if (n32 > 0 && L.nc16 > 0) {
+    cudaGraphNode_t c32;
+    if ((e = add_coupled_batch_node(g, &rn, 1, &c32, L.step, L.cwork, n32, cur, false)) !=
+        cudaSuccess)
+      return e;
+    return add_coupled_batch_node(g, &c32, 1, last, L.step, L.cwork + n32, L.nc16, cur, true);
+  }
+  return add_coupled_batch_node(g, &rn, 1, last, L.step, L.cwork, L.nc, cur, L.nc16 > 0);
 }
 
 // A graph of `nsteps` batch steps starting from copy `cur`, instantiated.
@@ -233,7 +243,7 @@ int rebuild(ehd_batch* b) {
   // lists of the three launches
   std::vector<ResidentSlot> rs(live.size());
   std::vector<StepSlot> ss(live.size());
-  std::vector<int2> work, mwork, cwork;
+  std::vector<int2> work, mwork, cwork, cwork16;
   for (size_t j = 0; j < live.size(); ++j) {
     ehd_sim* s = b->slots[live[j]].sim;
     ResidentSlot& r = rs[j];
@@ -257,8 +267,10 @@ int rebuild(ehd_batch* b) {
     q.mblocks = q.quad ? (s->kp.N / 4 + 255) / 256 : moments_blocks(s->kp.N);
     for (int t = 0; t < q.mblocks; ++t) mwork.push_back(make_int2((int)j, t));
     const int cb = (s->kp.N + 127) / 128;
-    for (int t = 0; t < cb; ++t) cwork.push_back(make_int2((int)j, t));
+    for (int t = 0; t < cb; ++t) (s->kp.half ? cwork16 : cwork).push_back(make_int2((int)j, t));
   }
+  const int nc16 = (int)cwork16.size();
+  cwork.insert(cwork.end(), cwork16.begin(), cwork16.end());
   if ((int)work.size() > b->tile_capacity || (int)mwork.size() > b->mwork_cap ||
       (int)cwork.size() > b->cwork_cap)
     return EHD_ERR_BUSY;
@@ -286,6 +298,7 @@ int rebuild(ehd_batch* b) {
   L.cwork = b->d_cwork;
   L.nm = (int)mwork.size();
   L.nc = (int)cwork.size();
+  L.nc16 = nc16;
   for (int c = 0; c < 2; ++c) {
     int st = build_batch_graph(L, c, 1, &b->exec[c]);
     if (st == EHD_OK) st = build_batch_graph(L, c, b->steps_per_graph, &b->execm[c]);

@@ -496,9 +496,10 @@ __host__ __device__ inline bool moments4_ok(const KParams& kp) {
 cudaError_t add_moments_batch_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
                                    cudaGraphNode_t* out, const StepSlot* slots, const int2* work,
                                    int nwork, int cur);
+// half: the work items are of FP16-storage slots (the pass's FP16 form), else FP32.
 cudaError_t add_coupled_batch_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
                                    cudaGraphNode_t* out, const StepSlot* slots, const int2* work,
-                                   int nwork, int cur);
+                                   int nwork, int cur, bool half);
 
 // Resident potential loop (poisson_resident.cu).  fixed_ty > 0: tiles of 64 x fixed_ty
 // (a multiple of 8 up to 64).

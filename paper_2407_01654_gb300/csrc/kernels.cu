@@ -843,17 +843,18 @@ __global__ void __launch_bounds__(256) k_moments_batch(const StepSlot* __restric
                         S.tol, S.min_iter, S.max_iter, S.fixed_iter, w.y, S.mblocks);
 }
 
-__global__ void __launch_bounds__(128) k_coupled_batch(const StepSlot* __restrict__ slots,
-                                                       const int2* __restrict__ work, int cur) {
+// One form per storage precision, each over the work items of its slots: the FP32 form
+// has the register budget of the single-simulation FP32 pass (7 CTAs per SM), which a
+// kernel holding both forms could not have.
+template <bool HALF>
+__global__ void __launch_bounds__(128, HALF ? 1 : EHD_COUPLED_MIN_CTAS)
+    k_coupled_batch(const StepSlot* __restrict__ slots, const int2* __restrict__ work,
+                    int cur) {
   const int2 w = work[blockIdx.x];
   const StepSlot& S = slots[w.x];
   const Pops Pi = pops_copy(S.k, S.b, cur), Po = pops_copy(S.k, S.b, cur ^ 1);
-  if (S.k.half)
-    coupled_body<true>(S.k, S.b.ss, cur, Pi, Po, S.b.phi, S.b.h, S.b.hist, S.b.ctl,
-                       S.b.partials, S.b.stats, w.y);
-  else
-    coupled_body<false>(S.k, S.b.ss, cur, Pi, Po, S.b.phi, S.b.h, S.b.hist, S.b.ctl,
-                        S.b.partials, S.b.stats, w.y);
+  coupled_body<HALF>(S.k, S.b.ss, cur, Pi, Po, S.b.phi, S.b.h, S.b.hist, S.b.ctl, S.b.partials,
+                     S.b.stats, w.y);
 }
 
 // Diagnostics: puts the grid barrier's arrival count half the counter range behind every
@@ -1190,8 +1191,10 @@ cudaError_t add_moments_batch_node(cudaGraph_t g, const cudaGraphNode_t* deps, s
 
 cudaError_t add_coupled_batch_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd,
                                    cudaGraphNode_t* out, const StepSlot* slots, const int2* work,
-                                   int nwork, int cur) {
-  return add_batch_node(g, deps, nd, out, (void*)k_coupled_batch, 128, slots, work, nwork, cur);
+                                   int nwork, int cur, bool half) {
+  return add_batch_node(g, deps, nd, out,
+                        half ? (void*)k_coupled_batch<true> : (void*)k_coupled_batch<false>, 128,
+                        slots, work, nwork, cur);
 }
 
 cudaError_t add_poisson_node(cudaGraph_t g, cudaGraphNode_t* out, const KParams& kp,
