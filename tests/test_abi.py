@@ -135,3 +135,13 @@ def test_slabs_create_rejects_bad_arguments(L, change, nslabs):
     h = ctypes.c_void_p()
     assert L.ehd_slabs_create(ctypes.byref(p), nslabs, None, ctypes.byref(h)) == 1
     assert not h.value
+
+
+def test_null_handles_are_refused(L):
+    """Entry points given a null simulation handle return EHD_ERR_INVALID_ARG (1) without
+    touching the device."""
+    out = (ctypes.c_double * 3)()
+    assert L.ehd_contact_line(None, ctypes.c_double(0.5), out) == 1
+    assert L.ehd_step(None, 1, None) == 1
+    assert L.ehd_use_graphs(None, 1) == 1
+    assert L.ehd_read_fields(None, 1, None, 0) == 1

@@ -159,3 +159,11 @@ def test_contact_line_tracking(gpu):
     e.set_fields(z, z, z, z)
     assert all(math.isnan(v) for v in e.contact_line().values())
     e.close()
+    # a lattice periodic in y has no wall to find a contact line on
+    pb, fb, _, _ = wl.gaussian_bell(N=32)
+    b = gpu.Sim(pb)
+    b.set_fields(fb["phi"], fb["q"], fb["ux"], fb["uy"])
+    with pytest.raises(gpu.EhdError) as err:
+        b.contact_line()
+    assert err.value.code == 1
+    b.close()
