@@ -254,6 +254,15 @@ int ehd_read_fields(ehd_sim* sim, unsigned mask, void* const* out, int mem);
  * with fewer than 2 rows, a slab, level outside (0, 1)). */
 int ehd_contact_line(ehd_sim* sim, double level, double* out);
 
+/* Debugging (no counterpart in the paper): in the index-checking build
+ * (libehd_checked.so, `python -m paper_2407_01654_gb300.build --checked`) the kernels test
+ * every index they form from lattice coordinates, for the population, potential,
+ * history and phi fields, against the field's size, and count and clamp any out of
+ * range; *count receives this simulation's count since it was created.  In the normal
+ * build nothing is counted and *count is 0.  Synchronises the stream.
+ * Errors: EHD_ERR_INVALID_ARG (null pointer). */
+int ehd_diag_index_errors(ehd_sim* sim, unsigned* count);
+
 /* Complete state (populations, potential distribution, lagged quantities, step counter)
  * as an opaque host blob: ehd_state_bytes gives its size; ehd_save_state fills `buf`;
  * ehd_load_state restores it into a simulation with the same parameters, after which the

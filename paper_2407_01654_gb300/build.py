@@ -2,7 +2,11 @@
 
 Each translation unit is compiled by nvcc in parallel, then linked into one shared
 library with the CUDA runtime linked statically.  Usage: python -m
-paper_2407_01654_gb300.build [--verbose] [--ptxas-info]
+paper_2407_01654_gb300.build [--verbose] [--ptxas-info] [--checked]
+
+--checked builds libehd_checked.so instead (-DEHD_CHECKED): the kernels test the indices
+they form from lattice coordinates, count any out of range (ehd_diag_index_errors) and
+clamp it, for debugging; it is slower and not what the benchmark runs.
 """
 from __future__ import annotations
 
@@ -17,6 +21,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libehd.so")
+LIB_CHECKED = os.path.join(HERE, "libehd_checked.so")
 SOURCES = ["kernels.cu", "poisson.cu", "poisson_resident.cu", "noalloc.cu", "batch.cu", "api.cu",
            "diag.cu", "slabs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -45,20 +50,25 @@ def _run(cmd, verbose):
     return r.stdout + r.stderr
 
 
-def build(verbose=False, ptxas_info=False, force=False):
-    """Compiles the library if a source is newer than it (or force).  Returns its path."""
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(verbose=False, ptxas_info=False, force=False, checked=False):
+    """Compiles the library if a source is newer than it (or force).  Returns its path.
+    checked: the index-checking debug build (libehd_checked.so)."""
+    lib = LIB_CHECKED if checked else LIB
+    bdir = BUILD_DIR + ("_checked" if checked else "")
+    os.makedirs(bdir, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     deps = srcs + [os.path.join(CSRC, "ehd_internal.cuh"), os.path.join(CSRC, "sim_internal.h"),
                    os.path.join(ROOT, "include", "ehd.h"), os.path.abspath(__file__)]
-    if (not force and os.path.exists(LIB)
-            and all(os.path.getmtime(LIB) >= os.path.getmtime(d) for d in deps)):
-        return LIB
+    if (not force and os.path.exists(lib)
+            and all(os.path.getmtime(lib) >= os.path.getmtime(d) for d in deps)):
+        return lib
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    if checked:
+        extra = extra + ["-DEHD_CHECKED"]
     objs = []
     cmds = []
     for s in srcs:
-        o = os.path.join(BUILD_DIR, os.path.basename(s).replace(".cu", ".o"))
+        o = os.path.join(bdir, os.path.basename(s).replace(".cu", ".o"))
         objs.append(o)
         cmds.append([nvcc(), *ARCH, *FLAGS, *FILE_FLAGS.get(os.path.basename(s), []), *extra,
                      "-c", s, "-o", o])
@@ -67,13 +77,13 @@ def build(verbose=False, ptxas_info=False, force=False):
     if ptxas_info:
         for o in outs:
             print(o)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     # -ldl: the header-only NVTX ranges look their tool up with dlopen
     _run([nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-ldl"], verbose)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(verbose="--verbose" in sys.argv, ptxas_info="--ptxas-info" in sys.argv, force=True)
-    print(LIB)
+    print(build(verbose="--verbose" in sys.argv, ptxas_info="--ptxas-info" in sys.argv,
+                force=True, checked="--checked" in sys.argv))

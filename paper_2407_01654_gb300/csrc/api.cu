@@ -481,7 +481,11 @@ void choose_scales(ehd_sim* s, double qmax, double umax) {
 
 extern "C" {
 
+#ifdef EHD_CHECKED
+const char* ehd_version(void) { return "ehd-gb300 0.1 (sm_103a, checked indices)"; }
+#else
 const char* ehd_version(void) { return "ehd-gb300 0.1 (sm_103a)"; }
+#endif
 
 int ehd_abi_sizes(size_t* params_bytes, size_t* stats_bytes) {
   if (params_bytes) *params_bytes = sizeof(ehd_params);
@@ -564,6 +568,7 @@ int sim_create(const ehd_params* params, void* workspace, size_t workspace_bytes
   s->b.stats = reinterpret_cast<DevStats*>(base + L.stats);
   s->b.exports = reinterpret_cast<float*>(base + L.exports);
   s->b.rpartials = reinterpret_cast<float2*>(base + L.rpartials);
+  s->kp.oob = &s->b.ctl->oob;
   // resident potential loop: needs cooperative launch, one tile per SM on this device,
   // and an export area within the reserved space
   {
@@ -669,6 +674,14 @@ void ehd_destroy(ehd_sim* s) {
   if (s->h_stats) cudaFreeHost(s->h_stats);
   if (s->h_stage) cudaFreeHost(s->h_stage);
   delete s;
+}
+
+int ehd_diag_index_errors(ehd_sim* s, unsigned* count) {
+  if (!s || !count) return EHD_ERR_INVALID_ARG;
+  EHD_CUDA(cudaMemcpyAsync(count, &s->b.ctl->oob, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                           s->stream));
+  EHD_CUDA(cudaStreamSynchronize(s->stream));
+  return EHD_OK;
 }
 
 int ehd_contact_line(ehd_sim* s, double level, double* out) {

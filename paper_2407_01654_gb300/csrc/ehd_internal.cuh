@@ -115,7 +115,25 @@ struct KParams {
   int half;
   float psc[3];             // S_f
   float ipsc[3];            // 1 / S_f
+  unsigned* oob;            // checked build: where out-of-range indices are counted
 };
+
+// Checked build (-DEHD_CHECKED; no counterpart in the paper): the indices the per-node
+// helpers, the stencil loads, the coupled pass's stores and the two-step loop's state
+// loads and stores form from lattice coordinates are tested against their field's size;
+// one out of range is counted at k.oob and replaced by 0, so the run goes on without
+// touching memory outside the field (no trap: a failing device assert is not an option on
+// a shared GPU).  Other builds compile EHD_IDX to the index itself.
+#ifdef EHD_CHECKED
+__device__ __forceinline__ size_t checked_index(const KParams& k, size_t i, size_t n) {
+  if (i < n) return i;
+  if (k.oob) atomicAdd(k.oob, 1u);
+  return 0;
+}
+#define EHD_IDX(k, i, n) ::ehd::checked_index((k), (size_t)(i), (size_t)(n))
+#else
+#define EHD_IDX(k, i, n) ((size_t)(i))
+#endif
 
 // One copy of the g, l, f populations.  FP32: p32 = [28][N] (the 27 populations, then the
 // low part of g_0).  FP16: p32 = rest populations [3][N] and the low part of g_0, p16 =
@@ -133,6 +151,7 @@ template <bool HALF>
 __device__ __forceinline__ float ld_pop(const KParams& k, const Pops& P, int field, int i,
                                         size_t idx) {
   const size_t N = (size_t)k.N;
+  idx = EHD_IDX(k, idx, N);
   if (!HALF) return __ldg(P.p32 + (size_t)(field * 9 + i) * N + idx);
   if (i == 0) return __ldg(P.p32 + (size_t)field * N + idx);
   const __half v = P.p16[(size_t)(field * 8 + i - 1) * N + idx];
@@ -142,6 +161,7 @@ __device__ __forceinline__ float ld_pop(const KParams& k, const Pops& P, int fie
 template <bool HALF>
 __device__ __forceinline__ void st_pop(const KParams& k, const Pops& P, int field, int i,
                                        size_t idx, float v) {
+  idx = EHD_IDX(k, idx, k.N);
   const size_t N = (size_t)k.N;
   if (!HALF) {
     // the hydrodynamic populations are read only by the next coupled pass: stored
@@ -160,10 +180,12 @@ __device__ __forceinline__ void st_pop(const KParams& k, const Pops& P, int fiel
 // The low part of the rest Cahn-Hilliard population g_0 = hi + lo (hi is population (0, 0)).
 template <bool HALF>
 __device__ __forceinline__ float ld_g0_lo(const KParams& k, const Pops& P, size_t idx) {
+  idx = EHD_IDX(k, idx, k.N);
   return __ldg(P.p32 + (size_t)(HALF ? 3 : NPOP) * k.N + idx);
 }
 template <bool HALF>
 __device__ __forceinline__ void st_g0_lo(const KParams& k, const Pops& P, size_t idx, float v) {
+  idx = EHD_IDX(k, idx, k.N);
   P.p32[(size_t)(HALF ? 3 : NPOP) * k.N + idx] = v;
 }
 // Stores a population and returns the value a later ld_pop of it reads (with FP16 storage
@@ -171,6 +193,7 @@ __device__ __forceinline__ void st_g0_lo(const KParams& k, const Pops& P, size_t
 template <bool HALF>
 __device__ __forceinline__ float st_pop_read(const KParams& k, const Pops& P, int field, int i,
                                              size_t idx, float v) {
+  idx = EHD_IDX(k, idx, k.N);
   const size_t N = (size_t)k.N;
   if (!HALF || i == 0) {
     st_pop<HALF>(k, P, field, i, idx, v);
@@ -274,7 +297,7 @@ struct Ctl {
   double slab_num, slab_den;// one slab's stopping sums of its last sub-iteration
   int mpart_n;              // > 0: the moments pass left its FP64 sums as this many
                             // per-CTA partials, reduced by the coupled pass
-  int pad2;
+  unsigned oob;             // checked build: out-of-range indices met (see EHD_IDX)
 };
 
 // Tiling of the resident potential loop: ntx x nty tiles of TX x TY nodes (the last

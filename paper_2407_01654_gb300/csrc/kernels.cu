@@ -25,6 +25,13 @@ __device__ __forceinline__ float ghost(float v, float a_cos) { return v + a_cos 
 __device__ __forceinline__ Stencil load_stencil(const KParams& k, const StepState& sa,
                                                 const float* __restrict__ phi, int x, int y) {
   const int nx = k.nx, ny = k.ny;
+#ifdef EHD_CHECKED
+  if (x < 0 || x >= nx || y < 0 || y >= ny) {  // never in a correct launch
+    checked_index(k, 1, 0);
+    x = 0;
+    y = 0;
+  }
+#endif
   if (x > 0 && x + 1 < nx && y > 0 && y + 1 < ny) {
     // away from every edge: the 3 x 3 neighbourhood at fixed offsets
     const float* r = phi + (size_t)(y + k.row0) * nx + x;
@@ -482,14 +489,17 @@ struct GlobalSrc {
   int idx;
   __device__ __forceinline__ float pop(int field, int i) const {
     return HALF ? ld_pop<HALF>(k, pin, field, i, idx)
-                : __ldcs(pin.p32 + (size_t)(field * 9 + i) * k.N + idx);
+                : __ldcs(pin.p32 + (size_t)(field * 9 + i) * k.N + EHD_IDX(k, idx, k.N));
   }
   __device__ __forceinline__ float g0_lo() const {
-    return HALF ? ld_g0_lo<HALF>(k, pin, idx) : __ldcs(pin.p32 + (size_t)NPOP * k.N + idx);
+    return HALF ? ld_g0_lo<HALF>(k, pin, idx)
+                : __ldcs(pin.p32 + (size_t)NPOP * k.N + EHD_IDX(k, idx, k.N));
   }
-  __device__ __forceinline__ float h(int i) const { return __ldg(hs + i * (size_t)k.N + idx); }
+  __device__ __forceinline__ float h(int i) const {
+    return __ldg(hs + i * (size_t)k.N + EHD_IDX(k, idx, k.N));
+  }
   __device__ __forceinline__ float hist_in(int j) const {
-    return __ldcs(hist + j * (size_t)k.N + idx);
+    return __ldcs(hist + j * (size_t)k.N + EHD_IDX(k, idx, k.N));
   }
 };
 
@@ -714,6 +724,7 @@ __device__ __forceinline__ void coupled_node(const KParams& k, const StepState& 
     st_pop<HALF>(k, pout, 1, dir, t, ln);
     st_pop<HALF>(k, pout, 2, dir, t, fn);
   }
+  idx = (int)EHD_IDX(k, idx, k.N);
   __stcs(hist + idx, s_adv);
   __stcs(hist + (size_t)N + idx, Jx);
   __stcs(hist + 2 * (size_t)N + idx, Jy);

@@ -664,7 +664,7 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
   float2 tc[NPT];
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
-    const int g = valid(s) ? (ty0 + ly0 + s * T::ROWS) * nx + tx0 + lx : 0;
+    const int g = (int)EHD_IDX(k, valid(s) ? (ty0 + ly0 + s * T::ROWS) * nx + tx0 + lx : 0, N);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const float v = hsrc[i * N + g];
@@ -748,7 +748,7 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
       rtw = k.walls && gy == ny - 1;
       // first import: the lattice's own post-stream state; coefficients once per solve
       const int gx = (tx0 + x + nx) % nx;
-      const int g = ((gy + ny) % ny) * nx + gx;
+      const int g = (int)EHD_IDX(k, ((gy + ny) % ny) * nx + gx, N);
 #pragma unroll
       for (int i = 0; i < 8; ++i) ring[i * T::NR + threadIdx.x] = hsrc[i * N + g];
       const float2 c = aq[g];
@@ -1089,7 +1089,7 @@ __device__ __forceinline__ void resident_loop2(const KParams& k, const ResidentG
 #pragma unroll
   for (int s = 0; s < NPT; ++s) {
     if (!valid(s)) continue;
-    const int g = (ty0 + ly0 + s * T::ROWS) * nx + tx0 + lx;
+    const int g = (int)EHD_IDX(k, (ty0 + ly0 + s * T::ROWS) * nx + tx0 + lx, N);
 #pragma unroll
     for (int i = 0; i < 8; ++i) hsrc[i * N + g] = (s & 1) ? h[s >> 1][i].y : h[s >> 1][i].x;
   }

@@ -128,6 +128,7 @@ SIGNATURES = {
                                        ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]),
     "ehd_contact_line": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double,
                                         ctypes.POINTER(ctypes.c_double)]),
+    "ehd_diag_index_errors": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint)]),
     "ehd_state_bytes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]),
     "ehd_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "ehd_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
@@ -364,6 +365,12 @@ class Sim:
         out = (ctypes.c_double * 3)()
         _check(lib().ehd_contact_line(self._h, float(level), out), "ehd_contact_line")
         return {"left": out[0], "right": out[1], "radius": out[2]}
+
+    def index_errors(self):
+        """Out-of-range indices the index-checking build met (always 0 otherwise)."""
+        n = ctypes.c_uint()
+        _check(lib().ehd_diag_index_errors(self._h, ctypes.byref(n)), "ehd_diag_index_errors")
+        return n.value
 
     def contact_radius_history(self, total_steps, every, level=0.5):
         """Runs total_steps steps and returns [(steps run, radius)] of the contact line on
