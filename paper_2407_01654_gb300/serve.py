@@ -36,6 +36,7 @@ class Request:
     iters: int = 0
     steady: bool = False
     capped: bool = False
+    failed: str = ""            # why the request ended without a result ("" if it did not)
     rel_change: tuple = (math.nan, math.nan)
 
 
@@ -92,7 +93,9 @@ class WallClock:
 def serve(backend, requests, clock, window=500, on_finish=None):
     """Runs the requests through the backend; returns them with admission and finish
     times filled.  Admission is first fit over the queue in arrival order (a request that
-    does not fit does not block smaller ones behind it)."""
+    does not fit does not block smaller ones behind it).  A request whose admission fails
+    (an error from the backend, e.g. an allocation that fails or bad parameters) or whose
+    state turns non-finite ends as failed, and the others run on."""
     pending = sorted(requests, key=lambda r: r.arrival)
     queue = []
     live = {}
@@ -108,7 +111,14 @@ def serve(backend, requests, clock, window=500, on_finish=None):
         still = []
         for r in queue:
             t0 = clock.now()
-            slot = backend.admit(r.params, r.fields, r.id)
+            try:
+                slot = backend.admit(r.params, r.fields, r.id)
+            except (RuntimeError, MemoryError, ValueError) as e:
+                spent["admit"] += clock.now() - t0
+                r.failed = f"admission: {e}"
+                r.admitted = r.finished = clock.now()
+                done.append(r)
+                continue
             spent["admit"] += clock.now() - t0
             if slot is None:
                 still.append(r)
@@ -137,8 +147,10 @@ def serve(backend, requests, clock, window=500, on_finish=None):
             r.iters = st.get("poisson_iters", 0)
             r.rel_change = (st["rel_change_phi"], st["rel_change_u"])
             if st["steady"] or st["capped"] or st["status"] == 5:
-                r.steady = bool(st["steady"])
+                r.steady = bool(st["steady"]) and st["status"] != 5
                 r.capped = bool(st["capped"]) and not r.steady
+                if st["status"] == 5:
+                    r.failed = "non-finite state"
                 r.finished = clock.now()
                 if on_finish is not None:
                     on_finish(backend, st["slot"], r)
@@ -151,19 +163,23 @@ def serve(backend, requests, clock, window=500, on_finish=None):
 
 
 def summarize(done, wall):
-    lat = np.array([r.finished - r.arrival for r in done])
-    run = np.array([r.finished - r.admitted for r in done])
+    """Latencies and throughput over the requests that ran to an end (steady or capped);
+    failed ones are counted apart."""
+    ok = [r for r in done if not r.failed]
+    lat = np.array([r.finished - r.arrival for r in ok])
+    run = np.array([r.finished - r.admitted for r in ok])
     return {
         "requests": len(done),
         "steady": int(sum(r.steady for r in done)),
         "capped": int(sum(r.capped for r in done)),
+        "failed": int(sum(bool(r.failed) for r in done)),
         "wall_s": wall,
-        "sims_per_hour": len(done) / wall * 3600.0 if wall > 0 else math.nan,
+        "sims_per_hour": len(ok) / wall * 3600.0 if wall > 0 else math.nan,
         "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else math.nan,
         "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else math.nan,
         "p50_admit_to_steady_s": float(np.percentile(run, 50)) if len(run) else math.nan,
         "p99_admit_to_steady_s": float(np.percentile(run, 99)) if len(run) else math.nan,
-        "steps_total": int(sum(r.steps for r in done)),
+        "steps_total": int(sum(r.steps for r in ok)),
         "node_steps_total": int(sum(r.steps * r.params["nx"] * r.params["ny"] for r in done)),
         "poisson_iters_per_step": (float(sum(r.iters for r in done)) /
                                    max(1, sum(r.steps for r in done))),

@@ -232,3 +232,45 @@ def test_tuned_batch_schedule(gpu, tmp_path, monkeypatch):
     reqs = [request(n, i) for i, n in enumerate((64, 64, 128, 256))]
     best = autotune.tune_batch(reqs, steps=32, budget=512 << 20)
     assert best in autotune.batch_candidates()
+
+
+def test_non_finite_request_is_refused_without_disturbing_the_batch(gpu):
+    """A request with a NaN in phi is refused at admission (EHD_ERR_NONFINITE), its
+    workspace given back; the requests already in the batch compute exactly what they
+    compute without the attempt, and the serving loop records the request as failed."""
+    from paper_2407_01654_gb300 import serve
+    pa, fa = request(64, 5)
+    ref_b = gpu.Batch(128 << 20, max_slots=4)
+    s = ref_b.admit(pa, fa, 1)
+    ref_b.run(100)
+    ref = ref_b.read_fields(s)
+    ref_b.close()
+
+    b = gpu.Batch(128 << 20, max_slots=4)
+    s = b.admit(pa, fa, 1)
+    b.run(40)
+    before = b.info()
+    pn, fn = request(64, 6)
+    fn = dict(fn)
+    fn["phi"] = fn["phi"].copy()
+    fn["phi"][10, 10] = np.nan
+    with pytest.raises(gpu.EhdError) as err:
+        b.admit(pn, fn, 2)
+    assert err.value.code == 5
+    after = b.info()
+    for key in ("live_slots", "arena_used", "tiles_used"):
+        assert after[key] == before[key], key
+    b.run(60)
+    got = b.read_fields(s)
+    for k in FIELDS:
+        assert np.array_equal(got[k], ref[k]), k
+    b.close()
+
+    # through the serving loop: the bad request ends as failed, the good one runs on
+    reqs = [serve.Request(id=0, arrival=0.0, params=pa, fields=fa),
+            serve.Request(id=1, arrival=0.0, params=pn, fields=fn)]
+    be = gpu.Batch(128 << 20, max_slots=4, steady_tol=1e-30, step_cap=200)
+    done = serve.serve(be, reqs, serve.WallClock(), window=100)
+    by = {r.id: r for r in done}
+    assert by[1].failed.startswith("admission") and by[0].capped and not by[0].failed
+    be.close()

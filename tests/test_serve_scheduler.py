@@ -116,3 +116,41 @@ def test_request_generator_is_seeded():
     assert [r.params["nx"] for r in a] == [r.params["nx"] for r in b]
     assert all(r.params["nx"] in (16, 32) for r in a)
     assert a[-1].arrival > a[0].arrival > 0
+
+
+class FailingBatch(FakeBatch):
+    """A FakeBatch whose admission of the ids in `bad_alloc` fails (a mocked allocation
+    failure) and whose requests in `nan` report a non-finite state after their first
+    window."""
+
+    def __init__(self, clock, capacity, need, bad_alloc=(), nan=(), **kw):
+        super().__init__(clock, capacity, need, **kw)
+        self.bad_alloc, self.nan = set(bad_alloc), set(nan)
+
+    def admit(self, params, fields, rid):
+        if rid in self.bad_alloc:
+            raise MemoryError("mocked allocation failure")
+        return super().admit(params, fields, rid)
+
+    def poll(self):
+        out = super().poll()
+        for st in out:
+            if self.live[st["slot"]][0] in self.nan and st["steps"] > 0:
+                st["status"] = 5
+        return out
+
+
+def test_failed_requests_free_their_slots():
+    """A request whose admission fails and one whose state turns non-finite end as failed;
+    the other requests run to steady as before and the failures' slots are freed."""
+    clock = FakeClock()
+    be = FailingBatch(clock, capacity=64 * 64 * 2, need={0: 1000, 1: 1000, 2: 1500, 3: 1000},
+                      bad_alloc={1}, nan={2}, slots=2)
+    reqs = [req(i, 0.0, 64) for i in range(4)]
+    done = serve.serve(be, reqs, clock, window=500)
+    by = {r.id: r for r in done}
+    assert len(done) == 4 and not be.live and be.used == 0
+    assert by[1].failed.startswith("admission") and by[2].failed == "non-finite state"
+    assert by[0].steady and by[3].steady and not by[0].failed and not by[3].failed
+    s = serve.summarize(done, clock.now())
+    assert s["failed"] == 2 and s["steady"] == 2
