@@ -101,13 +101,13 @@ KERNEL_FILES = {
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # of the bench workload (summaries under profiles/, named for the kernel and workload)
 RECORDED_TRAFFIC = {
-    # one potential solve of the two-step loop (about 380 sub-iterations on the captured
-    # spin-up step; the solve's DRAM traffic does not grow with them): 21.022 MB read,
-    # 0.035 MB written
-    "k_poisson_resident2": (21056768, "8adaa3938685046a"),
-    # one coupled pass, caches flushed before the launch: 90.245 MB read, 15.035 MB written
+    # one potential solve of the two-step loop (about 470 sub-iterations on the captured
+    # spin-up step; the solve's DRAM traffic does not grow with them): 21.065 MB read,
+    # 0.018 MB written
+    "k_poisson_resident2": (21082624, "f87fc70718e4b657"),
+    # one coupled pass, caches flushed before the launch: 90.249 MB read, 15.630 MB written
     # back during the launch (the rest of its writes leave L2 later)
-    "k_coupled": (105280256, "4c3f74e1ec68f400"),
+    "k_coupled": (105878784, "4e700ba3eee77e05"),
 }
 
 
