@@ -545,7 +545,8 @@ def serve_arm(backend, reqs, window):
     done = serve.serve(backend, reqs, clock, window=window)
     summ = serve.summarize(done, clock.now())
     keys = ("requests", "steady", "capped", "wall_s", "sims_per_hour", "p50_latency_s",
-            "p99_latency_s", "p50_admit_to_steady_s", "p99_admit_to_steady_s",
+            "p99_latency_s", "p50_admit_to_end_s", "p99_admit_to_end_s",
+            "p50_admit_to_steady_s", "p99_admit_to_steady_s",
             "poisson_iters_per_step", "steps_total")
     return {k: summ[k] for k in keys}
 

@@ -164,10 +164,16 @@ def serve(backend, requests, clock, window=500, on_finish=None):
 
 def summarize(done, wall):
     """Latencies and throughput over the requests that ran to an end (steady or capped);
-    failed ones are counted apart."""
+    failed ones are counted apart.  Admit-to-steady percentiles cover the steady requests
+    only (None when none became steady); admit-to-end covers every completed request."""
     ok = [r for r in done if not r.failed]
     lat = np.array([r.finished - r.arrival for r in ok])
     run = np.array([r.finished - r.admitted for r in ok])
+    run_steady = np.array([r.finished - r.admitted for r in ok if r.steady])
+
+    def pct(a, q):
+        return float(np.percentile(a, q)) if len(a) else None
+
     return {
         "requests": len(done),
         "steady": int(sum(r.steady for r in done)),
@@ -175,10 +181,12 @@ def summarize(done, wall):
         "failed": int(sum(bool(r.failed) for r in done)),
         "wall_s": wall,
         "sims_per_hour": len(ok) / wall * 3600.0 if wall > 0 else math.nan,
-        "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else math.nan,
-        "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else math.nan,
-        "p50_admit_to_steady_s": float(np.percentile(run, 50)) if len(run) else math.nan,
-        "p99_admit_to_steady_s": float(np.percentile(run, 99)) if len(run) else math.nan,
+        "p50_latency_s": pct(lat, 50),
+        "p99_latency_s": pct(lat, 99),
+        "p50_admit_to_end_s": pct(run, 50),
+        "p99_admit_to_end_s": pct(run, 99),
+        "p50_admit_to_steady_s": pct(run_steady, 50),
+        "p99_admit_to_steady_s": pct(run_steady, 99),
         "steps_total": int(sum(r.steps for r in ok)),
         "node_steps_total": int(sum(r.steps * r.params["nx"] * r.params["ny"] for r in done)),
         "poisson_iters_per_step": (float(sum(r.iters for r in done)) /

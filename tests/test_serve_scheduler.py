@@ -154,3 +154,24 @@ def test_failed_requests_free_their_slots():
     assert by[0].steady and by[3].steady and not by[0].failed and not by[3].failed
     s = serve.summarize(done, clock.now())
     assert s["failed"] == 2 and s["steady"] == 2
+
+
+def test_admit_to_steady_counts_steady_requests_only():
+    """Capped requests end at their cap, not at steady state: their admit-to-end times do
+    not enter the admit-to-steady percentiles."""
+    p = {"nx": 8, "ny": 8}
+
+    def done(i, admitted, finished, steady):
+        return serve.Request(id=i, arrival=0.0, params=p, fields={}, admitted=admitted,
+                             finished=finished, steps=10, steady=steady, capped=not steady)
+
+    capped_only = [done(0, 0.0, 5.0, False), done(1, 1.0, 9.0, False)]
+    s = serve.summarize(capped_only, 10.0)
+    assert s["steady"] == 0 and s["capped"] == 2
+    assert s["p50_admit_to_steady_s"] is None and s["p99_admit_to_steady_s"] is None
+    assert s["p50_admit_to_end_s"] == pytest.approx(6.5)
+    mixed = capped_only + [done(2, 2.0, 3.0, True), done(3, 2.0, 5.0, True)]
+    s = serve.summarize(mixed, 10.0)
+    assert s["p50_admit_to_steady_s"] == pytest.approx(2.0)
+    assert s["p99_admit_to_steady_s"] == pytest.approx(2.98)
+    assert s["p99_admit_to_end_s"] == pytest.approx(7.91)  # 5 + 0.97 (8 - 5)
