@@ -24,6 +24,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -137,7 +138,9 @@ class ClockSampler:
     def __init__(self, gpu_index=0):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples are kept beside the run ($EHD_CLOCKS_DIR, else the temp folder)
+        folder = os.environ.get("EHD_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(folder, f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
