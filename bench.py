@@ -480,6 +480,18 @@ def run_gpu(args, rank, world):
             "hbm_streamed_equivalent_frac":
                 BYTES_POTENTIAL * nodes_f / (marginal_us * 1e-6) / 1e9 / peak,
             "solve_fixed_us": kinds["potential"]["us_per_launch"] - kbar * marginal_us}
+        if loop_kind == 3:
+            # a cycle (two sub-iterations) of the two-step loop with its exchange alone:
+            # band export, grid barrier, ring import, no arithmetic
+            try:
+                floor_us = ehd.grid_exchange_floor(p["nx"], p["ny"], stream.cuda_stream) * 1e6
+                roof_pot["sync_floor"] = {
+                    "what": "ehd_diag_grid_exchange: the two-step loop's exchange without its "
+                            "arithmetic (64x56 tiles, 896 threads, one cooperative launch)",
+                    "us_per_cycle": floor_us, "cycle_us": 2 * marginal_us,
+                    "frac_of_cycle": floor_us / (2 * marginal_us)}
+            except ehd.EhdError as e:
+                roof_pot["sync_floor"] = {"unavailable": str(e)}
     else:
         roof_pot = {"bound": "hbm", "kernel": "k_poisson", "achieved": BYTES_POTENTIAL * nodes_f / t_it / 1e9,
                     "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs (copy)", "unit": "GB/s",

@@ -322,6 +322,22 @@ int ehd_diag_expire_barrier(ehd_sim* sim);
  * Errors: EHD_ERR_INVALID_ARG (null pointer), EHD_ERR_CUDA. */
 int ehd_diag_smem_bandwidth(void* stream, double* bytes_per_second);
 
+/* Measurement helper (no counterpart in the paper): the synchronisation floor of the
+ * two-step on-chip potential loop on an nx x ny lattice, in seconds per cycle (one cycle =
+ * two sub-iterations).  One cooperative launch of 64 x 56 tiles, 896 threads each, runs
+ * the loop's exchange without its arithmetic: each cycle a tile writes its two-node-wide
+ * band (464 nodes x 8 populations, FP32) to global memory, meets every tile at a grid
+ * barrier (release add, acquire poll; each wait bounded at 2 s) and reads the two-node-wide
+ * ring (496 nodes x 8 populations) from its eight neighbours' bands (periodic in x and y).
+ * The figure is the difference of the best times of 1088 and 64 cycles over the extra
+ * 1024, so the launch and start-up are left out.  Queues its launches on `stream` (NULL:
+ * default stream), synchronises it, and allocates and frees its own device buffer (about
+ * 30 KB per tile); not for use during stream capture.
+ * Errors: EHD_ERR_INVALID_ARG (null pointer; fewer than 3 tiles in x or y);
+ * EHD_ERR_TOO_LARGE (more tiles than the device holds at once); EHD_ERR_TIMEOUT (a
+ * barrier wait ran out); EHD_ERR_CUDA. */
+int ehd_diag_grid_exchange(void* stream, int nx, int ny, double* seconds_per_cycle);
+
 /* Releases the simulation (and its workspace if the library allocated it). */
 void ehd_destroy(ehd_sim* sim);
 

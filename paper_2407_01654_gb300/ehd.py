@@ -160,6 +160,8 @@ SIGNATURES = {
                                                    ctypes.POINTER(ctypes.c_double)]),
     "ehd_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(KernelTimes)]),
     "ehd_diag_smem_bandwidth": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "ehd_diag_grid_exchange": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_double)]),
     "ehd_use_graphs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "ehd_slabs_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int, ctypes.c_void_p,
                                         ctypes.POINTER(ctypes.c_void_p)]),
@@ -208,6 +210,16 @@ def smem_bandwidth(stream=None):
     stores, measured by ehd_diag_smem_bandwidth)."""
     v = ctypes.c_double()
     _check(lib().ehd_diag_smem_bandwidth(stream, ctypes.byref(v)), "ehd_diag_smem_bandwidth")
+    return v.value
+
+
+def grid_exchange_floor(nx, ny, stream=None):
+    """Seconds per cycle of the two-step on-chip loop's exchange alone (band export, grid
+    barrier, ring import; no arithmetic) on an nx x ny lattice of 64 x 56 tiles, measured by
+    ehd_diag_grid_exchange."""
+    v = ctypes.c_double()
+    _check(lib().ehd_diag_grid_exchange(stream, int(nx), int(ny), ctypes.byref(v)),
+           "ehd_diag_grid_exchange")
     return v.value
 
 

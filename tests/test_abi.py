@@ -145,3 +145,16 @@ def test_null_handles_are_refused(L):
     assert L.ehd_step(None, 1, None) == 1
     assert L.ehd_use_graphs(None, 1) == 1
     assert L.ehd_read_fields(None, 1, None, 0) == 1
+
+
+def test_grid_exchange_refuses_before_touching_the_device(L):
+    """The synchronisation-floor helper checks its arguments first: a null result pointer
+    or a lattice with fewer than 3 tiles of 64 x 56 in a direction (its ring would meet the
+    same neighbour on both sides) is refused with EHD_ERR_INVALID_ARG (1)."""
+    v = ctypes.c_double()
+    L.ehd_diag_grid_exchange.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_double)]
+    assert L.ehd_diag_grid_exchange(None, 512, 1024, None) == 1
+    assert L.ehd_diag_grid_exchange(None, 128, 1024, ctypes.byref(v)) == 1  # 2 tiles in x
+    assert L.ehd_diag_grid_exchange(None, 512, 112, ctypes.byref(v)) == 1  # 2 tiles in y
+    assert L.ehd_diag_grid_exchange(None, 0, 1024, ctypes.byref(v)) == 1
