@@ -421,6 +421,32 @@ def run_gpu(args, rank, world):
                "poisson_iters_mean": st2["poisson_iters_total"] / args.steps}
         assert np.isfinite(out["phi"]).all()
 
+    # the same workload with the moving populations stored as FP16 deviations (a second
+    # figure; the headline is FP32): the schedule tuned for that storage, its own spin-up
+    # from the same start fields, a window of the same length
+    fp16 = None
+    if rank == 0 and not args.no_fp16:
+        p16 = dict(p, precision=1)
+        if not args.no_tune:
+            p16.update(autotune.tune(p16, fields=f))
+        s16 = ehd.Sim(p16, stream=stream)
+        s16.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
+        s16.step(args.spinup)
+        s16.step(args.warmup)
+        ms16 = timed_steps(s16, args.steps)
+        st16 = s16.read_stats()
+        s16.close()
+        if st16["status"] not in (0, 4):
+            raise RuntimeError(f"FP16-storage steps failed with status {st16['status']}")
+        fp16 = {"value": nodes * args.steps / (ms16 / 1e3) / 1e6, "unit": UNIT,
+                "ms_per_step": ms16 / args.steps,
+                "poisson_iters_mean": st16["poisson_iters_total"] / args.steps,
+                "storage": "24 moving populations as FP16 deviations from the lattice "
+                           "weights, rest populations, potential populations and arithmetic "
+                           "FP32",
+                "schedule": ({k: p16[k] for k in ("poisson_loop", "tile_rows")}
+                             if not args.no_tune else "built-in")}
+
     if rank != 0:
         return
     peak, peak_kind = peaks()
@@ -530,6 +556,8 @@ def run_gpu(args, rank, world):
         "gpu_launches": launches,
         "e2e": e2e,
     }
+    if fp16 is not None:
+        line["fp16_storage"] = fp16
     line["clocks"] = clk.summary()
     line["clocks"]["window"] = ("nvidia-smi every 50 ms while a copy of the simulation ran the "
                                 "same steps right before and right after the timed region")
@@ -633,6 +661,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-fp16", action="store_true",
+                    help="skip the second figure with FP16-deviation population storage")
     ap.add_argument("--spinup", type=int, default=SPINUP_STEPS,
                     help="untimed steps before the warm-up (the workload's start state); "
                          "profiling captures use fewer to keep the launches before them few")

@@ -509,10 +509,10 @@ struct StepSlot {
   int quad;          // 1: moments four nodes per thread, as k_moments4 (moments4_ok)
 };
 
-// Whether a lattice's moments pass takes four nodes per thread with 16-byte loads
-// (k_moments4): FP32 populations, no slab, N a multiple of 4.
+// Whether a lattice's moments pass takes four nodes per thread with vector loads
+// (k_moments4): no slab, N a multiple of 4 (either storage precision).
 __host__ __device__ inline bool moments4_ok(const KParams& kp) {
-  return !kp.half && !kp.slab && kp.N % 4 == 0 && kp.N == kp.nint;
+  return !kp.slab && kp.N % 4 == 0 && kp.N == kp.nint;
 }
 
 // Batched moments / coupled passes: one launch over work[] = (slot, block of that slot).

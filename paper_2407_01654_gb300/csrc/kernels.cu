@@ -400,7 +400,21 @@ __global__ void __launch_bounds__(256) k_moments(KParams k, const StepState* __r
 // form's grid-stride loop waited on one node's loads before the next).  Per node the
 // arithmetic is moments_body's, in the same order; only the FP32 partial sums group the
 // nodes differently.
-template <bool TAIL>
+// Four consecutive FP16-stored moving populations of plane (field, i), as the FP32 values
+// ld_pop<true> reads for each of them (one 8-byte load).
+__device__ __forceinline__ float4 ld_pop4_half(const KParams& k, const Pops& P, int field, int i,
+                                               size_t q4) {
+  const uint2 raw = __ldg(reinterpret_cast<const uint2*>(P.p16 + (size_t)(field * 8 + i - 1) * k.N) + q4);
+  const __half2 a = *reinterpret_cast<const __half2*>(&raw.x);
+  const __half2 b = *reinterpret_cast<const __half2*>(&raw.y);
+  const float s = __fmul_rn(k.ipsc[field], wgt(i));
+  return make_float4(__fmul_rn(__low2float(a), s), __fmul_rn(__high2float(a), s),
+                     __fmul_rn(__low2float(b), s), __fmul_rn(__high2float(b), s));
+}
+
+// Four consecutive nodes per thread (N a multiple of 4): 16-byte loads of each FP32 plane
+// and 8-byte loads of each FP16 plane; per node the arithmetic of moments_body.
+template <bool TAIL, bool HALF>
 __device__ __forceinline__ void moments4_body(const KParams& k, const StepState* __restrict__ ss,
                                               const Pops& pops, const float* __restrict__ hist,
                                               float* __restrict__ phi_out,
@@ -414,13 +428,25 @@ __device__ __forceinline__ void moments4_body(const KParams& k, const StepState*
   int bad = 0;
   if (q4 < N4) {
     const float4* P = reinterpret_cast<const float4*>(pops.p32) + q4;
-    float4 g[9], l[9];
+    float4 g[9], l[9], lo;
+    if (HALF) {
+      // FP32 planes: the rest populations of g and l, then g0's low part in plane 3
+      g[0] = __ldg(P);
+      l[0] = __ldg(P + N4);
+      lo = __ldg(P + 3 * N4);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      g[i] = __ldg(P + i * N4);
-      l[i] = __ldg(P + (9 + i) * N4);
+      for (int i = 1; i < 9; ++i) {
+        g[i] = ld_pop4_half(k, pops, 0, i, q4);
+        l[i] = ld_pop4_half(k, pops, 1, i, q4);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        g[i] = __ldg(P + i * N4);
+        l[i] = __ldg(P + (9 + i) * N4);
+      }
+      lo = __ldg(P + NPOP * N4);
     }
-    const float4 lo = __ldg(P + NPOP * N4);
     const float4 R = __ldg(reinterpret_cast<const float4*>(hist + 3 * (size_t)k.N) + q4);
     float ph[4], qq[4];
     const float* gf = reinterpret_cast<const float*>(g);
@@ -451,7 +477,7 @@ __device__ __forceinline__ void moments4_body(const KParams& k, const StepState*
     moments_partial_only(k, ss, partials, ctl, tol, min_iter, max_iter, fixed_iter, bid, nblk,
                          phi_acc, q_acc, bad);
 }
-template <bool TAIL>
+template <bool TAIL, bool HALF>
 __global__ void __launch_bounds__(256) k_moments4(KParams k, const StepState* __restrict__ ss,
                                                   Pops pops, const float* __restrict__ hist,
                                                   float* __restrict__ phi_out,
@@ -459,8 +485,14 @@ __global__ void __launch_bounds__(256) k_moments4(KParams k, const StepState* __
                                                   double2* __restrict__ partials, Ctl* ctl,
                                                   double tol, int min_iter, int max_iter,
                                                   int fixed_iter) {
-  moments4_body<TAIL>(k, ss, pops, hist, phi_out, aq, partials, ctl, tol, min_iter, max_iter,
-                      fixed_iter, blockIdx.x, gridDim.x);
+  moments4_body<TAIL, HALF>(k, ss, pops, hist, phi_out, aq, partials, ctl, tol, min_iter,
+                            max_iter, fixed_iter, blockIdx.x, gridDim.x);
+}
+// The k_moments4 form for a lattice: with or without the cross-CTA tail, by storage.
+static inline const void* moments4_kernel(const KParams& kp, bool tail) {
+  if (kp.half)
+    return tail ? (const void*)k_moments4<true, true> : (const void*)k_moments4<false, true>;
+  return tail ? (const void*)k_moments4<true, false> : (const void*)k_moments4<false, false>;
 }
 // Whether a lattice takes k_moments4 (moments4_ok, in the header), and its grid.
 static inline int moments4_blocks(const KParams& kp) { return (kp.N / 4 + 255) / 256; }
@@ -807,7 +839,8 @@ __device__ __forceinline__ void coupled_body(const KParams& k, StepState* ss, in
 // 128 threads.  The FP32 form (specialised below): at least 7 CTAs per SM (at most
 // 72 registers); the pass is bound by memory latency, and 7 resident CTAs run it 2.5 %
 // faster than the 6 that 80 registers allow (8 CTAs at 64 registers spill more and run
-// slower).  The FP16-storage form keeps the registers it needs.
+// slower).  The FP16-storage form: at least 6 CTAs per SM (80 registers, no spills),
+// 1.6 us faster at 512 x 1024 than the 5 its 96 registers allowed; 7 and 8 spill.
 template <bool HALF>
 __global__ void __launch_bounds__(128) k_coupled(KParams k, StepState* ss, int cur, Pops pin,
                                                  Pops pout,
@@ -832,6 +865,20 @@ __global__ void __launch_bounds__(128, EHD_COUPLED_MIN_CTAS) k_coupled<false>(KP
                                                            DevStats* stats) {
   coupled_body<false>(k, ss, cur, pin, pout, phi_f, hbuf, hist, ctl, partials, stats, blockIdx.x);
 }
+#ifndef EHD_COUPLED16_MIN_CTAS
+#define EHD_COUPLED16_MIN_CTAS 6
+#endif
+template <>
+__global__ void __launch_bounds__(128, EHD_COUPLED16_MIN_CTAS) k_coupled<true>(KParams k, StepState* ss, int cur,
+                                                            Pops pin, Pops pout,
+                                                            const float* __restrict__ phi_f,
+                                                            const float* __restrict__ hbuf,
+                                                            float* __restrict__ hist,
+                                                            Ctl* ctl,
+                                                            const double2* __restrict__ partials,
+                                                            DevStats* stats) {
+  coupled_body<true>(k, ss, cur, pin, pout, phi_f, hbuf, hist, ctl, partials, stats, blockIdx.x);
+}
 
 // ------------------------------------------------------------------------------------
 // Batched forms: one launch over the blocks of several simulations.  work[b] = (slot,
@@ -843,9 +890,14 @@ __global__ void __launch_bounds__(256) k_moments_batch(const StepSlot* __restric
   const int2 w = work[blockIdx.x];
   const StepSlot& S = slots[w.x];
   const Pops P = pops_copy(S.k, S.b, cur);
-  if (S.quad)  // the blocks and arithmetic of the slot's own k_moments4<true> launch
-    moments4_body<true>(S.k, S.b.ss + cur, P, S.b.hist, S.b.phi, S.b.aq, S.b.partials, S.b.ctl,
-                        S.tol, S.min_iter, S.max_iter, S.fixed_iter, w.y, S.mblocks);
+  if (S.quad && S.k.half)  // the blocks and arithmetic of the slot's own k_moments4 launch
+    moments4_body<true, true>(S.k, S.b.ss + cur, P, S.b.hist, S.b.phi, S.b.aq, S.b.partials,
+                              S.b.ctl, S.tol, S.min_iter, S.max_iter, S.fixed_iter, w.y,
+                              S.mblocks);
+  else if (S.quad)
+    moments4_body<true, false>(S.k, S.b.ss + cur, P, S.b.hist, S.b.phi, S.b.aq, S.b.partials,
+                               S.b.ctl, S.tol, S.min_iter, S.max_iter, S.fixed_iter, w.y,
+                               S.mblocks);
   else if (S.k.half)
     moments_body<true>(S.k, S.b.ss + cur, P, S.b.hist, S.b.phi, S.b.aq, S.b.partials, S.b.ctl,
                        S.tol, S.min_iter, S.max_iter, S.fixed_iter, w.y, S.mblocks);
@@ -1058,15 +1110,19 @@ cudaError_t launch_moments(const KParams& kp, const Buffers& b, int cur, double 
   const int nb = moments_blocks(kp.nint);
   const Pops P = pops_copy(kp, b, cur);
   if (moments4_ok(kp)) {
-    if (sums_in_coupled && !kp.neutralize)
-      k_moments4<false><<<moments4_blocks(kp), 256, 0, st>>>(kp, b.ss + cur, P, b.hist, b.phi,
-                                                             b.aq, b.partials, b.ctl, tol,
-                                                             min_iter, max_iter, fixed_iter);
-    else
-      k_moments4<true><<<moments4_blocks(kp), 256, 0, st>>>(kp, b.ss + cur, P, b.hist, b.phi,
-                                                            b.aq, b.partials, b.ctl, tol,
-                                                            min_iter, max_iter, fixed_iter);
-    return cudaGetLastError();
+    const bool tail = !(sums_in_coupled && !kp.neutralize);
+    KParams k = kp;
+    const StepState* ss = b.ss + cur;
+    Pops pops = P;
+    const float* hist = b.hist;
+    float* phi = b.phi;
+    float2* aq = b.aq;
+    double2* partials = b.partials;
+    Ctl* ctl = b.ctl;
+    void* args[] = {&k, &ss, &pops, &hist, &phi, &aq, &partials, &ctl, &tol, &min_iter,
+                    &max_iter, &fixed_iter};
+    return cudaLaunchKernel(moments4_kernel(kp, tail), dim3(moments4_blocks(kp)), dim3(256), args,
+                            0, st);
   }
   if (kp.half)
     k_moments<true><<<nb, 256, 0, st>>>(kp, b.ss + cur, P, b.hist, b.phi, b.aq, b.partials,
@@ -1152,8 +1208,7 @@ cudaError_t add_moments_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t 
                   &fixed_iter};
   cudaKernelNodeParams p = {};
   p.func = moments4_ok(kp)
-               ? ((sums_in_coupled && !kp.neutralize) ? (void*)k_moments4<false>
-                                                      : (void*)k_moments4<true>)
+               ? const_cast<void*>(moments4_kernel(kp, !(sums_in_coupled && !kp.neutralize)))
                : (kp.half ? (void*)k_moments<true> : (void*)k_moments<false>);
   p.gridDim = dim3(moments4_ok(kp) ? moments4_blocks(kp) : moments_blocks(kp.nint));
   p.blockDim = dim3(256);
