@@ -103,12 +103,12 @@ KERNEL_FILES = {
 # of the bench workload (summaries under profiles/, named for the kernel and workload)
 RECORDED_TRAFFIC = {
     # one potential solve of the two-step loop (about 470 sub-iterations on the captured
-    # spin-up step; the solve's DRAM traffic does not grow with them): 21.065 MB read,
-    # 0.018 MB written
-    "k_poisson_resident2": (21082624, "f87fc70718e4b657"),
-    # one coupled pass, caches flushed before the launch: 90.249 MB read, 15.630 MB written
+    # spin-up step; the solve's DRAM traffic does not grow with them): 21.025 MB read,
+    # 0.034 MB written
+    "k_poisson_resident2": (21059328, "63a0ab55b417a67c"),
+    # one coupled pass, caches flushed before the launch: 90.245 MB read, 15.610 MB written
     # back during the launch (the rest of its writes leave L2 later)
-    "k_coupled": (105878784, "4e700ba3eee77e05"),
+    "k_coupled": (105855232, "18eaf79c57ebe6d9"),
 }
 
 
