@@ -171,9 +171,16 @@ __device__ __forceinline__ void st_pop(const KParams& k, const Pops& P, int fiel
     else
       P.p32[(size_t)(field * 9 + i) * N + idx] = v;
   } else if (i == 0) {
-    P.p32[(size_t)field * N + idx] = v;
+    if (field == 2)  // as above: the hydrodynamic populations evict-first
+      __stcs(P.p32 + (size_t)field * N + idx, v);
+    else
+      P.p32[(size_t)field * N + idx] = v;
   } else {
-    P.p16[(size_t)(field * 8 + i - 1) * N + idx] = __float2half_rn(v * (k.psc[field] * inv_wgt(i)));
+    const __half hv = __float2half_rn(v * (k.psc[field] * inv_wgt(i)));
+    if (field == 2)
+      __stcs(P.p16 + (size_t)(field * 8 + i - 1) * N + idx, hv);
+    else
+      P.p16[(size_t)(field * 8 + i - 1) * N + idx] = hv;
   }
 }
 
@@ -200,7 +207,10 @@ __device__ __forceinline__ float st_pop_read(const KParams& k, const Pops& P, in
     return v;
   }
   const __half hv = __float2half_rn(v * (k.psc[field] * inv_wgt(i)));
-  P.p16[(size_t)(field * 8 + i - 1) * N + idx] = hv;
+  if (field == 2)
+    __stcs(P.p16 + (size_t)(field * 8 + i - 1) * N + idx, hv);
+  else
+    P.p16[(size_t)(field * 8 + i - 1) * N + idx] = hv;
   return __half2float(hv) * (k.ipsc[field] * wgt(i));
 }
 // phi = sum_i g_i of a node (Eq. weq49) with g_0 = hi + lo: the moving populations in

@@ -519,13 +519,16 @@ struct GlobalSrc {
   const float* __restrict__ hs;
   const float* __restrict__ hist;
   int idx;
+  // with FP16 storage the value ld_pop<true> reads, through the same evict-first loads
   __device__ __forceinline__ float pop(int field, int i) const {
-    return HALF ? ld_pop<HALF>(k, pin, field, i, idx)
-                : __ldcs(pin.p32 + (size_t)(field * 9 + i) * k.N + EHD_IDX(k, idx, k.N));
+    const size_t j = EHD_IDX(k, idx, k.N);
+    if (!HALF) return __ldcs(pin.p32 + (size_t)(field * 9 + i) * k.N + j);
+    if (i == 0) return __ldcs(pin.p32 + (size_t)field * k.N + j);
+    const __half v = __ldcs(pin.p16 + (size_t)(field * 8 + i - 1) * k.N + j);
+    return __half2float(v) * (k.ipsc[field] * wgt(i));
   }
   __device__ __forceinline__ float g0_lo() const {
-    return HALF ? ld_g0_lo<HALF>(k, pin, idx)
-                : __ldcs(pin.p32 + (size_t)NPOP * k.N + EHD_IDX(k, idx, k.N));
+    return __ldcs(pin.p32 + (size_t)(HALF ? 3 : NPOP) * k.N + EHD_IDX(k, idx, k.N));
   }
   __device__ __forceinline__ float h(int i) const {
     return __ldg(hs + i * (size_t)k.N + EHD_IDX(k, idx, k.N));
