@@ -422,10 +422,10 @@ def run_gpu(args, rank, world):
         assert np.isfinite(out["phi"]).all()
 
     # the same workload with the moving populations stored as FP16 deviations (a second
-    # figure; the headline is FP32): the schedule tuned for that storage, its own spin-up
-    # from the same start fields, a window of the same length
+    # figure, one GPU only; the headline is FP32): the schedule tuned for that storage, its
+    # own spin-up from the same start fields, a window of the same length
     fp16 = None
-    if rank == 0 and not args.no_fp16:
+    if world == 1 and not args.no_fp16:
         p16 = dict(p, precision=1)
         if not args.no_tune:
             p16.update(autotune.tune(p16, fields=f))
