@@ -73,6 +73,11 @@ FLOPS_POTENTIAL = 96
 # post-collision populations stored (32 B) and the 8 streamed ones loaded (32 B); the ring
 # and export band traffic on top of it is overhead, not counted
 SMEM_BYTES_POTENTIAL = 64
+# thread instructions per lattice node and potential sub-iteration of the two-step on-chip
+# loop, the ring's redundant work included (ncu: 629.2 M warp instructions over 524 288
+# nodes x 379 sub-iterations, profiles/k_poisson_resident_sessile512x1024.md); at four
+# warp instructions per clock and SM they set the loop's issue floor
+INSTR_POTENTIAL = 101.3
 SM_MAX_MHZ = 2070.0
 
 
@@ -511,11 +516,20 @@ def run_gpu(args, rank, world):
             # band export, grid barrier, ring import, no arithmetic
             try:
                 floor_us = ehd.grid_exchange_floor(p["nx"], p["ny"], stream.cuda_stream) * 1e6
+                # instruction issue of a cycle on the busiest SM at the maximum SM clock
+                nodes_per_sm = nodes_f / props.multi_processor_count
+                issue_us = 2 * nodes_per_sm * INSTR_POTENTIAL / 32 / 4 / (SM_MAX_MHZ * 1e6) * 1e6
                 roof_pot["sync_floor"] = {
                     "what": "ehd_diag_grid_exchange: the two-step loop's exchange without its "
                             "arithmetic (64x56 tiles, 896 threads, one cooperative launch)",
                     "us_per_cycle": floor_us, "cycle_us": 2 * marginal_us,
-                    "frac_of_cycle": floor_us / (2 * marginal_us)}
+                    "frac_of_cycle": floor_us / (2 * marginal_us),
+                    "issue_us_per_cycle": issue_us,
+                    "design_floor_us_per_cycle": floor_us + issue_us,
+                    "design_frac": (floor_us + issue_us) / (2 * marginal_us),
+                    "design_floor_is": "the measured exchange plus the issue of "
+                                       f"{INSTR_POTENTIAL} instructions per node and "
+                                       "sub-iteration at 4 warp instructions per clock and SM"}
             except ehd.EhdError as e:
                 roof_pot["sync_floor"] = {"unavailable": str(e)}
     else:
