@@ -1,7 +1,7 @@
 """Steady fields against the FP64 oracle: the two-layer planar set-up of Sec. 6.1 (4 x 64,
 permittivity ratio 10, conductivity ratio 0.1, fixed wall potentials) run to its steady
-state, 20 000 steps with the paper's stopping rule (tolerance 1e-5) on both sides.  Bar
-(the benchmark spec): relative L2 <= 1e-3 per field on steady fields.
+state, 20 000 steps with the paper's stopping rule (tolerance 1e-5) on both sides.  Bar:
+relative L2 <= 1e-3 per field on steady fields.
 
 At the steady state the fluid is at rest (u is zero up to a decaying transient of about
 1e-8), so u is compared on an absolute scale: the RMS difference must stay below 1e-3 of
