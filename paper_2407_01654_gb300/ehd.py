@@ -223,6 +223,27 @@ def grid_exchange_floor(nx, ny, stream=None):
     return v.value
 
 
+def output_pointers(outs, shape, device):
+    """Addresses of caller-owned output buffers for ehd_read_fields, after checking that
+    each has the shape and type the call writes: C-contiguous numpy float64 on the host,
+    contiguous float32 CUDA tensors for device reads.  Raises ValueError otherwise."""
+    ptrs = []
+    for o in outs:
+        if device:
+            if not (_is_torch_cuda(o) and str(o.dtype) == "torch.float32"
+                    and tuple(o.shape) == tuple(shape) and o.is_contiguous()):
+                raise ValueError("device outputs must be contiguous float32 CUDA tensors "
+                                 f"of shape {tuple(shape)}")
+            ptrs.append(o.data_ptr())
+        else:
+            if not (isinstance(o, np.ndarray) and o.dtype == np.float64
+                    and o.shape == tuple(shape) and o.flags.c_contiguous and o.flags.writeable):
+                raise ValueError("host outputs must be writeable C-contiguous float64 arrays "
+                                 f"of shape {tuple(shape)}")
+            ptrs.append(o.ctypes.data)
+    return ptrs
+
+
 class Sim:
     """One simulation on the GPU.
 
@@ -351,22 +372,28 @@ class Sim:
             _check(code, "ehd_solve_potential")
         return it.value, rel.value, code
 
-    def read_fields(self, names=FIELDS, device=False):
-        """dict name -> numpy float64 array [ny, nx] (or torch float32 CUDA tensors)."""
+    def read_fields(self, names=FIELDS, device=False, out=None):
+        """dict name -> numpy float64 array [ny, nx] (or torch float32 CUDA tensors).
+        out: optional dict name -> caller-owned array of that shape and type (C-contiguous
+        numpy float64 on the host, contiguous float32 CUDA tensors with device=True) that
+        the library writes into, so that repeated reads reuse their buffers; it must hold
+        every requested field."""
         mask = 0
         for n in names:
             mask |= 1 << FIELDS.index(n)
         order = [n for n in FIELDS if mask & (1 << FIELDS.index(n))]
-        if device:
+        if out is not None:
+            outs = [out[n] for n in order]
+            ptrs = output_pointers(outs, (self.ny, self.nx), device)
+        elif device:
             import torch
             outs = [torch.empty((self.ny, self.nx), dtype=torch.float32, device="cuda")
                     for _ in order]
             ptrs = [o.data_ptr() for o in outs]
-            mem = EHD_DEVICE
         else:
             outs = [np.empty((self.ny, self.nx), dtype=np.float64) for _ in order]
             ptrs = [o.ctypes.data for o in outs]
-            mem = EHD_HOST
+        mem = EHD_DEVICE if device else EHD_HOST
         arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
         _check(lib().ehd_read_fields(self._h, mask, arr, mem), "ehd_read_fields")
         return dict(zip(order, outs))

@@ -158,3 +158,21 @@ def test_grid_exchange_refuses_before_touching_the_device(L):
     assert L.ehd_diag_grid_exchange(None, 128, 1024, ctypes.byref(v)) == 1  # 2 tiles in x
     assert L.ehd_diag_grid_exchange(None, 512, 112, ctypes.byref(v)) == 1  # 2 tiles in y
     assert L.ehd_diag_grid_exchange(None, 0, 1024, ctypes.byref(v)) == 1
+
+
+def test_caller_owned_output_buffers_are_checked():
+    """read_fields(out=...) passes the caller's arrays to ehd_read_fields only when each has
+    the shape and type the call writes (host: C-contiguous float64)."""
+    import numpy as np
+    good = [np.zeros((6, 4)), np.zeros((6, 4))]
+    assert ehd.output_pointers(good, (6, 4), False) == [a.ctypes.data for a in good]
+    for bad in (np.zeros((6, 4), np.float32), np.zeros((4, 6)), np.zeros((6, 8))[:, ::2],
+                [[0.0] * 4] * 6):
+        with pytest.raises(ValueError):
+            ehd.output_pointers([bad], (6, 4), False)
+    ro = np.zeros((6, 4))
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        ehd.output_pointers([ro], (6, 4), False)
+    with pytest.raises(ValueError):  # a host array is not a device output
+        ehd.output_pointers([np.zeros((6, 4))], (6, 4), True)
