@@ -353,6 +353,20 @@ def test_fp16_storage_errors_per_field(gpu, which):
     assert all(v <= FP16_BAR for v in errs.values()), errs
 
 
+def test_full_size_sessile_fp16(gpu):
+    """FP16-deviation storage on the full 512 x 1024 benchmark lattice in the launch
+    configuration its benchmark figure uses (the two-step on-chip loop, 64 x 56 tiles):
+    every node of every field after 10 steps, each field within the FP16 bar."""
+    p, f, _ = wl.sessile_drop(seed=0, start_step=10000, poisson_fixed_iter=2,
+                              poisson_loop=3, tile_rows=56, precision=1)
+    f = wl.perturbed(p, f, seed=5, u_amp=1e-3, q_amp=1e-4)
+    o, g, fo, fg, so, sg = run_pair(gpu, p, f, 10)
+    errs = {grp: rel(np.stack([fg[k] for k in ks]), np.stack([fo[k] for k in ks]))
+            for grp, ks in GROUPS.items()}
+    print("fp16 storage relative L2, 512x1024", {k: f"{v:.2e}" for k, v in errs.items()})
+    assert all(v <= FP16_BAR for v in errs.values()), errs
+
+
 def test_fp16_save_load_bit_exact(gpu):
     p, f = droplet_box(48, 40, 9.0, seed=8, precision=1)
     a = gpu.Sim(p)
