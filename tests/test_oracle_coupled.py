@@ -3,11 +3,55 @@ Sec. 6.1 run to its steady state."""
 import math
 
 import numpy as np
+import pytest
 from scipy import integrate
 
 import analytic as an
 from oracle import ehd
 from paper_2407_01654_gb300 import workloads as wl
+
+
+NY = 32
+
+
+def layers_run():
+    """The two-layer planar set-up of Sec. 6.1 run 2000 full coupled steps on the oracle:
+    (params, oracle parameters, stats, fields)."""
+    p, f = wl.planar_layers(nx=4, ny=NY, eps_v=0.5, sigma_v=0.1, alpha=0.002,
+                            varphi_high=0.1, width=4.0)
+    s = ehd.Sim(p)
+    s.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
+    st = s.step(2000)
+    return p, ehd.Params.from_dict(p), st, s.fields()
+
+
+_LAYERS = []
+
+
+def layers():
+    if not _LAYERS:
+        _LAYERS.append(layers_run())
+    return _LAYERS[0]
+
+
+def force_balance_residual(F):
+    """At rest the momentum equation (Sec. 2.1) reduces to grad p = F, with the body
+    force F = hbar grad(phi) + q E of Eq. weq30 (p is the modified pressure).  On the
+    lattice the balance holds between the central difference of p across a row and the
+    force averaged over that row and its two neighbours (weights 1/4, 1/2, 1/4).  Returns
+    the relative L2 mismatch over the rows two or more nodes away from the walls, the force
+    formed from the returned fields (phi's gradient by central differences, which is the
+    isotropic stencil for a profile along y)."""
+    phi, q, Ey, mu, p = (F[k][:, 0] for k in ("phi", "q", "Ey", "mu", "p"))
+    ny = len(phi)
+    dphi = np.zeros(ny)
+    dp = np.zeros(ny)
+    dphi[1:-1] = 0.5 * (phi[2:] - phi[:-2])
+    dp[1:-1] = 0.5 * (p[2:] - p[:-2])
+    Fy = mu * dphi + q * Ey
+    r = slice(2, ny - 2)
+    avg = 0.25 * Fy[1:-3] + 0.5 * Fy[2:-2] + 0.25 * Fy[3:-1]
+    return float(np.linalg.norm(dp[r] - avg) / np.linalg.norm(Fy[r]))
 
 
 def test_planar_layers_steady_state():
@@ -17,14 +61,8 @@ def test_planar_layers_steady_state():
     Eq. weq72 within 15 % (the interface is 4 nodes wide on 32 rows); the interface
     charge obeys Gauss's law Q = J (eps_v/sigma_v - eps_l/sigma_l) within 8 %; the flow
     stays at rest; the potential loop needs one sub-iteration per step once steady."""
-    ny = 32
-    p, f = wl.planar_layers(nx=4, ny=ny, eps_v=0.5, sigma_v=0.1, alpha=0.002,
-                            varphi_high=0.1, width=4.0)
-    P = ehd.Params.from_dict(p)
-    s = ehd.Sim(p)
-    s.set_fields(f["phi"], f["q"], f["ux"], f["uy"])
-    st = s.step(2000)
-    F = s.fields()
+    ny = NY
+    p, P, st, F = layers()
     yc, W = (ny - 1) / 2, 4.0
     phi_y = lambda t: 0.5 + 0.5 * math.tanh(2 * (yc - t) / W)
     dphi = lambda t: -(1 / W) * (1 - math.tanh(2 * (yc - t) / W) ** 2)
@@ -42,3 +80,31 @@ def test_planar_layers_steady_state():
     assert abs(Q / (J * (P.eps_v / P.sigma_v - P.eps_l / P.sigma_l)) - 1) < 0.08
     assert np.abs(F["uy"]).max() < 1e-5
     assert st.poisson_iters[-1] == 1
+
+
+def test_planar_layers_pressure_balances_the_body_force():
+    """The layers at rest: the pressure gradient balances F = hbar grad(phi) + q E within
+    4 % (2 % measured after 2000 steps, the rest of the start transient still decaying;
+    0.24 % after 5000)."""
+    _, _, _, F = layers()
+    assert np.abs(F["uy"]).max() < 1e-5
+    assert force_balance_residual(F) < 0.04
+
+
+@pytest.mark.parametrize("mistake", ["reversed q E", "dropped hbar grad phi"])
+def test_planted_mistakes_in_the_body_force_fail(monkeypatch, mistake):
+    """Planted mistakes in Eq. weq30: the electric force with the wrong sign (the balance
+    is 200 % off) or the capillary force hbar grad(phi) left out (9 % off).  The flow
+    still stays at rest (the layers are one-dimensional), so only the force balance sees
+    them."""
+    orig = ehd.body_force
+
+    def wrong(P, mu_c, gphi_x, gphi_y, q, Ex, Ey, rho):
+        if mistake == "reversed q E":
+            return orig(P, mu_c, gphi_x, gphi_y, -q, Ex, Ey, rho)
+        return orig(P, 0.0 * mu_c, gphi_x, gphi_y, q, Ex, Ey, rho)
+
+    monkeypatch.setattr(ehd, "body_force", wrong)
+    _, _, _, F = layers_run()
+    assert np.abs(F["uy"]).max() < 1e-5
+    assert force_balance_residual(F) > 0.06
