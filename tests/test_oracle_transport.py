@@ -264,6 +264,47 @@ def test_planted_mistake_ch_source_time_term_fails(monkeypatch):
 # ---------------------------------------------------------------------------------------
 
 
+def uniform_flow_errors(rho_l, phi0, steps=20, N=16, u=(0.06, -0.03), p0=0.01):
+    """A single phase (phi = phi0 everywhere, so no interface, charge or force) moving at
+    the uniform velocity u with the uniform pressure p0, periodic: the exact solution is
+    that nothing changes.  Returns the largest deviations of u and p after `steps` steps."""
+    p = wl.make_params(nx=N, ny=N, walls_y=0, rho_l=rho_l, rho_v=1.0, mu_l=0.1, mu_v=0.1,
+                       eps_l=1.0, eps_v=1.0, sigma_l=0.0, sigma_v=0.0, alpha=0.02,
+                       gamma=0.01, width=4.0, mobility=0.05, poisson_fixed_iter=1,
+                       neutralize_charge=1)
+    z = np.zeros((N, N))
+    s = ehd.Sim(p)
+    s.set_fields(z + phi0, z, z + u[0], z + u[1], z + p0)
+    s.step(steps)
+    F = s.fields()
+    du = max(np.abs(F["ux"] - u[0]).max(), np.abs(F["uy"] - u[1]).max())
+    return du, np.abs(F["p"] - p0).max()
+
+
+@pytest.mark.parametrize("rho_l,phi0", [(1.0, 0.0), (3.0, 1.0)])
+def test_uniform_flow_keeps_velocity_and_pressure(rho_l, phi0):
+    """Uniform flow is an exact steady state (Galilean invariance): after 20 steps u and p
+    equal their initial values to rounding (1e-14).  The pressure is the moment of
+    Eq. eq32, whose rho s_0(u) term removes the velocity's share of the rest population."""
+    du, dp = uniform_flow_errors(rho_l, phi0)
+    assert du < 1e-14 and dp < 1e-14
+
+
+def test_planted_mistake_pressure_without_velocity_term_fails(monkeypatch):
+    """Planted mistake: the rho s_0(u) term left out of the pressure moment (Eq. eq32).
+    Each step then feeds the wrong pressure back into the equilibrium, and the uniform
+    flow's pressure drifts away from p0 (by 0.047 after 20 steps here)."""
+    orig = ehd.Sim._pressure
+
+    def wrong(self, phi, rho, ux, uy, gphi_x, gphi_y):
+        return (orig(self, phi, rho, ux, uy, gphi_x, gphi_y)
+                - ehd.CS2 / (1.0 - ehd.W[0]) * rho * ehd.s_i(ux, uy)[0])
+
+    monkeypatch.setattr(ehd.Sim, "_pressure", wrong)
+    du, dp = uniform_flow_errors(1.0, 0.0)
+    assert dp > 1e-2
+
+
 def test_momentum_budget_exact():
     """Exact momentum budget of the hydro LBE on a fully periodic domain (Eqs. weq38,
     weq39 with sum c_i R_bar_i = F, and the lagged u closure of Algorithm 1): sum_x sum_i c f
