@@ -345,3 +345,29 @@ def test_fields_mu_uniform_phase_in_uniform_field():
     field_part = 0.5 * ehd.deps_dphi(P, c) * E * E
     assert abs(field_part) > 1e-3 * abs(want)
     assert np.allclose(F["mu"], want, rtol=0, atol=1e-6 * abs(field_part))
+
+
+def test_initial_ch_populations_carry_the_initial_chemical_potential():
+    """Algorithm 1 step 1 (reading R12): the CH populations start at the equilibrium of
+    Eq. weq46 for the initial phi and its chemical potential (Eq. weq31, no field yet).
+    That equilibrium's second moment is c_s^2 hbar I, so sum_i c_iy^2 g_i = c_s^2 hbar,
+    sum_i c_ix c_iy g_i = 0 and sum_i g_i = phi.  hbar is formed here from the bulk term
+    and kappa times the central second difference, which is the isotropic Laplacian for a
+    profile along y (a periodic band, so no wall rows)."""
+    ny, nx = 32, 4
+    p = wl.make_params(nx=nx, ny=ny, walls_y=0)
+    P = ehd.Params.from_dict(p)
+    y = np.arange(ny, dtype=float)[:, None] * np.ones((1, nx))
+    # a band twice as steep as the equilibrium profile, so that hbar is far from zero
+    phi = wl.tanh_profile(8.0 - np.abs(y - ny / 2), 0.5 * p["width"])
+    z = np.zeros((ny, nx))
+    s = ehd.Sim(p)
+    s.set_fields(phi, z, z, z)
+    lap = np.roll(phi, 1, axis=0) + np.roll(phi, -1, axis=0) - 2.0 * phi
+    hbar = 4.0 * P.beta * phi * (phi - 0.5) * (phi - 1.0) - P.kappa * lap
+    cx = np.array([c[0] for c in ehd.C], dtype=float)[:, None, None]
+    cy = np.array([c[1] for c in ehd.C], dtype=float)[:, None, None]
+    assert np.allclose((cy * cy * s.g).sum(axis=0), ehd.CS2 * hbar, atol=1e-14, rtol=0)
+    assert np.allclose((cx * cy * s.g).sum(axis=0), 0.0, atol=1e-15)
+    assert np.allclose(s.g.sum(axis=0), phi, atol=1e-14, rtol=0)
+    assert np.abs(hbar).max() > 1e-3   # the check has something to see

@@ -208,6 +208,43 @@ def test_flat_interface_stationary():
     assert drift[0] < 1e-2 and drift[0] / drift[1] > 4.0
 
 
+def ch_cosine_decay_error(N, amp=1e-3, t1=50, t2=450):
+    """A small cosine amp cos(2 pi x / N) on the bulk phase phi = 0 (periodic N x 4, no
+    flow to speak of, no charge).  Linearising the CH equation about phi = 0, where the
+    bulk free energy's second derivative is 2 beta, the mode decays as exp(-lambda t) with
+    lambda = M k^2 (2 beta + kappa k^2) (Sec. 2.2; M the mobility of Sec. 3.2).  Returns
+    the relative error of the measured rate from step t1 to t2."""
+    ny = 4
+    p = wl.make_params(nx=N, ny=ny, walls_y=0, rho_l=1.0, rho_v=1.0, mu_l=0.1, mu_v=0.1,
+                       eps_l=1.0, eps_v=1.0, sigma_l=0.0, sigma_v=0.0, alpha=0.02,
+                       gamma=0.01, width=4.0, mobility=0.05, poisson_fixed_iter=1,
+                       neutralize_charge=1)
+    x = np.meshgrid(np.arange(N, dtype=float), np.arange(ny, dtype=float))[0]
+    k = 2 * math.pi / N
+    z = np.zeros((ny, N))
+    s = _sim(p, dict(phi=amp * np.cos(k * x), q=z, ux=z, uy=z))
+
+    def amplitude():
+        return 2 * (s.fields()["phi"][0] * np.cos(k * x[0])).mean()
+
+    s.step(t1)
+    a1 = amplitude()
+    s.step(t2 - t1)
+    a2 = amplitude()
+    P = s.P
+    lam = -math.log(a2 / a1) / (t2 - t1)
+    return lam / (P.mobility * k * k * (2 * P.beta + P.kappa * k * k)) - 1
+
+
+def test_ch_cosine_mode_decays_at_the_linearised_rate():
+    """The linearised CH decay rate M k^2 (2 beta + kappa k^2): within 5e-3 at N = 64 and
+    1e-3 at N = 128 (measured 1.3e-3 and 3.4e-4: second order).  This pins the CH
+    relaxation time against the mobility (M = c_s^2 (tau_g - 1/2)) and the chemical
+    potential's bulk and gradient terms together."""
+    assert abs(ch_cosine_decay_error(64)) < 5e-3
+    assert abs(ch_cosine_decay_error(128)) < 1e-3
+
+
 def translated_band_spread_change(u0=0.05, N=64, t1=100, t2=300):
     """A band of phase l (20 nodes wide, two flat interfaces of width 4, uniform density
     and viscosity, no charge) in a periodic N x 4 box of fluid moving at u0 along x.  The
