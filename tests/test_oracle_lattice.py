@@ -371,3 +371,24 @@ def test_initial_ch_populations_carry_the_initial_chemical_potential():
     assert np.allclose((cx * cy * s.g).sum(axis=0), 0.0, atol=1e-15)
     assert np.allclose(s.g.sum(axis=0), phi, atol=1e-14, rtol=0)
     assert np.abs(hbar).max() > 1e-3   # the check has something to see
+
+
+def test_initial_populations_carry_the_initial_flux_and_momentum():
+    """Algorithm 1 step 1 (reading R12): the charge and hydrodynamic populations start at
+    the equilibria of Eqs. weq61 and weq40 for the initial fields, whose first moments are
+    the charge flux q u and the momentum rho u (rho from the initial phi)."""
+    ny, nx = 12, 10
+    p = wl.make_params(nx=nx, ny=ny, walls_y=1, rho_l=3.0, rho_v=1.0)
+    P = ehd.Params.from_dict(p)
+    phi = RNG.uniform(0.0, 1.0, size=(ny, nx))
+    q = RNG.normal(size=(ny, nx)) * 1e-3
+    ux, uy = RNG.normal(size=(2, ny, nx)) * 1e-2
+    s = ehd.Sim(p)
+    s.set_fields(phi, q, ux, uy, RNG.normal(size=(ny, nx)) * 1e-3)
+    cx = np.array([c[0] for c in ehd.C], dtype=float)[:, None, None]
+    cy = np.array([c[1] for c in ehd.C], dtype=float)[:, None, None]
+    rho = P.rho_v + phi * (P.rho_l - P.rho_v)
+    assert np.allclose((cx * s.l).sum(axis=0), q * ux, atol=1e-16, rtol=0)
+    assert np.allclose((cy * s.l).sum(axis=0), q * uy, atol=1e-16, rtol=0)
+    assert np.allclose((cx * s.f).sum(axis=0), rho * ux, atol=1e-15, rtol=0)
+    assert np.allclose((cy * s.f).sum(axis=0), rho * uy, atol=1e-15, rtol=0)

@@ -59,3 +59,18 @@ def test_ramp_and_clamp():
     assert abs(ehd.cos_theta_eff(P, 50)[0] - 0.8 * 0.25) < 1e-15
     P2 = ehd.Params.from_dict(wl.make_params(nx=4, ny=4, theta_bottom_deg=30.0, ew_bottom=0.8))
     assert ehd.cos_theta_eff(P2, 0)[0] == 1.0
+
+
+def test_each_wall_takes_its_own_young_angle():
+    """A cap hanging from the top wall with theta_top = 60 degrees, the bottom wall set to
+    120 degrees: it keeps 60 degrees within 2 (the mirror image of the bottom-wall case,
+    so each wall's rule reads its own angle)."""
+    nx, ny, R = 64, 32, 14
+    p = wl.make_params(nx=nx, ny=ny, walls_y=1, gamma=0.03, width=4.0, mobility=0.1,
+                       mu_l=0.1, mu_v=0.1, theta_bottom_deg=120.0, theta_top_deg=60.0)
+    phi0 = cap(nx, ny, R, 60.0, 4.0)[::-1].copy()
+    z = np.zeros((ny, nx))
+    s = ehd.Sim(p)
+    s.set_fields(phi0, z, z, z)
+    s.step(1500)
+    assert abs(an.cap_contact_angle(s.fields()["phi"][::-1]) - 60.0) < 2.0
